@@ -1,0 +1,163 @@
+"""ctypes binding of the C ABI in include/bdl.h -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes the
+same arguments (device pointers as Python ints, the stream as an int handle);
+all computation happens in the CUDA library.  Loading fails loudly if the
+library has not been built: there is no fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libbdl_gb300.so")
+
+BDL_OK, BDL_EINVAL, BDL_ENOMEM, BDL_ECUDA, BDL_ETIMEOUT, BDL_EINTERNAL = range(6)
+
+SYMBOLS = [
+    "bdl_default_config", "bdl_create", "bdl_insert", "bdl_erase", "bdl_knn", "bdl_size",
+    "bdl_destroy", "bdl_status_string", "bdl_last_error", "bdl_tree_mask", "bdl_buffer_ids",
+    "bdl_tree_info", "bdl_tree_export", "bdl_bloom_export", "bdl_knn_stats", "bdl_launch_count",
+]
+
+
+class BdlConfig(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("buffer_size", ctypes.c_int32),
+                ("bloom_bits_per_key", ctypes.c_int32), ("bloom_hashes", ctypes.c_int32),
+                ("hash_seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class BdlError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s failed: status %d (%s): %s" % (where, status, status_string(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the shared library (build it first with build_lib.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library not built: %s is missing (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "bdl_default_config": (None, [P]),
+        "bdl_create": (i32, [i32, P, P, i64, P, P, P]),
+        "bdl_insert": (i32, [P, P, i64, P, P]),
+        "bdl_erase": (i32, [P, P, i64, P, P]),
+        "bdl_knn": (i32, [P, P, i64, i32, P, P, P]),
+        "bdl_size": (i32, [P, P]),
+        "bdl_destroy": (i32, [P]),
+        "bdl_status_string": (ctypes.c_char_p, [i32]),
+        "bdl_last_error": (ctypes.c_char_p, []),
+        "bdl_tree_mask": (i32, [P, P, P]),
+        "bdl_buffer_ids": (i32, [P, P, i64, P, P]),
+        "bdl_tree_info": (i32, [P, i32, P]),
+        "bdl_tree_export": (i32, [P, i32, P, P, P, P, P, P, P]),
+        "bdl_bloom_export": (i32, [P, i32, P, P]),
+        "bdl_knn_stats": (i32, [P, i32, P]),
+        "bdl_launch_count": (u64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(st):
+    return load().bdl_status_string(st).decode()
+
+
+def last_error():
+    return load().bdl_last_error().decode()
+
+
+def check(st, where):
+    if st != BDL_OK:
+        raise BdlError(st, where, last_error())
+    return st
+
+
+def _ref(x):
+    return ctypes.byref(x)
+
+
+# --- entry points (same names as the C ABI) --------------------------------
+
+def bdl_default_config():
+    cfg = BdlConfig()
+    load().bdl_default_config(_ref(cfg))
+    return cfg
+
+
+def bdl_create(dim, cfg, pts_dev, n, out_ids_dev, stream):
+    """Returns (status, forest handle)."""
+    h = ctypes.c_void_p()
+    st = load().bdl_create(dim, _ref(cfg) if cfg is not None else None, pts_dev, n,
+                           out_ids_dev, stream, _ref(h))
+    return st, h.value
+
+
+def bdl_insert(f, pts_dev, n, out_ids_dev, stream):
+    return load().bdl_insert(f, pts_dev, n, out_ids_dev, stream)
+
+
+def bdl_erase(f, ids_dev, n, stream):
+    """Returns (status, number erased)."""
+    out = ctypes.c_int64(0)
+    st = load().bdl_erase(f, ids_dev, n, _ref(out), stream)
+    return st, out.value
+
+
+def bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
+    return load().bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream)
+
+
+def bdl_size(f):
+    out = ctypes.c_int64(0)
+    st = load().bdl_size(f, _ref(out))
+    return st, out.value
+
+
+def bdl_destroy(f):
+    return load().bdl_destroy(f)
+
+
+def bdl_tree_mask(f):
+    m = ctypes.c_uint64(0)
+    nb = ctypes.c_int64(0)
+    st = load().bdl_tree_mask(f, _ref(m), _ref(nb))
+    return st, m.value, nb.value
+
+
+def bdl_buffer_ids(f, out_host_ptr, cap, stream):
+    n = ctypes.c_int64(0)
+    st = load().bdl_buffer_ids(f, out_host_ptr, cap, _ref(n), stream)
+    return st, n.value
+
+
+def bdl_tree_info(f, level, info_host_ptr):
+    return load().bdl_tree_info(f, level, info_host_ptr)
+
+
+def bdl_tree_export(f, level, key, child, box, live, leaf_off, ids, stream):
+    return load().bdl_tree_export(f, level, key, child, box, live, leaf_off, ids, stream)
+
+
+def bdl_bloom_export(f, level, words, stream):
+    return load().bdl_bloom_export(f, level, words, stream)
+
+
+def bdl_knn_stats(f, enable, out_host_ptr):
+    return load().bdl_knn_stats(f, enable, out_host_ptr)
+
+
+def bdl_launch_count():
+    return int(load().bdl_launch_count())

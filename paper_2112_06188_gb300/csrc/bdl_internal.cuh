@@ -1,0 +1,280 @@
+// bdl_internal.cuh -- types and device helpers shared by the CUDA translation
+// units of the BDL-tree library (forest.cu, build.cu, erase.cu, knn.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/bdl.h"
+
+namespace bdl {
+
+constexpr int kMaxDim = 16;
+constexpr int kMaxLevel = 40;          // trees 0..39; ids < 2^31 keep us far below
+constexpr int kMaxK = 32;
+constexpr int kCoordBits = 20;         // grid [0, 2^20)
+constexpr int kKeyBits = 51;           // composite key: coord << 31 | id
+constexpr uint32_t kTomb = 0x80000000u;  // erased point: id | kTomb (negative int32)
+constexpr int kHistBins = 2048;        // 11-bit digit of the global median search
+constexpr int kHistShift = kCoordBits - 11;
+
+extern std::atomic<uint64_t> g_launches;
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+// Composite split key in one dimension (coordinate, ties by id): Sec. IV-A1
+// needs a strict order so that every node splits its points exactly in half.
+__host__ __device__ inline uint64_t comp_key(int32_t coord, int32_t id) {
+  return ((uint64_t)(uint32_t)coord << 31) | (uint64_t)(uint32_t)id;
+}
+
+// Smallest power of two >= l/2: levels of the bottom part of a vEB split.
+__host__ __device__ inline int veb_bottom(int l) {
+  int lb = 1;
+  while (2 * lb < l) lb *= 2;
+  return lb;
+}
+
+// Slot of node (depth t, index i at that depth) in the vEB layout of a
+// complete tree with l levels (Alg. 1): the top l_t levels come first, then
+// the 2^l_t bottom trees of l_b levels, each laid out recursively.
+__host__ __device__ inline int64_t veb_slot(int l, int t, int64_t i) {
+  int64_t off = 0;
+  while (l > 1) {
+    int lb = veb_bottom(l);
+    int lt = l - lb;
+    if (t < lt) {
+      l = lt;
+    } else {
+      int tt = t - lt;
+      int64_t j = i >> tt;
+      off += (((int64_t)1 << lt) - 1) + j * (((int64_t)1 << lb) - 1);
+      i &= ((int64_t)1 << tt) - 1;
+      t = tt;
+      l = lb;
+    }
+  }
+  return off;
+}
+
+// Point range of segment `idx` at depth t of a tree over s points, where every
+// split gives the left child ceil(m/2) points.  O(t).
+__host__ __device__ inline void seg_range(int64_t s, int t, int64_t idx, int64_t &start,
+                                          int64_t &size) {
+  start = 0;
+  size = s;
+  for (int u = t - 1; u >= 0; --u) {
+    int64_t l = (size + 1) >> 1;
+    if ((idx >> u) & 1) {
+      start += l;
+      size -= l;
+    } else {
+      size = l;
+    }
+  }
+}
+
+// Segment at depth t that holds position p (0 <= p < s).  O(t).
+__host__ __device__ inline int64_t seg_of(int64_t s, int t, int64_t p, int64_t &start,
+                                          int64_t &size) {
+  start = 0;
+  size = s;
+  int64_t idx = 0;
+  for (int u = 0; u < t; ++u) {
+    int64_t l = (size + 1) >> 1;
+    if (p < start + l) {
+      size = l;
+      idx = 2 * idx;
+    } else {
+      start += l;
+      size -= l;
+      idx = 2 * idx + 1;
+    }
+  }
+  return idx;
+}
+
+// Split levels of a tree over s points with leaves of at most L points:
+// h = ceil(log2(ceil(s / L))).
+__host__ __device__ inline int tree_height(int64_t s, int L) {
+  int64_t nl = (s + L - 1) / L;
+  int h = 0;
+  while (((int64_t)1 << h) < nl) h++;
+  return h;
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014) applied to x.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Split-block bloom filter position of an id: block and one bit per word.
+__host__ __device__ inline void bloom_hash(uint64_t seed, int64_t blocks, int32_t id,
+                                           int64_t &blk, uint64_t &bits) {
+  uint64_t h1 = splitmix64(seed ^ (uint64_t)(uint32_t)id);
+  bits = splitmix64(h1);
+  blk = (int64_t)(h1 & (uint64_t)(blocks - 1));
+}
+
+__device__ inline uint32_t bloom_word_bit(uint64_t bits, int w) {
+  return 1u << ((bits >> (5 * w)) & 31u);
+}
+
+// ---------------------------------------------------------------------------
+// device views
+// ---------------------------------------------------------------------------
+
+struct TreeView {          // one static tree, device pointers
+  const int32_t *pts;      // SoA [dim][size]
+  int32_t *ids;            // [size]; erased: id | kTomb
+  const uint64_t *key;     // [nnodes]
+  const int2 *child;       // [nnodes]
+  const int32_t *box;      // [nnodes][2*dim]
+  int32_t *live;           // [nnodes]
+  const int32_t *leaf_off; // [2^h + 1]
+  const uint32_t *bloom;   // [blocks * 8] or nullptr
+  int64_t size;
+  int64_t nnodes;
+  int64_t bloom_blocks;
+  int32_t h;
+  int32_t level;
+};
+
+struct ForestView {        // what the k-NN and erase kernels see
+  int ntrees;              // nonempty trees, largest first
+  TreeView tree[kMaxLevel];
+  const int32_t *idtab;    // [id][dim]
+  const int32_t *buf;      // buffer ids
+  int64_t nbuf;
+  int dim;
+  unsigned long long *err; // device error word (bit codes below), never null
+};
+
+// Device error codes: a kernel that finds an index outside its buffers
+// records one of these bits and skips the access instead of faulting.
+enum : unsigned long long {
+  kErrChild = 1,       // child slot outside the node array
+  kErrLeaf = 2,        // leaf range outside the point array
+  kErrStack = 4,       // traversal stack full
+  kErrPartition = 8,   // partition destination outside its segment
+  kErrGather = 16,     // gather destination outside its tree
+};
+
+// ---------------------------------------------------------------------------
+// host-side state
+// ---------------------------------------------------------------------------
+
+struct Tree {
+  int level = 0;
+  int64_t size = 0, live = 0;
+  int h = 0;
+  int64_t nnodes = 0, nleaves = 0;
+  void *block = nullptr;   // one pool allocation holding the arrays below
+  size_t bytes = 0;
+  int32_t *pts = nullptr, *ids = nullptr, *box = nullptr, *live_nodes = nullptr,
+          *leaf_off = nullptr;
+  uint64_t *key = nullptr;
+  int2 *child = nullptr;
+  uint32_t *bloom = nullptr;   // separate allocation, built lazily
+  int64_t bloom_blocks = 0;
+  size_t bloom_bytes = 0;
+};
+
+// One tree to build: where its input points are and where its arrays go.
+struct BuildTree {
+  Tree *tree;
+  int64_t base;            // first position in the staging arrays (multiple of 8)
+  int64_t s;
+  int h;
+  int g;                   // levels split by the global kernels
+};
+
+struct Scratch;            // allocation helper (forest.cu)
+
+}  // namespace bdl
+
+struct bdl_forest {
+  int dim = 0;
+  bdl_config cfg{};
+  int device = 0;
+  cudaMemPool_t pool = nullptr;
+  int32_t *idtab = nullptr;      // [id_cap][dim]
+  uint32_t *alive = nullptr;     // [id_cap / 32]
+  int64_t id_cap = 0, next_id = 0;
+  int32_t *buf = nullptr;        // [X] ascending ids
+  int64_t nbuf = 0;
+  bdl::Tree *trees[bdl::kMaxLevel] = {};
+  uint64_t F = 0;
+  int64_t live = 0;              // host mirror of the live count
+  int64_t bytes_in_use = 0;
+  int64_t *pinned = nullptr;     // small pinned host scratch for counts
+  int64_t *dev_small = nullptr;  // small device scratch for counts / flags
+  unsigned long long *err = nullptr;  // device error word (inside dev_small)
+  bool debug_check = false;      // BDL_DEBUG_CHECK=1: sync and check err after each call
+  unsigned long long *knn_stats = nullptr;  // [3] device counters, or nullptr
+};
+
+namespace bdl {
+
+// ---- forest.cu ----
+int set_error(int status, const std::string &msg);
+int cuda_check(cudaError_t e, const char *what);
+int dev_alloc(bdl_forest *f, void **p, size_t bytes, cudaStream_t s);
+void dev_free(bdl_forest *f, void *p, size_t bytes, cudaStream_t s);
+ForestView forest_view(const bdl_forest *f);
+int smem_subtree_capacity(int dim);
+
+// ---- build.cu ----
+// Gather the points of the new trees into staging and build them.
+struct PoolSrc {
+  const int32_t *buf;      // sorted buffer ids (nbuf of them)
+  int64_t nbuf;
+  const int32_t *arr;      // explicit ids, or nullptr for a range
+  int64_t first;           // first id of the range
+};
+struct ClearedSrc {        // a cleared tree whose live points join a new tree
+  const int32_t *pts;
+  const int32_t *ids;
+  int64_t size;
+  int32_t dst;             // index into the BuildTree list
+};
+int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<ClearedSrc> &cl,
+                const PoolSrc &pool, const std::vector<int64_t> &pool_lo,
+                const std::vector<int64_t> &from_cleared, cudaStream_t s);
+int build_scratch_bytes(const bdl_forest *f, const std::vector<BuildTree> &bt, size_t *bytes);
+void launch_pool_tail(const PoolSrc &pool, int64_t from, int64_t count, int32_t *dst,
+                      cudaStream_t s);
+void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s);
+
+// ---- erase.cu ----
+void launch_append_validate(const int32_t *pts, int64_t n, int dim, int32_t *idtab_dst,
+                            int64_t *flag, cudaStream_t s);
+void launch_set_alive(uint32_t *alive, int64_t first, int64_t n, cudaStream_t s);
+void launch_iota(int32_t *out, int64_t first, int64_t n, cudaStream_t s);
+void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
+                       int32_t *list, int64_t *count, cudaStream_t s);
+void launch_bloom_build(const Tree *t, uint64_t seed, cudaStream_t s);
+void launch_erase_locate(const ForestView &fv, uint64_t seed, const int32_t *list, int64_t n,
+                         cudaStream_t s);
+void launch_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n,
+                           cudaStream_t s);
+void launch_gather_roots(const ForestView &fv, int64_t *out, cudaStream_t s);
+int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n,
+                        int32_t *out, cudaStream_t s);
+
+// ---- knn.cu ----
+int launch_knn(const ForestView &fv, const int32_t *q, int64_t m, int k, int32_t *out_ids,
+               int64_t *out_d2, unsigned long long *stats, cudaStream_t s);
+
+}  // namespace bdl
+
+#define BDL_LAUNCHED() (::bdl::g_launches.fetch_add(1, std::memory_order_relaxed))

@@ -1,0 +1,1086 @@
+// build.cu -- batched construction of the static kd-trees of one Insert_L
+// (Alg. 3 line 5): gather the points of every new tree, then build all of them
+// together with median splits in vEB layout (Alg. 1).
+//
+// GPU design (level-synchronous instead of Alg. 1's recursion):
+//  * Every new tree is a complete tree with h = ceil(log2(ceil(s/L))) split
+//    levels; the segment of points under node (depth t, index i) is fixed by
+//    s alone (left child = ceil(m/2) points), so all trees advance depth by
+//    depth in shared launches.
+//  * Global levels (segments larger than one CTA's shared memory): an 11-bit
+//    histogram of the split coordinate per segment, a per-segment bucket
+//    search, a candidate gather of the median's bucket, an exact radix select
+//    on the candidates' (low coordinate bits, id) key, and a partition pass
+//    that moves whole records into the other staging buffer.
+//  * Once segments fit in shared memory, one CTA builds each remaining
+//    subtree entirely on chip (radix select on the composite key with
+//    per-level digit widths, rank-counting for segments <= 64 points),
+//    writes leaves, bounding boxes and live counts, and stores the points in
+//    leaf order.
+//  * Node slots follow the vEB layout in closed form (veb_slot), children are
+//    stored explicitly, boxes of the global-level nodes are merged bottom-up.
+#include "bdl_internal.cuh"
+
+#include <algorithm>
+
+namespace bdl {
+
+namespace {
+
+constexpr int kItems = 8;          // records per thread in the tiled kernels
+constexpr int kSubThreads = 1024;  // threads of the subtree kernel
+constexpr int kWarpMode = 64;      // segments this small use rank counting
+constexpr int kMaxRadixSegs = 128; // segments per level in radix mode (cap / 64)
+
+struct SegState {
+  unsigned long long cand_n;   // candidates gathered
+  unsigned long long lcur;     // records placed left / right
+  unsigned long long rcur;
+  uint64_t median;             // composite key of the median
+  int64_t rank;                // 1-based rank of the median inside its bucket
+  int32_t bucket;              // top-11-bit bucket of the split coordinate
+  int32_t nbucket;
+};
+
+struct NodeOut {               // where a tree's arrays go
+  int32_t *pts, *ids, *box, *live, *leaf_off;
+  uint64_t *key;
+  int2 *child;
+};
+
+struct LvTree {
+  int64_t base, s, seg_off, tile_off;
+  int32_t t, c, h, slot;
+};
+
+struct LvParams {
+  int ntrees, dim, tile;
+  int64_t S;
+  const int32_t *src;
+  int32_t *dst;
+  uint32_t *hist;
+  SegState *seg;
+  uint64_t *cand;
+  unsigned long long *err;
+  LvTree tr[kMaxLevel];
+  NodeOut out[kMaxLevel];
+};
+
+__device__ __forceinline__ int find_tree_by_tile(const LvParams &P, int64_t b) {
+  int j = 0;
+  while (j + 1 < P.ntrees && P.tr[j + 1].tile_off <= b) j++;
+  return j;
+}
+
+__device__ __forceinline__ int find_tree_by_seg(const LvParams &P, int64_t g) {
+  int j = 0;
+  while (j + 1 < P.ntrees && P.tr[j + 1].seg_off <= g) j++;
+  return j;
+}
+
+// ---------------------------------------------------------------------------
+// K5: gather the points of each new tree into the staging arrays
+// ---------------------------------------------------------------------------
+
+struct GatherParams {
+  int nsrc, ntrees, dim;
+  int64_t S;
+  int32_t *stg;                       // staging A: [dim+1][S]
+  unsigned long long *cursor;         // per new tree: records placed from cleared trees
+  unsigned long long *err;
+  // cleared sources
+  const int32_t *spts[kMaxLevel];
+  const int32_t *sids[kMaxLevel];
+  int64_t ssize[kMaxLevel];
+  int64_t sblk[kMaxLevel + 1];        // block prefix
+  int32_t sdst[kMaxLevel];
+  // new trees
+  int64_t base[kMaxLevel];
+  int64_t from_cleared[kMaxLevel];
+  int64_t pool_lo[kMaxLevel + 1];     // pool chunk of tree j: [pool_lo[j], pool_lo[j+1])
+  // pool
+  const int32_t *pbuf;
+  int64_t pnbuf;
+  const int32_t *parr;
+  int64_t pfirst;
+  const int32_t *idtab;
+};
+
+__device__ __forceinline__ int32_t pool_id(const int32_t *buf, int64_t nbuf, const int32_t *arr,
+                                           int64_t first, int64_t k) {
+  if (k < nbuf) return buf[k];
+  return arr ? arr[k - nbuf] : (int32_t)(first + (k - nbuf));
+}
+
+__global__ void k_gather_cleared(const GatherParams P) {
+  __shared__ int wsum[32];
+  __shared__ unsigned long long sbase;
+  int b = blockIdx.x;
+  int src = 0;
+  while (src + 1 < P.nsrc && P.sblk[src + 1] <= b) src++;
+  int64_t p = (int64_t)(b - P.sblk[src]) * blockDim.x + threadIdx.x;
+  bool ok = p < P.ssize[src];
+  int32_t id = ok ? P.sids[src][p] : -1;
+  bool live = ok && id >= 0;
+  // block-exclusive count of live records
+  unsigned bal = __ballot_sync(0xffffffffu, live);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int wpre = __popc(bal & ((1u << lane) - 1));
+  if (lane == 0) wsum[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { int v = wsum[w]; wsum[w] = acc; acc += v; }
+    sbase = atomicAdd(&P.cursor[P.sdst[src]], (unsigned long long)acc);
+  }
+  __syncthreads();
+  if (!live) return;
+  int j = P.sdst[src];
+  int64_t rel = (int64_t)sbase + wsum[warp] + wpre;
+  if (rel >= P.from_cleared[j]) {   // more live records than the plan counted
+    atomicOr(P.err, kErrGather);
+    return;
+  }
+  int64_t dst = P.base[j] + rel;
+  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = P.spts[src][c * P.ssize[src] + p];
+  P.stg[P.dim * P.S + dst] = id;
+}
+
+__global__ void k_gather_pool(const GatherParams P, int64_t total) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  int j = 0;
+  while (j + 1 < P.ntrees && P.pool_lo[j + 1] <= k) j++;
+  int32_t id = pool_id(P.pbuf, P.pnbuf, P.parr, P.pfirst, k);
+  int64_t dst = P.base[j] + P.from_cleared[j] + (k - P.pool_lo[j]);
+  const int32_t *src = P.idtab + (int64_t)id * P.dim;
+  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = src[c];
+  P.stg[P.dim * P.S + dst] = id;
+}
+
+// ---------------------------------------------------------------------------
+// K1 global levels: histogram, bucket search, candidate gather, exact select
+// ---------------------------------------------------------------------------
+
+struct TileSegs {
+  int64_t p0, p1;          // tile [p0, p1) relative to the tree
+  int64_t idx0, st0, sz0;  // first segment
+  int64_t st1, sz1;        // second segment (sz1 = 0 if none)
+};
+
+__device__ __forceinline__ TileSegs tile_segs(const LvParams &P, const LvTree &T, int64_t b) {
+  TileSegs g;
+  g.p0 = (b - T.tile_off) * P.tile;
+  g.p1 = min(g.p0 + (int64_t)P.tile, T.s);
+  g.idx0 = seg_of(T.s, T.t, g.p0, g.st0, g.sz0);
+  g.sz1 = 0;
+  g.st1 = g.st0 + g.sz0;
+  if (g.p1 > g.st1) seg_range(T.s, T.t, g.idx0 + 1, g.st1, g.sz1);
+  return g;
+}
+
+__global__ void k_level_hist(const LvParams P) {
+  __shared__ uint32_t h[2][kHistBins];
+  int b = blockIdx.x;
+  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  TileSegs g = tile_segs(P, T, b);
+  for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int32_t *x = P.src + T.c * P.S + T.base;
+  for (int64_t p = g.p0 + threadIdx.x; p < g.p1; p += blockDim.x) {
+    int32_t c = x[p];
+    atomicAdd(&h[p >= g.st1][c >> kHistShift], 1u);
+  }
+  __syncthreads();
+  uint32_t *h0 = P.hist + (T.seg_off + g.idx0) * kHistBins;
+  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) {
+    uint32_t v = h[0][i];
+    if (v) atomicAdd(&h0[i], v);
+    if (g.sz1) {
+      v = h[1][i];
+      if (v) atomicAdd(&h0[kHistBins + i], v);
+    }
+  }
+}
+
+// One warp per segment: the bucket holding the median (rank ceil(m/2)).
+__global__ void k_level_bucket(const LvParams P, int64_t nseg) {
+  int64_t gs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gs >= nseg) return;
+  int lane = threadIdx.x & 31;
+  const LvTree &T = P.tr[find_tree_by_seg(P, gs)];
+  int64_t st, sz;
+  seg_range(T.s, T.t, gs - T.seg_off, st, sz);
+  int64_t r = (sz + 1) >> 1;
+  const uint32_t *hh = P.hist + gs * kHistBins;
+  int64_t below = 0;
+  for (int base = 0; base < kHistBins; base += 32) {
+    uint32_t v = hh[base + lane];
+    uint32_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (below + tot >= r) {
+      bool hit = (below + inc >= r) && (below + inc - v < r);
+      unsigned m = __ballot_sync(0xffffffffu, hit);
+      int src = __ffs(m) - 1;
+      uint32_t vv = __shfl_sync(0xffffffffu, v, src);
+      uint32_t ii = __shfl_sync(0xffffffffu, inc, src);
+      if (lane == 0) {
+        SegState &S = P.seg[gs];
+        S.bucket = base + src;
+        S.nbucket = (int32_t)vv;
+        S.rank = r - (below + ii - vv);
+        S.cand_n = 0;
+        S.lcur = 0;
+        S.rcur = 0;
+      }
+      return;
+    }
+    below += tot;
+  }
+}
+
+// Gather the (low coordinate bits, id) keys of every record in its segment's
+// median bucket, at the segment's own range of the candidate array.
+__global__ void k_level_collect(const LvParams P) {
+  __shared__ unsigned cnt[2];
+  __shared__ unsigned long long basev[2];
+  int b = blockIdx.x;
+  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  TileSegs g = tile_segs(P, T, b);
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const SegState *s0 = &P.seg[T.seg_off + g.idx0];
+  int32_t bk0 = s0[0].bucket, bk1 = g.sz1 ? s0[1].bucket : -1;
+  const int32_t *x = P.src + T.c * P.S + T.base;
+  const int32_t *xi = P.src + P.dim * P.S + T.base;
+  uint64_t key[kItems];
+  unsigned slot[kItems];
+  int nk = 0;
+  for (int64_t p = g.p0 + threadIdx.x; p < g.p1; p += blockDim.x) {
+    int32_t c = x[p];
+    int w = p >= g.st1;
+    if ((c >> kHistShift) == (w ? bk1 : bk0)) {
+      key[nk] = ((uint64_t)(c & ((1 << kHistShift) - 1)) << 31) | (uint32_t)xi[p];
+      slot[nk] = (atomicAdd(&cnt[w], 1u) << 1) | (unsigned)w;
+      nk++;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 && (threadIdx.x == 0 || g.sz1) && cnt[threadIdx.x])
+    basev[threadIdx.x] = atomicAdd(&P.seg[T.seg_off + g.idx0 + threadIdx.x].cand_n,
+                                   (unsigned long long)cnt[threadIdx.x]);
+  __syncthreads();
+  for (int i = 0; i < nk; ++i) {
+    int w = slot[i] & 1;
+    int64_t st = w ? g.st1 : g.st0;
+    P.cand[T.base + st + basev[w] + (slot[i] >> 1)] = key[i];
+  }
+}
+
+// One CTA per segment: exact select of the median among its bucket's keys
+// (8-bit digits over the 40-bit candidate key), then the node is written.
+__global__ void k_level_select(const LvParams P, int64_t nseg) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t s_pre;
+  __shared__ int64_t s_rank;
+  __shared__ uint32_t s_cnt;
+  __shared__ uint64_t s_found;
+  __shared__ uint64_t keys[2048];
+  int64_t gs = blockIdx.x;
+  if (gs >= nseg) return;
+  const LvTree &T = P.tr[find_tree_by_seg(P, gs)];
+  int64_t idx = gs - T.seg_off;
+  int64_t st, sz;
+  seg_range(T.s, T.t, idx, st, sz);
+  SegState &S = P.seg[gs];
+  int64_t n = (int64_t)S.cand_n;
+  const uint64_t *cand = P.cand + T.base + st;
+  bool in_smem = n <= 2048;
+  if (in_smem)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) keys[i] = cand[i];
+  if (threadIdx.x == 0) { s_pre = 0; s_rank = S.rank; s_cnt = (uint32_t)n; s_found = ~0ull; }
+  __syncthreads();
+  const int kbits = 31 + kHistShift;   // 40
+  int shift = kbits;
+  while (true) {
+    if (s_cnt == 1) {
+      // the unique key with this prefix
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        uint64_t k = in_smem ? keys[i] : cand[i];
+        if ((k >> shift) == (s_pre >> shift)) s_found = k;
+      }
+      __syncthreads();
+      break;
+    }
+    if (shift == 0) {
+      if (threadIdx.x == 0) s_found = s_pre;
+      __syncthreads();
+      break;
+    }
+    int ns = max(0, shift - 8);
+    int ww = shift - ns;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      uint64_t k = in_smem ? keys[i] : cand[i];
+      if ((k >> shift) == (s_pre >> shift)) atomicAdd(&hist[(k >> ns) & ((1u << ww) - 1)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t below = 0;
+      for (int j = 0; j < (1 << ww); ++j) {
+        if (below + hist[j] >= s_rank) {
+          s_pre |= (uint64_t)j << ns;
+          s_rank -= below;
+          s_cnt = hist[j];
+          break;
+        }
+        below += hist[j];
+      }
+    }
+    shift = ns;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    uint64_t k40 = s_found;
+    uint32_t coord = ((uint32_t)S.bucket << kHistShift) | (uint32_t)(k40 >> 31);
+    uint64_t med = comp_key((int32_t)coord, (int32_t)(k40 & 0x7fffffffu));
+    S.median = med;
+    const NodeOut &o = P.out[T.slot];
+    int l = T.h + 1;
+    int64_t v = veb_slot(l, T.t, idx);
+    o.key[v] = med;
+    o.child[v] = make_int2((int)veb_slot(l, T.t + 1, 2 * idx), (int)veb_slot(l, T.t + 1, 2 * idx + 1));
+  }
+}
+
+// K2: partition every tile's records around their segment's median into the
+// other staging buffer.  Left records of a segment go to [st, st+ceil(m/2)),
+// right ones after; each CTA reserves its ranges with one atomic per class.
+__global__ void k_level_partition(const LvParams P) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long cbase[4];
+  int b = blockIdx.x;
+  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  TileSegs g = tile_segs(P, T, b);
+  const SegState *s0 = &P.seg[T.seg_off + g.idx0];
+  uint64_t med0 = s0[0].median, med1 = g.sz1 ? s0[1].median : 0;
+  const int32_t *xc = P.src + T.c * P.S + T.base;
+  const int32_t *xi = P.src + P.dim * P.S + T.base;
+  int64_t pb = g.p0 + (int64_t)threadIdx.x * kItems;
+  int cls[kItems];
+  unsigned long long mine = 0;   // 4 x 16-bit class counts
+  for (int j = 0; j < kItems; ++j) {
+    int64_t p = pb + j;
+    cls[j] = -1;
+    if (p < g.p1) {
+      int w = p >= g.st1;
+      uint64_t k = comp_key(xc[p], xi[p]);
+      int c = 2 * w + (k > (w ? med1 : med0));
+      cls[j] = c;
+      mine += 1ull << (16 * c);
+    }
+  }
+  // block exclusive scan of the packed counts
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { unsigned long long v = wsum[w]; wsum[w] = acc; acc += v; }
+    for (int c = 0; c < 4; ++c) {
+      unsigned long long tot = (acc >> (16 * c)) & 0xffff;
+      cbase[c] = 0;
+      if (tot) {
+        const SegState &S = P.seg[T.seg_off + g.idx0 + (c >> 1)];
+        unsigned long long *cur = (c & 1) ? (unsigned long long *)&S.rcur : (unsigned long long *)&S.lcur;
+        cbase[c] = atomicAdd(cur, tot);
+      }
+    }
+  }
+  __syncthreads();
+  unsigned long long ex = inc - mine + wsum[warp];
+  int32_t dstp[kItems];
+  int run[4] = {0, 0, 0, 0};
+  for (int j = 0; j < kItems; ++j) {
+    int c = cls[j];
+    dstp[j] = -1;
+    if (c < 0) continue;
+    int64_t st = (c >> 1) ? g.st1 : g.st0;
+    int64_t sz = (c >> 1) ? g.sz1 : g.sz0;
+    int64_t off = (c & 1) ? ((sz + 1) >> 1) : 0;
+    int64_t rel = off + (int64_t)cbase[c] + (int64_t)((ex >> (16 * c)) & 0xffff) + run[c];
+    run[c]++;
+    int64_t lim = (c & 1) ? sz : ((sz + 1) >> 1);
+    if (rel >= lim) {               // the median did not split the segment in half
+      atomicOr(P.err, kErrPartition);
+      continue;
+    }
+    dstp[j] = (int32_t)(st + rel);
+  }
+  for (int c = 0; c <= P.dim; ++c) {
+    const int32_t *x = P.src + c * P.S + T.base;
+    int32_t *y = P.dst + c * P.S + T.base;
+    for (int j = 0; j < kItems; ++j)
+      if (dstp[j] >= 0) y[dstp[j]] = x[pb + j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1-K4 on chip: one CTA builds a whole subtree of <= cap records
+// ---------------------------------------------------------------------------
+
+struct SubTree {
+  int64_t base, s, blk_off;
+  int32_t h, t0, sel, slot;
+};
+
+struct SubParams {
+  int ntrees, dim, cap;
+  int64_t S;
+  const int32_t *stg[2];
+  unsigned long long *err;
+  SubTree tr[kMaxLevel];
+  NodeOut out[kMaxLevel];
+};
+
+__device__ __forceinline__ uint64_t skey(const int32_t *sc, const int32_t *sid, int cap, int c,
+                                         int it) {
+  return comp_key(sc[c * cap + it], sid[it]);
+}
+
+__global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ uint64_t s_pre[kMaxRadixSegs], s_res[kMaxRadixSegs];
+  __shared__ int32_t s_st[kMaxRadixSegs], s_sz[kMaxRadixSegs], s_rank[kMaxRadixSegs],
+      s_cnt[kMaxRadixSegs], s_cnt2[kMaxRadixSegs], s_lb[kMaxRadixSegs], s_dig[kMaxRadixSegs],
+      s_bel[kMaxRadixSegs];
+  __shared__ unsigned char s_done[kMaxRadixSegs], s_fnd[kMaxRadixSegs];
+  __shared__ uint32_t s_w[32];
+
+  const int cap = P.cap, dim = P.dim;
+  int b = blockIdx.x;
+  int tj = 0;
+  while (tj + 1 < P.ntrees && P.tr[tj + 1].blk_off <= b) tj++;
+  const SubTree &T = P.tr[tj];
+  const NodeOut &o = P.out[T.slot];
+  int64_t i0 = b - T.blk_off;
+  int64_t start0, m64;
+  seg_range(T.s, T.t0, i0, start0, m64);
+  const int m0 = (int)m64;
+  const int l = T.h + 1;
+
+  int32_t *sc = (int32_t *)sm;                          // [dim][cap]
+  int32_t *sid = sc + (size_t)dim * cap;                // [cap]
+  uint32_t *hist = (uint32_t *)(sid + cap);             // [2048]
+  uint32_t *ex = hist + kHistBins;                      // [2048]
+  uint16_t *perm0 = (uint16_t *)(ex + kHistBins);       // [cap]
+  uint16_t *perm1 = perm0 + cap;                        // [cap]
+  unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap]
+
+  const int32_t *src = P.stg[T.sel];
+  for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+    for (int c = 0; c < dim; ++c) sc[c * cap + q] = src[c * P.S + T.base + start0 + q];
+    sid[q] = src[dim * P.S + T.base + start0 + q];
+    perm0[q] = (uint16_t)q;
+    perm1[q] = (uint16_t)q;   // any slot a level leaves unwritten still names a record
+  }
+  __syncthreads();
+
+  const int U = T.h - T.t0;
+  uint16_t *cur = perm0, *nxt = perm1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+  for (int u = 0; u < U; ++u) {
+    const int t = T.t0 + u;
+    const int c = t % dim;
+    const int nseg = 1 << u;
+    int64_t st_, sz_;
+    seg_range(m0, u, 0, st_, sz_);
+    const int mmax = (int)sz_;
+    if (mmax > kWarpMode) {
+      // ---------------- radix mode: all segments of the level together ----
+      const int w = 11 - u;      // nseg << w == 2048 bins
+      for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        int64_t a, z;
+        seg_range(m0, u, s, a, z);
+        s_st[s] = (int)a;
+        s_sz[s] = (int)z;
+        s_pre[s] = 0;
+        s_rank[s] = (int)((z + 1) >> 1);
+        s_done[s] = 0;
+        s_fnd[s] = 0;
+        s_cnt[s] = 0;
+      }
+      for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+        int64_t a, z;
+        segid[q] = (unsigned char)seg_of(m0, u, q, a, z);
+      }
+      __syncthreads();
+      int shift = kKeyBits;
+      while (true) {
+        const int ns = max(0, shift - w);
+        const int ww = shift - ns;
+        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+          int s = segid[q];
+          if (s_done[s]) continue;
+          uint64_t k = skey(sc, sid, cap, c, cur[q]);
+          if ((k >> shift) != (s_pre[s] >> shift)) continue;
+          if (s_cnt[s] == 1) { s_res[s] = k; s_fnd[s] = 1; continue; }
+          atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << ww) - 1))], 1u);
+        }
+        __syncthreads();
+        // block exclusive scan of hist -> ex (2048 bins, 2 per thread)
+        {
+          int i2 = 2 * threadIdx.x;
+          uint32_t a0 = hist[i2], a1 = hist[i2 + 1];
+          uint32_t v = a0 + a1, inc = v;
+          for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+            if (lane >= o2) inc += y;
+          }
+          if (lane == 31) s_w[warp] = inc;
+          __syncthreads();
+          if (warp == 0) {
+            uint32_t x = lane < nwarps ? s_w[lane] : 0, xi = x;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
+              if (lane >= o2) xi += y;
+            }
+            if (lane < nwarps) s_w[lane] = xi - x;
+          }
+          __syncthreads();
+          uint32_t e = inc - v + s_w[warp];
+          ex[i2] = e;
+          ex[i2 + 1] = e + a0;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < kHistBins; j += blockDim.x) {
+          int s = j >> w;
+          if (s >= nseg || s_done[s] || s_cnt[s] == 1) continue;
+          uint32_t below = ex[j] - ex[s << w];
+          uint32_t cj = hist[j];
+          // record the bucket only: s_rank is read by the other bins of this
+          // segment in this same phase and is updated after the barrier
+          if (below < (uint32_t)s_rank[s] && (uint32_t)s_rank[s] <= below + cj) {
+            s_dig[s] = j & ((1 << w) - 1);
+            s_bel[s] = (int)below;
+            s_cnt2[s] = (int)cj;
+          }
+        }
+        __syncthreads();
+        int pending = 0;
+        for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+          if (s_done[s]) continue;
+          if (s_fnd[s]) { s_done[s] = 1; continue; }
+          s_pre[s] |= (uint64_t)s_dig[s] << ns;
+          s_rank[s] -= s_bel[s];
+          s_cnt[s] = s_cnt2[s];
+          if (ns == 0) { s_res[s] = s_pre[s]; s_done[s] = 1; continue; }
+          pending = 1;
+        }
+        shift = ns;
+        if (!__syncthreads_or(pending)) break;
+      }
+      // node keys
+      for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        int64_t bfs = (i0 << u) + s;
+        int64_t v = veb_slot(l, t, bfs);
+        o.key[v] = s_res[s];
+        o.child[v] = make_int2((int)veb_slot(l, t + 1, 2 * bfs), (int)veb_slot(l, t + 1, 2 * bfs + 1));
+      }
+      // stable partition by a block scan of the left flags (positions blocked per thread)
+      const int ipt = (cap + blockDim.x - 1) / blockDim.x;
+      const int q0 = threadIdx.x * ipt;
+      uint32_t flags = 0;
+      int cnt = 0;
+      for (int j = 0; j < ipt; ++j) {
+        int q = q0 + j;
+        if (q < m0) {
+          int s = segid[q];
+          bool left = skey(sc, sid, cap, c, cur[q]) <= s_res[s];
+          flags |= (uint32_t)left << j;
+          cnt += left;
+        }
+      }
+      uint32_t inc = cnt;
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+        if (lane >= o2) inc += y;
+      }
+      __syncthreads();
+      if (lane == 31) s_w[warp] = inc;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t x = lane < nwarps ? s_w[lane] : 0, xi = x;
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+          uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
+          if (lane >= o2) xi += y;
+        }
+        if (lane < nwarps) s_w[lane] = xi - x;
+      }
+      __syncthreads();
+      uint32_t e = inc - cnt + s_w[warp];
+      {
+        uint32_t run = e;
+        for (int j = 0; j < ipt; ++j) {
+          int q = q0 + j;
+          if (q < m0) {
+            int s = segid[q];
+            if (q == s_st[s]) s_lb[s] = (int)run;
+            run += (flags >> j) & 1;
+          }
+        }
+      }
+      __syncthreads();
+      {
+        uint32_t run = e;
+        for (int j = 0; j < ipt; ++j) {
+          int q = q0 + j;
+          if (q < m0) {
+            int s = segid[q];
+            int lrank = (int)run - s_lb[s];
+            int half = (s_sz[s] + 1) >> 1;
+            int rrank = (q - s_st[s]) - lrank;
+            bool left = (flags >> j) & 1;
+            int dst = left ? s_st[s] + lrank : s_st[s] + half + rrank;
+            if (left ? (lrank < 0 || lrank >= half) : (rrank < 0 || rrank >= s_sz[s] - half))
+              atomicOr(P.err, kErrPartition);
+            else
+              nxt[dst] = cur[q];
+            run += (flags >> j) & 1;
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---------------- warp mode: rank counting per segment --------------
+      for (int s = warp; s < nseg; s += nwarps) {
+        int64_t a64, z64;
+        seg_range(m0, u, s, a64, z64);
+        int a = (int)a64, z = (int)z64;
+        bool va = lane < z, vb = lane + 32 < z;
+        if (z > 64) { if (lane == 0) atomicOr(P.err, kErrPartition); continue; }
+        uint64_t ka = va ? skey(sc, sid, cap, c, cur[a + lane]) : ~0ull;
+        uint64_t kb = vb ? skey(sc, sid, cap, c, cur[a + 32 + lane]) : ~0ull;
+        int ra = 0, rb = 0;
+        int z1 = min(z, 32);
+        for (int y = 0; y < z1; ++y) {
+          uint64_t ky = __shfl_sync(0xffffffffu, ka, y);
+          ra += ky < ka;
+          rb += ky < kb;
+        }
+        for (int y = 32; y < z; ++y) {
+          uint64_t ky = __shfl_sync(0xffffffffu, kb, y - 32);
+          ra += ky < ka;
+          rb += ky < kb;
+        }
+        uint16_t pa = va ? cur[a + lane] : 0, pbv = vb ? cur[a + 32 + lane] : 0;
+        if (va) nxt[a + ra] = pa;
+        if (vb) nxt[a + rb] = pbv;
+        int mr = ((z + 1) >> 1) - 1;
+        int64_t bfs = (i0 << u) + s;
+        if ((va && ra == mr) || (vb && rb == mr)) {
+          int64_t v = veb_slot(l, t, bfs);
+          o.key[v] = (va && ra == mr) ? ka : kb;
+          o.child[v] = make_int2((int)veb_slot(l, t + 1, 2 * bfs), (int)veb_slot(l, t + 1, 2 * bfs + 1));
+        }
+      }
+      __syncthreads();
+    }
+    uint16_t *tmp = cur; cur = nxt; nxt = tmp;
+  }
+
+  // leaves: slot, leaf range, box, live count
+  const int nleaf = 1 << U;
+  const int64_t nleaves_tree = (int64_t)1 << T.h;
+  for (int lf = threadIdx.x; lf < nleaf; lf += blockDim.x) {
+    int64_t a64, z64;
+    seg_range(m0, U, lf, a64, z64);
+    int a = (int)a64, z = (int)z64;
+    int64_t leaf = (i0 << U) + lf;
+    int64_t v = veb_slot(l, T.h, leaf);
+    o.key[v] = 0;
+    o.child[v] = make_int2((int)(-1 - leaf), 0);
+    o.live[v] = z;
+    o.leaf_off[leaf] = (int32_t)(start0 + a);
+    if (leaf == nleaves_tree - 1) o.leaf_off[nleaves_tree] = (int32_t)T.s;
+    for (int cc = 0; cc < dim; ++cc) {
+      int32_t lo = INT32_MAX, hi = INT32_MIN;
+      for (int q = a; q < a + z; ++q) {
+        int32_t x = sc[cc * cap + cur[q]];
+        lo = min(lo, x);
+        hi = max(hi, x);
+      }
+      o.box[v * 2 * dim + cc] = lo;
+      o.box[v * 2 * dim + dim + cc] = hi;
+    }
+  }
+  // internal nodes of the subtree, bottom-up (children are in global memory)
+  for (int u = U - 1; u >= 0; --u) {
+    __syncthreads();
+    for (int s = threadIdx.x; s < (1 << u); s += blockDim.x) {
+      int64_t bfs = (i0 << u) + s;
+      int t = T.t0 + u;
+      int64_t v = veb_slot(l, t, bfs);
+      int64_t vl = veb_slot(l, t + 1, 2 * bfs), vr = veb_slot(l, t + 1, 2 * bfs + 1);
+      o.live[v] = o.live[vl] + o.live[vr];
+      for (int cc = 0; cc < dim; ++cc) {
+        o.box[v * 2 * dim + cc] = min(o.box[vl * 2 * dim + cc], o.box[vr * 2 * dim + cc]);
+        o.box[v * 2 * dim + dim + cc] =
+            max(o.box[vl * 2 * dim + dim + cc], o.box[vr * 2 * dim + dim + cc]);
+      }
+    }
+  }
+  // points in leaf order
+  for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+    int it = cur[q];
+    for (int cc = 0; cc < dim; ++cc) o.pts[cc * T.s + start0 + q] = sc[cc * cap + it];
+    o.ids[start0 + q] = sid[it];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: boxes and live counts of the global-level nodes, one depth per launch
+// ---------------------------------------------------------------------------
+
+struct BoxParams {
+  int ntrees, dim, t;
+  int64_t off[kMaxLevel + 1];
+  int32_t h[kMaxLevel];
+  int32_t slot[kMaxLevel];
+  NodeOut out[kMaxLevel];
+};
+
+__global__ void k_box_up(const BoxParams P) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.off[P.ntrees]) return;
+  int j = 0;
+  while (j + 1 < P.ntrees && P.off[j + 1] <= g) j++;
+  const NodeOut &o = P.out[P.slot[j]];
+  int l = P.h[j] + 1, t = P.t, dim = P.dim;
+  int64_t i = g - P.off[j];
+  int64_t v = veb_slot(l, t, i), vl = veb_slot(l, t + 1, 2 * i), vr = veb_slot(l, t + 1, 2 * i + 1);
+  o.live[v] = o.live[vl] + o.live[vr];
+  for (int c = 0; c < dim; ++c) {
+    o.box[v * 2 * dim + c] = min(o.box[vl * 2 * dim + c], o.box[vr * 2 * dim + c]);
+    o.box[v * 2 * dim + dim + c] = max(o.box[vl * 2 * dim + dim + c], o.box[vr * 2 * dim + dim + c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// buffer helpers
+// ---------------------------------------------------------------------------
+
+__global__ void k_pool_tail(const int32_t *buf, int64_t nbuf, const int32_t *arr, int64_t first,
+                            int64_t from, int64_t count, int32_t *dst) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) dst[k] = pool_id(buf, nbuf, arr, first, from + k);
+}
+
+// Single-CTA bitonic sort of n <= 16384 ids.
+__global__ void k_sort_small(int32_t *ids, int n, int np2) {
+  extern __shared__ int32_t a[];
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) a[i] = i < n ? ids[i] : INT32_MAX;
+  __syncthreads();
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        int p = i ^ j;
+        if (p > i) {
+          bool up = (i & k) == 0;
+          int32_t x = a[i], y = a[p];
+          if ((x > y) == up) { a[i] = y; a[p] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ids[i] = a[i];
+}
+
+constexpr size_t kSubtreeSmemMax = 212 * 1024;   // dynamic part; static part ~6 KB
+
+size_t subtree_smem_bytes(int dim, int cap) {
+  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + (size_t)cap;
+}
+
+NodeOut node_out(Tree *t) {
+  NodeOut o;
+  o.pts = t->pts;
+  o.ids = t->ids;
+  o.box = t->box;
+  o.live = t->live_nodes;
+  o.leaf_off = t->leaf_off;
+  o.key = t->key;
+  o.child = t->child;
+  return o;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct BuildLayout {
+  int cap, tile;
+  int64_t S;              // staging stride (multiple of 8)
+  int64_t nseg_max;       // segments of the widest global level
+  size_t stg_bytes, cand_bytes, hist_bytes, seg_bytes, cursor_bytes;
+};
+
+BuildLayout layout_of(const bdl_forest *f, std::vector<BuildTree> &bt) {
+  BuildLayout L;
+  L.cap = smem_subtree_capacity(f->dim);
+  L.tile = std::min(4096, L.cap);
+  int64_t S = 0;
+  int gmax = 0;
+  for (auto &b : bt) {
+    b.base = S;
+    S += (b.s + 7) / 8 * 8;
+    int g = 0;
+    while (g < b.h && ceil_div(b.s, (int64_t)1 << g) > L.cap) g++;
+    b.g = g;
+    gmax = std::max(gmax, g);
+  }
+  L.S = std::max<int64_t>(S, 8);
+  int64_t nmax = 0;
+  for (int it = 0; it < gmax; ++it) {
+    int64_t n = 0;
+    for (auto &b : bt)
+      if (b.g > it) n += (int64_t)1 << it;
+    nmax = std::max(nmax, n);
+  }
+  L.nseg_max = nmax;
+  L.stg_bytes = (size_t)(f->dim + 1) * L.S * 4;
+  L.cand_bytes = gmax ? (size_t)L.S * 8 : 0;
+  L.hist_bytes = (size_t)nmax * kHistBins * 4;
+  L.seg_bytes = (size_t)nmax * sizeof(SegState);
+  L.cursor_bytes = kMaxLevel * 8;
+  return L;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+int smem_subtree_capacity(int dim) {
+  for (int cap = 8192; cap >= 2048; cap >>= 1)
+    if (subtree_smem_bytes(dim, cap) <= kSubtreeSmemMax) return cap;
+  return 2048;
+}
+
+int build_scratch_bytes(const bdl_forest *f, const std::vector<BuildTree> &bt0, size_t *bytes) {
+  std::vector<BuildTree> bt = bt0;
+  BuildLayout L = layout_of(f, bt);
+  *bytes = 2 * align256(L.stg_bytes) + align256(L.cand_bytes) + align256(L.hist_bytes) +
+           align256(L.seg_bytes) + align256(L.cursor_bytes);
+  return BDL_OK;
+}
+
+int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<ClearedSrc> &cl,
+                const PoolSrc &pool, const std::vector<int64_t> &pool_lo,
+                const std::vector<int64_t> &from_cleared, cudaStream_t s) {
+  if (bt.empty()) return BDL_OK;
+  const int dim = f->dim;
+  BuildLayout L = layout_of(f, bt);
+  size_t total = 2 * align256(L.stg_bytes) + align256(L.cand_bytes) + align256(L.hist_bytes) +
+                 align256(L.seg_bytes) + align256(L.cursor_bytes);
+  void *block = nullptr;
+  int st = dev_alloc(f, &block, total, s);
+  if (st) return st;
+  unsigned char *p = (unsigned char *)block;
+  int32_t *stg[2];
+  stg[0] = (int32_t *)p; p += align256(L.stg_bytes);
+  stg[1] = (int32_t *)p; p += align256(L.stg_bytes);
+  uint64_t *cand = (uint64_t *)p; p += align256(L.cand_bytes);
+  uint32_t *hist = (uint32_t *)p; p += align256(L.hist_bytes);
+  SegState *seg = (SegState *)p; p += align256(L.seg_bytes);
+  unsigned long long *cursor = (unsigned long long *)p;
+
+  // ---- K5 gather ----
+  {
+    GatherParams G;
+    memset(&G, 0, sizeof(G));
+    G.nsrc = (int)cl.size();
+    G.ntrees = (int)bt.size();
+    G.dim = dim;
+    G.S = L.S;
+    G.stg = stg[0];
+    G.cursor = cursor;
+    G.err = f->err;
+    int64_t blk = 0;
+    const int TB = 256;
+    for (size_t i = 0; i < cl.size(); ++i) {
+      G.spts[i] = cl[i].pts;
+      G.sids[i] = cl[i].ids;
+      G.ssize[i] = cl[i].size;
+      G.sdst[i] = cl[i].dst;
+      G.sblk[i] = blk;
+      blk += ceil_div(cl[i].size, TB);
+    }
+    G.sblk[cl.size()] = blk;
+    for (size_t j = 0; j < bt.size(); ++j) {
+      G.base[j] = bt[j].base;
+      G.from_cleared[j] = from_cleared[j];
+      G.pool_lo[j] = pool_lo[j];
+    }
+    G.pool_lo[bt.size()] = pool_lo[bt.size()];
+    G.pbuf = pool.buf;
+    G.pnbuf = pool.nbuf;
+    G.parr = pool.arr;
+    G.pfirst = pool.first;
+    G.idtab = f->idtab;
+    if (cudaMemsetAsync(cursor, 0, L.cursor_bytes, s) != cudaSuccess) return cuda_check(cudaGetLastError(), "memset");
+    if (blk) {
+      k_gather_cleared<<<(unsigned)blk, TB, 0, s>>>(G);
+      BDL_LAUNCHED();
+    }
+    int64_t np = pool_lo[bt.size()];
+    if (np) {
+      k_gather_pool<<<(unsigned)ceil_div(np, 256), 256, 0, s>>>(G, np);
+      BDL_LAUNCHED();
+    }
+  }
+
+  std::vector<NodeOut> outs(bt.size());
+  for (size_t j = 0; j < bt.size(); ++j) outs[j] = node_out(bt[j].tree);
+
+  // ---- global levels ----
+  int gmax = 0;
+  for (auto &b : bt) gmax = std::max(gmax, b.g);
+  std::vector<int> sel(bt.size(), 0);
+  for (int it = 0; it < gmax; ++it) {
+    LvParams P;
+    memset(&P, 0, sizeof(P));
+    P.dim = dim;
+    P.tile = L.tile;
+    P.S = L.S;
+    P.src = stg[it & 1];
+    P.dst = stg[(it & 1) ^ 1];
+    P.hist = hist;
+    P.seg = seg;
+    P.cand = cand;
+    P.err = f->err;
+    int n = 0;
+    int64_t segs = 0, tiles = 0;
+    for (size_t j = 0; j < bt.size(); ++j) {
+      if (bt[j].g <= it) continue;
+      LvTree &T = P.tr[n];
+      T.base = bt[j].base;
+      T.s = bt[j].s;
+      T.t = it;
+      T.c = it % dim;
+      T.h = bt[j].h;
+      T.slot = n;
+      T.seg_off = segs;
+      T.tile_off = tiles;
+      P.out[n] = outs[j];
+      segs += (int64_t)1 << it;
+      tiles += ceil_div(bt[j].s, L.tile);
+      sel[j] = (it + 1) & 1;
+      n++;
+    }
+    P.ntrees = n;
+    if (cudaMemsetAsync(hist, 0, (size_t)segs * kHistBins * 4, s) != cudaSuccess)
+      return cuda_check(cudaGetLastError(), "memset hist");
+    k_level_hist<<<(unsigned)tiles, 512, 0, s>>>(P);
+    BDL_LAUNCHED();
+    k_level_bucket<<<(unsigned)ceil_div(segs, 8), 256, 0, s>>>(P, segs);
+    BDL_LAUNCHED();
+    k_level_collect<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P);
+    BDL_LAUNCHED();
+    k_level_select<<<(unsigned)segs, 256, 0, s>>>(P, segs);
+    BDL_LAUNCHED();
+    k_level_partition<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P);
+    BDL_LAUNCHED();
+  }
+
+  // ---- subtrees on chip ----
+  {
+    SubParams P;
+    memset(&P, 0, sizeof(P));
+    P.ntrees = (int)bt.size();
+    P.dim = dim;
+    P.cap = L.cap;
+    P.S = L.S;
+    P.stg[0] = stg[0];
+    P.stg[1] = stg[1];
+    P.err = f->err;
+    int64_t blocks = 0;
+    for (size_t j = 0; j < bt.size(); ++j) {
+      SubTree &T = P.tr[j];
+      T.base = bt[j].base;
+      T.s = bt[j].s;
+      T.h = bt[j].h;
+      T.t0 = bt[j].g;
+      T.sel = bt[j].g ? sel[j] : 0;
+      T.slot = (int)j;
+      T.blk_off = blocks;
+      P.out[j] = outs[j];
+      blocks += (int64_t)1 << bt[j].g;
+    }
+    size_t smem = subtree_smem_bytes(dim, L.cap);
+    cudaError_t e = cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSubtreeSmemMax);
+    if (e != cudaSuccess) {
+      dev_free(f, block, total, s);
+      return cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
+    }
+    k_subtree<<<(unsigned)blocks, kSubThreads, smem, s>>>(P);
+    BDL_LAUNCHED();
+  }
+
+  // ---- boxes of the global-level nodes ----
+  for (int t = gmax - 1; t >= 0; --t) {
+    BoxParams B;
+    memset(&B, 0, sizeof(B));
+    B.dim = dim;
+    B.t = t;
+    int n = 0;
+    int64_t off = 0;
+    for (size_t j = 0; j < bt.size(); ++j) {
+      if (bt[j].g <= t) continue;
+      B.off[n] = off;
+      B.h[n] = bt[j].h;
+      B.slot[n] = n;
+      B.out[n] = outs[j];
+      off += (int64_t)1 << t;
+      n++;
+    }
+    B.off[n] = off;
+    B.ntrees = n;
+    k_box_up<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(B);
+    BDL_LAUNCHED();
+  }
+  int err = cuda_check(cudaGetLastError(), "build kernels");
+  dev_free(f, block, total, s);
+  return err;
+}
+
+void launch_pool_tail(const PoolSrc &pool, int64_t from, int64_t count, int32_t *dst,
+                      cudaStream_t s) {
+  if (count <= 0) return;
+  k_pool_tail<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(pool.buf, pool.nbuf, pool.arr,
+                                                              pool.first, from, count, dst);
+  BDL_LAUNCHED();
+}
+
+void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s) {
+  if (n <= 1) return;
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
+  k_sort_small<<<1, 1024, (size_t)np2 * 4, s>>>(ids, (int)n, np2);
+  BDL_LAUNCHED();
+}
+
+}  // namespace bdl

@@ -1,0 +1,168 @@
+"""Pythonic wrapper over the C ABI: a Forest object taking torch tensors.
+
+Device tensors are passed straight through; host tensors are copied to the
+device on the forest's stream and results copied back (the end-to-end path).
+PyTorch only provides memory and streams here -- every step of the method
+runs in the CUDA library.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Forest:
+    """A batch-dynamic kd-tree forest resident on one GPU."""
+
+    def __init__(self, dim, points=None, leaf_size=16, buffer_size=1024, bloom_bits_per_key=16,
+                 hash_seed=0x5EED, hbm_budget_bytes=0, device=None, stream=None):
+        capi.load()
+        self.dim = dim
+        self.device = torch.device(device or "cuda")
+        self.stream = stream
+        cfg = capi.bdl_default_config()
+        cfg.leaf_size, cfg.buffer_size = leaf_size, buffer_size
+        cfg.bloom_bits_per_key, cfg.hash_seed = bloom_bits_per_key, hash_seed
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        self.cfg = cfg
+        with torch.cuda.device(self.device):
+            st, h = capi.bdl_create(dim, cfg, None, 0, None, _stream_handle(stream))
+        capi.check(st, "bdl_create")
+        self._h = h
+        if points is not None:
+            self.insert(points)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.bdl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self.stream if self.stream is not None else torch.cuda.current_stream(self.device)
+
+    def _dev(self, x, dtype):
+        """Device tensor of x; host data goes through pinned memory on the forest's stream."""
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x))
+        x = torch.as_tensor(x)
+        if x.is_cuda:
+            return x.to(dtype).contiguous()
+        x = x.to(dtype).contiguous()
+        if not x.is_pinned():
+            x = x.pin_memory()
+        with torch.cuda.stream(self._stream()):
+            return x.to(self.device, non_blocking=True)
+
+    def _host(self, t):
+        self._stream().synchronize()
+        return t.cpu()
+
+    def insert(self, points):
+        """Insert_L: returns the new ids (device tensor if points were on the device)."""
+        on_host = not (isinstance(points, torch.Tensor) and points.is_cuda)
+        p = self._dev(points, torch.int32).reshape(-1, self.dim)
+        ids = torch.empty(p.shape[0], dtype=torch.int32, device=self.device)
+        capi.check(capi.bdl_insert(self._h, _ptr(p), p.shape[0], _ptr(ids),
+                                   _stream_handle(self.stream)), "bdl_insert")
+        return self._host(ids) if on_host else ids
+
+    def erase(self, ids):
+        """Erase_L: returns the number of points erased."""
+        i = self._dev(ids, torch.int32).reshape(-1)
+        st, n = capi.bdl_erase(self._h, _ptr(i), i.shape[0], _stream_handle(self.stream))
+        capi.check(st, "bdl_erase")
+        return n
+
+    def knn(self, queries, k, out=None):
+        """kNN_L: (ids [m,k] int32, d2 [m,k] int64), sorted by (d2, id)."""
+        on_host = not (isinstance(queries, torch.Tensor) and queries.is_cuda)
+        q = self._dev(queries, torch.int32).reshape(-1, self.dim)
+        m = q.shape[0]
+        if out is None:
+            oi = torch.empty((m, k), dtype=torch.int32, device=self.device)
+            od = torch.empty((m, k), dtype=torch.int64, device=self.device)
+        else:
+            oi, od = out
+        capi.check(capi.bdl_knn(self._h, _ptr(q), m, k, _ptr(oi), _ptr(od),
+                                _stream_handle(self.stream)), "bdl_knn")
+        if on_host:
+            return self._host(oi), self._host(od)
+        return oi, od
+
+    def size(self):
+        st, n = capi.bdl_size(self._h)
+        capi.check(st, "bdl_size")
+        return n
+
+    def tree_mask(self):
+        st, m, nb = capi.bdl_tree_mask(self._h)
+        capi.check(st, "bdl_tree_mask")
+        return m
+
+    def tree_levels(self):
+        m = self.tree_mask()
+        return [i for i in range(64) if (m >> i) & 1]
+
+    def buffer_ids(self):
+        out = np.empty(self.cfg.buffer_size, dtype=np.int32)
+        st, n = capi.bdl_buffer_ids(self._h, out.ctypes.data_as(ctypes.c_void_p), len(out),
+                                    _stream_handle(self.stream))
+        capi.check(st, "bdl_buffer_ids")
+        return out[:n].copy()
+
+    def tree(self, level):
+        """Tree `level` as numpy arrays, in the layout the oracle exports."""
+        info = np.zeros(6, dtype=np.int64)
+        if capi.bdl_tree_info(self._h, level, info.ctypes.data_as(ctypes.c_void_p)) != 0:
+            return None
+        size, live, h, nn, blocks = (int(x) for x in info[:5])
+        d = self.dim
+        key = np.empty(nn, np.int64)
+        child = np.empty(2 * nn, np.int32)
+        box = np.empty(nn * 2 * d, np.int32)
+        nlive = np.empty(nn, np.int32)
+        leaf_off = np.empty((1 << h) + 1, np.int32)
+        ids = np.empty(size, np.int32)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        capi.check(capi.bdl_tree_export(self._h, level, P(key), P(child), P(box), P(nlive),
+                                        P(leaf_off), P(ids), _stream_handle(self.stream)),
+                   "bdl_tree_export")
+        bloom = None
+        if blocks:
+            bloom = np.empty(blocks * 8, np.uint32)
+            capi.check(capi.bdl_bloom_export(self._h, level, P(bloom), _stream_handle(self.stream)),
+                       "bdl_bloom_export")
+        dead = ids < 0
+        real = np.where(dead, ids & 0x7FFFFFFF, ids).astype(np.int32)
+        return dict(size=size, live=live, h=h, nnodes=nn, key=key, child=child.reshape(nn, 2),
+                    box=box.reshape(nn, 2 * d), node_live=nlive, leaf_off=leaf_off,
+                    ids=real, dead=dead, bloom=bloom)
+
+    def knn_stats(self, enable=None):
+        """enable=True/False switches per-query visit counting on/off (and resets);
+        enable=None reads (nodes visited, leaf points examined, queries)."""
+        if enable is None:
+            out = np.zeros(3, np.int64)
+            capi.check(capi.bdl_knn_stats(self._h, 0, out.ctypes.data_as(ctypes.c_void_p)),
+                       "bdl_knn_stats")
+            return tuple(int(x) for x in out)
+        capi.check(capi.bdl_knn_stats(self._h, 1 if enable else 0, None), "bdl_knn_stats")
+        return None

@@ -8,3 +8,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the CUDA library")
+
+# the library's in-kernel bounds checks report through a device error word;
+# the tests make every call wait and check it
+os.environ.setdefault("BDL_DEBUG_CHECK", "1")
