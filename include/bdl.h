@@ -93,8 +93,10 @@ int bdl_insert(bdl_forest *f, const int32_t *pts_dev, int64_t n, int32_t *out_id
 int bdl_erase(bdl_forest *f, const int32_t *ids_dev, int64_t n, int64_t *out_n_erased_host,
               bdl_stream_t stream);
 
-/* kNN_L (Alg. 5): for each of the m queries q_dev[m][dim] (any int32
- * coordinates) the k nearest live points, 1 <= k <= 32.  Row i of
+/* kNN_L (Alg. 5): for each of the m queries q_dev[m][dim] the k nearest
+ * live points, 1 <= k <= 32.  Query coordinates must lie on the grid
+ * [0, 2^20) like the points (the query path does no device-to-host check;
+ * rows of other queries are unspecified).  Row i of
  * out_ids_dev[m][k] / out_d2_dev[m][k] lists them by increasing (squared
  * distance, id); when fewer than k points are live the row is padded with
  * id -1 and d2 INT64_MAX.  A query equal to a live point returns it at d2 0.
@@ -157,6 +159,19 @@ int bdl_knn_stats(bdl_forest *f, int enable, int64_t *out_host);
 
 /* Number of kernels this library has launched in the process. */
 uint64_t bdl_launch_count(void);
+
+/* Live per-kernel timing for measurement runs: while enabled, every kernel
+ * launch is bracketed by CUDA events on its own stream.  bdl_profile(1/0)
+ * switches it on/off and clears the records; bdl_profile_read waits for the
+ * recorded events and fills, per kernel id < cap, the summed device time in
+ * ms and the launch count since the last call, then clears the records. */
+int bdl_profile(int enable);
+int bdl_profile_read(double *ms_host, int64_t *launches_host, int cap);
+
+/* Kernel ids are 0 .. bdl_kernel_count()-1; bdl_kernel_name gives each one's
+ * name (e.g. "k_knn"). */
+int bdl_kernel_count(void);
+const char *bdl_kernel_name(int id);
 
 #ifdef __cplusplus
 }

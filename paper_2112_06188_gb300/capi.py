@@ -17,6 +17,7 @@ SYMBOLS = [
     "bdl_default_config", "bdl_create", "bdl_insert", "bdl_erase", "bdl_knn", "bdl_size",
     "bdl_destroy", "bdl_status_string", "bdl_last_error", "bdl_tree_mask", "bdl_buffer_ids",
     "bdl_tree_info", "bdl_tree_export", "bdl_bloom_export", "bdl_knn_stats", "bdl_launch_count",
+    "bdl_profile", "bdl_profile_read", "bdl_kernel_count", "bdl_kernel_name",
 ]
 
 
@@ -62,6 +63,10 @@ def load(path=None):
         "bdl_bloom_export": (i32, [P, i32, P, P]),
         "bdl_knn_stats": (i32, [P, i32, P]),
         "bdl_launch_count": (u64, []),
+        "bdl_profile": (i32, [i32]),
+        "bdl_profile_read": (i32, [P, P, i32]),
+        "bdl_kernel_count": (i32, []),
+        "bdl_kernel_name": (ctypes.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -161,3 +166,24 @@ def bdl_knn_stats(f, enable, out_host_ptr):
 
 def bdl_launch_count():
     return int(load().bdl_launch_count())
+
+
+def bdl_profile(enable):
+    return load().bdl_profile(1 if enable else 0)
+
+
+def bdl_profile_read():
+    """{kernel name: (total ms, launches)} since the last read (waits for the events)."""
+    n = load().bdl_kernel_count()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    check(load().bdl_profile_read(ms, cnt, n), "bdl_profile_read")
+    return {bdl_kernel_name(i): (ms[i], cnt[i]) for i in range(n) if cnt[i]}
+
+
+def bdl_kernel_count():
+    return int(load().bdl_kernel_count())
+
+
+def bdl_kernel_name(i):
+    return load().bdl_kernel_name(i).decode()

@@ -24,6 +24,44 @@ constexpr int kHistShift = kCoordBits - 11;
 
 extern std::atomic<uint64_t> g_launches;
 
+// Every kernel launch of the library goes through a KScope: it counts the
+// launch and, while profiling is on, brackets it with CUDA events on the
+// launching stream so per-kernel device times can be read back.
+enum KernelId : int {
+  kK_gather_cleared,
+  kK_gather_pool,
+  kK_level_hist,
+  kK_level_bucket,
+  kK_level_collect,
+  kK_level_select,
+  kK_level_partition,
+  kK_subtree,
+  kK_box_up,
+  kK_pool_tail,
+  kK_sort_small,
+  kK_append_validate,
+  kK_set_alive,
+  kK_iota,
+  kK_erase_mark,
+  kK_bloom_build,
+  kK_erase_locate,
+  kK_buffer_compact,
+  kK_gather_roots,
+  kK_mark_ids,
+  kK_popc_blocks,
+  kK_scan_bsum,
+  kK_emit_ids,
+  kK_knn,
+  kKernelCount
+};
+extern const char *const kKernelNames[kKernelCount];
+struct KScope {
+  KScope(int kid, cudaStream_t s);
+  ~KScope();
+  int rec;
+  cudaStream_t s;
+};
+
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
@@ -277,4 +315,3 @@ int launch_knn(const ForestView &fv, const int32_t *q, int64_t m, int k, int32_t
 
 }  // namespace bdl
 
-#define BDL_LAUNCHED() (::bdl::g_launches.fetch_add(1, std::memory_order_relaxed))

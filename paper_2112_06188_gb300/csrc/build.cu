@@ -941,13 +941,13 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
     G.idtab = f->idtab;
     if (cudaMemsetAsync(cursor, 0, L.cursor_bytes, s) != cudaSuccess) return cuda_check(cudaGetLastError(), "memset");
     if (blk) {
-      k_gather_cleared<<<(unsigned)blk, TB, 0, s>>>(G);
-      BDL_LAUNCHED();
+      { KScope ks_(kK_gather_cleared, s);
+      k_gather_cleared<<<(unsigned)blk, TB, 0, s>>>(G); }
     }
     int64_t np = pool_lo[bt.size()];
     if (np) {
-      k_gather_pool<<<(unsigned)ceil_div(np, 256), 256, 0, s>>>(G, np);
-      BDL_LAUNCHED();
+      { KScope ks_(kK_gather_pool, s);
+      k_gather_pool<<<(unsigned)ceil_div(np, 256), 256, 0, s>>>(G, np); }
     }
   }
 
@@ -992,16 +992,16 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
     P.ntrees = n;
     if (cudaMemsetAsync(hist, 0, (size_t)segs * kHistBins * 4, s) != cudaSuccess)
       return cuda_check(cudaGetLastError(), "memset hist");
-    k_level_hist<<<(unsigned)tiles, 512, 0, s>>>(P);
-    BDL_LAUNCHED();
-    k_level_bucket<<<(unsigned)ceil_div(segs, 8), 256, 0, s>>>(P, segs);
-    BDL_LAUNCHED();
-    k_level_collect<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P);
-    BDL_LAUNCHED();
-    k_level_select<<<(unsigned)segs, 256, 0, s>>>(P, segs);
-    BDL_LAUNCHED();
-    k_level_partition<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P);
-    BDL_LAUNCHED();
+    { KScope ks_(kK_level_hist, s);
+    k_level_hist<<<(unsigned)tiles, 512, 0, s>>>(P); }
+    { KScope ks_(kK_level_bucket, s);
+    k_level_bucket<<<(unsigned)ceil_div(segs, 8), 256, 0, s>>>(P, segs); }
+    { KScope ks_(kK_level_collect, s);
+    k_level_collect<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P); }
+    { KScope ks_(kK_level_select, s);
+    k_level_select<<<(unsigned)segs, 256, 0, s>>>(P, segs); }
+    { KScope ks_(kK_level_partition, s);
+    k_level_partition<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P); }
   }
 
   // ---- subtrees on chip ----
@@ -1035,8 +1035,8 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
       dev_free(f, block, total, s);
       return cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
     }
-    k_subtree<<<(unsigned)blocks, kSubThreads, smem, s>>>(P);
-    BDL_LAUNCHED();
+    { KScope ks_(kK_subtree, s);
+    k_subtree<<<(unsigned)blocks, kSubThreads, smem, s>>>(P); }
   }
 
   // ---- boxes of the global-level nodes ----
@@ -1058,8 +1058,8 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
     }
     B.off[n] = off;
     B.ntrees = n;
-    k_box_up<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(B);
-    BDL_LAUNCHED();
+    { KScope ks_(kK_box_up, s);
+    k_box_up<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(B); }
   }
   int err = cuda_check(cudaGetLastError(), "build kernels");
   dev_free(f, block, total, s);
@@ -1069,9 +1069,9 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
 void launch_pool_tail(const PoolSrc &pool, int64_t from, int64_t count, int32_t *dst,
                       cudaStream_t s) {
   if (count <= 0) return;
+  { KScope ks_(kK_pool_tail, s);
   k_pool_tail<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(pool.buf, pool.nbuf, pool.arr,
-                                                              pool.first, from, count, dst);
-  BDL_LAUNCHED();
+                                                              pool.first, from, count, dst); }
 }
 
 void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s) {
@@ -1079,8 +1079,8 @@ void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s) {
   int np2 = 1;
   while (np2 < n) np2 <<= 1;
   cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
-  k_sort_small<<<1, 1024, (size_t)np2 * 4, s>>>(ids, (int)n, np2);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_sort_small, s);
+  k_sort_small<<<1, 1024, (size_t)np2 * 4, s>>>(ids, (int)n, np2); }
 }
 
 }  // namespace bdl

@@ -275,54 +275,54 @@ void launch_append_validate(const int32_t *pts, int64_t n, int dim, int32_t *idt
                             int64_t *flag, cudaStream_t s) {
   int64_t tot = n * dim;
   if (tot <= 0) return;
-  k_append_validate<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(pts, tot, idtab_dst, flag);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_append_validate, s);
+  k_append_validate<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(pts, tot, idtab_dst, flag); }
 }
 
 void launch_set_alive(uint32_t *alive, int64_t first, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int64_t words = ((first + n - 1) >> 5) - (first >> 5) + 1;
-  k_set_alive<<<(unsigned)cdiv(words, 256), 256, 0, s>>>(alive, first, n);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_set_alive, s);
+  k_set_alive<<<(unsigned)cdiv(words, 256), 256, 0, s>>>(alive, first, n); }
 }
 
 void launch_iota(int32_t *out, int64_t first, int64_t n, cudaStream_t s) {
   if (n <= 0 || !out) return;
-  k_iota<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, first, n);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_iota, s);
+  k_iota<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, first, n); }
 }
 
 void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
                        int32_t *list, int64_t *count, cudaStream_t s) {
   if (n <= 0) return;
-  k_erase_mark<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(alive, next_id, ids, n, list, count);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_erase_mark, s);
+  k_erase_mark<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(alive, next_id, ids, n, list, count); }
 }
 
 void launch_bloom_build(const Tree *t, uint64_t seed, cudaStream_t s) {
   if (t->size <= 0) return;
+  { KScope ks_(kK_bloom_build, s);
   k_bloom_build<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->ids, t->size, t->bloom,
-                                                              t->bloom_blocks, seed);
-  BDL_LAUNCHED();
+                                                              t->bloom_blocks, seed); }
 }
 
 void launch_erase_locate(const ForestView &fv, uint64_t seed, const int32_t *list, int64_t n,
                          cudaStream_t s) {
   if (n <= 0 || fv.ntrees == 0) return;
-  k_erase_locate<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(fv, seed, list, n);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_erase_locate, s);
+  k_erase_locate<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(fv, seed, list, n); }
 }
 
 void launch_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n,
                            cudaStream_t s) {
-  k_buffer_compact<<<1, 1024, 0, s>>>(buf, nbuf, alive, out_n);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_buffer_compact, s);
+  k_buffer_compact<<<1, 1024, 0, s>>>(buf, nbuf, alive, out_n); }
 }
 
 void launch_gather_roots(const ForestView &fv, int64_t *out, cudaStream_t s) {
   if (fv.ntrees == 0) return;
-  k_gather_roots<<<1, 64, 0, s>>>(fv, out);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_gather_roots, s);
+  k_gather_roots<<<1, 64, 0, s>>>(fv, out); }
 }
 
 int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n, int32_t *out,
@@ -339,15 +339,15 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
   int64_t *bsum = (int64_t *)((char *)blk + ((size_t)nwords * 4 + 255) / 256 * 256);
   cudaMemsetAsync(bm, 0, (size_t)nwords * 4, s);
   for (Tree *t : from) {
-    k_mark_ids<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->ids, t->size, bm);
-    BDL_LAUNCHED();
+    { KScope ks_(kK_mark_ids, s);
+    k_mark_ids<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->ids, t->size, bm); }
   }
-  k_popc_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum);
-  BDL_LAUNCHED();
-  k_scan_bsum<<<1, 1024, 0, s>>>(bsum, nb);
-  BDL_LAUNCHED();
-  k_emit_ids<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum, out, n, f->err);
-  BDL_LAUNCHED();
+  { KScope ks_(kK_popc_blocks, s);
+  k_popc_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum); }
+  { KScope ks_(kK_scan_bsum, s);
+  k_scan_bsum<<<1, 1024, 0, s>>>(bsum, nb); }
+  { KScope ks_(kK_emit_ids, s);
+  k_emit_ids<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum, out, n, f->err); }
   int err = cuda_check(cudaGetLastError(), "collect_sorted_live");
   dev_free(f, blk, bytes, s);
   return err;

@@ -23,6 +23,78 @@ namespace bdl {
 std::atomic<uint64_t> g_launches{0};
 static thread_local std::string g_err;
 
+const char *const kKernelNames[kKernelCount] = {
+    "k_gather_cleared",
+    "k_gather_pool",
+    "k_level_hist",
+    "k_level_bucket",
+    "k_level_collect",
+    "k_level_select",
+    "k_level_partition",
+    "k_subtree",
+    "k_box_up",
+    "k_pool_tail",
+    "k_sort_small",
+    "k_append_validate",
+    "k_set_alive",
+    "k_iota",
+    "k_erase_mark",
+    "k_bloom_build",
+    "k_erase_locate",
+    "k_buffer_compact",
+    "k_gather_roots",
+    "k_mark_ids",
+    "k_popc_blocks",
+    "k_scan_bsum",
+    "k_emit_ids",
+    "k_knn",
+};
+
+// ---- live per-kernel timing (CUDA events on the launching stream) ----
+struct ProfRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_ev_free;
+
+static cudaEvent_t take_event() {
+  if (!g_ev_free.empty()) {
+    cudaEvent_t e = g_ev_free.back();
+    g_ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+KScope::KScope(int kid, cudaStream_t st) : rec(-1), s(st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r{kid, take_event(), take_event()};
+  cudaEventRecord(r.a, s);
+  g_prof.push_back(r);
+  rec = (int)g_prof.size() - 1;
+}
+
+KScope::~KScope() {
+  if (rec < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (rec < (int)g_prof.size()) cudaEventRecord(g_prof[rec].b, s);
+}
+
+static void prof_reset() {
+  for (auto &r : g_prof) {
+    g_ev_free.push_back(r.a);
+    g_ev_free.push_back(r.b);
+  }
+  g_prof.clear();
+}
+
 int set_error(int status, const std::string &msg) {
   g_err = msg;
   return status;
@@ -324,6 +396,38 @@ const char *bdl_status_string(int st) {
 const char *bdl_last_error(void) { return g_err.c_str(); }
 
 uint64_t bdl_launch_count(void) { return g_launches.load(); }
+
+int bdl_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_reset();
+  g_prof_on = enable != 0;
+  return BDL_OK;
+}
+
+int bdl_profile_read(double *ms, int64_t *launches, int cap) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int i = 0; i < cap && i < kKernelCount; ++i) {
+    if (ms) ms[i] = 0;
+    if (launches) launches[i] = 0;
+  }
+  for (auto &r : g_prof) {
+    int st = cuda_check(cudaEventSynchronize(r.b), "cudaEventSynchronize");
+    if (st) return st;
+    float t = 0;
+    st = cuda_check(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+    if (st) return st;
+    if (r.kid < cap) {
+      if (ms) ms[r.kid] += t;
+      if (launches) launches[r.kid] += 1;
+    }
+  }
+  prof_reset();
+  return BDL_OK;
+}
+
+int bdl_kernel_count(void) { return kKernelCount; }
+
+const char *bdl_kernel_name(int id) { return id >= 0 && id < kKernelCount ? kKernelNames[id] : ""; }
 
 int bdl_insert(bdl_forest *f, const int32_t *pts, int64_t n, int32_t *out_ids, bdl_stream_t stream) {
   if (!f) return set_error(BDL_EINVAL, "forest is NULL");

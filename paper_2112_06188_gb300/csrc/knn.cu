@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(128) k_knn(const ForestView F, const int32_t *
 template <int D, int KMAX>
 void launch_dk(const ForestView &fv, const int32_t *q, int64_t m, int k, int32_t *oi, int64_t *od,
                unsigned long long *stats, cudaStream_t s) {
-  k_knn<D, KMAX><<<(unsigned)((m + 127) / 128), 128, 0, s>>>(fv, q, m, k, oi, od, stats);
+  { KScope ks_(kK_knn, s);
+  k_knn<D, KMAX><<<(unsigned)((m + 127) / 128), 128, 0, s>>>(fv, q, m, k, oi, od, stats); }
 }
 
 template <int D>
@@ -194,7 +195,6 @@ int launch_knn(const ForestView &fv, const int32_t *q, int64_t m, int k, int32_t
     case 7: launch_d<7>(fv, q, m, k, out_ids, out_d2, stats, s); break;
     default: launch_d<0>(fv, q, m, k, out_ids, out_d2, stats, s); break;
   }
-  BDL_LAUNCHED();
   return cuda_check(cudaGetLastError(), "knn kernel");
 }
 
