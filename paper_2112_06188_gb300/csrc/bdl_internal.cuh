@@ -52,6 +52,8 @@ enum KernelId : int {
   kK_scan_bsum,
   kK_emit_ids,
   kK_knn,
+  kK_pack_nodes,
+  kK_qsort,
   kKernelCount
 };
 extern const char *const kKernelNames[kKernelCount];
@@ -171,15 +173,23 @@ __device__ inline uint32_t bloom_word_bit(uint64_t bits, int w) {
 // device views
 // ---------------------------------------------------------------------------
 
+// Ints of one point record in a tree: dim coordinates, the id, padding to a
+// multiple of 16 bytes (so a 3-D point is one int4: x, y, z, id).
+__host__ __device__ constexpr int rec_ints(int dim) { return (dim + 1 + 3) / 4 * 4; }
+
+// Ints of one packed k-NN node record: left/right child codes, their live
+// counts and their boxes (lo[dim], hi[dim] each), padded to 32 bytes.
+__host__ __device__ constexpr int packed_node_ints(int dim) { return (4 + 4 * dim + 7) / 8 * 8; }
+
 struct TreeView {          // one static tree, device pointers
-  const int32_t *pts;      // SoA [dim][size]
-  int32_t *ids;            // [size]; erased: id | kTomb
+  int32_t *pts;            // [size][rec_ints(dim)]: coordinates, id (erased: id | kTomb)
   const uint64_t *key;     // [nnodes]
   const int2 *child;       // [nnodes]
   const int32_t *box;      // [nnodes][2*dim]
   int32_t *live;           // [nnodes]
   const int32_t *leaf_off; // [2^h + 1]
   const uint32_t *bloom;   // [blocks * 8] or nullptr
+  const int32_t *pk;       // packed internal nodes for k-NN, vEB order of the h internal levels
   int64_t size;
   int64_t nnodes;
   int64_t bloom_blocks;
@@ -218,10 +228,11 @@ struct Tree {
   int64_t nnodes = 0, nleaves = 0;
   void *block = nullptr;   // one pool allocation holding the arrays below
   size_t bytes = 0;
-  int32_t *pts = nullptr, *ids = nullptr, *box = nullptr, *live_nodes = nullptr,
-          *leaf_off = nullptr;
+  int32_t *pts = nullptr;      // [size][rec_ints(dim)] in leaf order
+  int32_t *box = nullptr, *live_nodes = nullptr, *leaf_off = nullptr;
   uint64_t *key = nullptr;
   int2 *child = nullptr;
+  int32_t *pk = nullptr;       // packed internal nodes (k-NN), (2^h - 1) records
   uint32_t *bloom = nullptr;   // separate allocation, built lazily
   int64_t bloom_blocks = 0;
   size_t bloom_bytes = 0;
@@ -280,8 +291,7 @@ struct PoolSrc {
   int64_t first;           // first id of the range
 };
 struct ClearedSrc {        // a cleared tree whose live points join a new tree
-  const int32_t *pts;
-  const int32_t *ids;
+  const int32_t *pts;      // point records
   int64_t size;
   int32_t dst;             // index into the BuildTree list
 };
@@ -300,7 +310,7 @@ void launch_set_alive(uint32_t *alive, int64_t first, int64_t n, cudaStream_t s)
 void launch_iota(int32_t *out, int64_t first, int64_t n, cudaStream_t s);
 void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
                        int32_t *list, int64_t *count, cudaStream_t s);
-void launch_bloom_build(const Tree *t, uint64_t seed, cudaStream_t s);
+void launch_bloom_build(const Tree *t, int dim, uint64_t seed, cudaStream_t s);
 void launch_erase_locate(const ForestView &fv, uint64_t seed, const int32_t *list, int64_t n,
                          cudaStream_t s);
 void launch_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n,
@@ -310,8 +320,14 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
                         int32_t *out, cudaStream_t s);
 
 // ---- knn.cu ----
-int launch_knn(const ForestView &fv, const int32_t *q, int64_t m, int k, int32_t *out_ids,
-               int64_t *out_d2, unsigned long long *stats, cudaStream_t s);
+int launch_knn(const ForestView &fv, const int32_t *q, const int32_t *perm, int64_t m, int k,
+               int32_t *out_ids, int64_t *out_d2, unsigned long long *stats, cudaStream_t s);
+void launch_pack_nodes(const Tree *t, int dim, cudaStream_t s);
+// Spatial order of the queries (counting sort on a Morton prefix of their
+// coordinates): perm[m] gets query indices; scratch of query_sort_bytes().
+size_t query_sort_bytes(int64_t m, int dim);
+void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,
+                       cudaStream_t s);
 
 }  // namespace bdl
 

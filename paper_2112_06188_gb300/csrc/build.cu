@@ -43,7 +43,7 @@ struct SegState {
 };
 
 struct NodeOut {               // where a tree's arrays go
-  int32_t *pts, *ids, *box, *live, *leaf_off;
+  int32_t *pts, *box, *live, *leaf_off;
   uint64_t *key;
   int2 *child;
 };
@@ -89,8 +89,7 @@ struct GatherParams {
   unsigned long long *cursor;         // per new tree: records placed from cleared trees
   unsigned long long *err;
   // cleared sources
-  const int32_t *spts[kMaxLevel];
-  const int32_t *sids[kMaxLevel];
+  const int32_t *spts[kMaxLevel];     // point records of the cleared trees
   int64_t ssize[kMaxLevel];
   int64_t sblk[kMaxLevel + 1];        // block prefix
   int32_t sdst[kMaxLevel];
@@ -120,7 +119,8 @@ __global__ void k_gather_cleared(const GatherParams P) {
   while (src + 1 < P.nsrc && P.sblk[src + 1] <= b) src++;
   int64_t p = (int64_t)(b - P.sblk[src]) * blockDim.x + threadIdx.x;
   bool ok = p < P.ssize[src];
-  int32_t id = ok ? P.sids[src][p] : -1;
+  const int rs = rec_ints(P.dim);
+  int32_t id = ok ? P.spts[src][p * rs + P.dim] : -1;
   bool live = ok && id >= 0;
   // block-exclusive count of live records
   unsigned bal = __ballot_sync(0xffffffffu, live);
@@ -142,7 +142,7 @@ __global__ void k_gather_cleared(const GatherParams P) {
     return;
   }
   int64_t dst = P.base[j] + rel;
-  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = P.spts[src][c * P.ssize[src] + p];
+  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = P.spts[src][p * rs + c];
   P.stg[P.dim * P.S + dst] = id;
 }
 
@@ -743,11 +743,14 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       }
     }
   }
-  // points in leaf order
+  // point records in leaf order
+  const int rs = rec_ints(dim);
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
     int it = cur[q];
-    for (int cc = 0; cc < dim; ++cc) o.pts[cc * T.s + start0 + q] = sc[cc * cap + it];
-    o.ids[start0 + q] = sid[it];
+    int32_t *dst = o.pts + (start0 + q) * rs;
+    for (int cc = 0; cc < dim; ++cc) dst[cc] = sc[cc * cap + it];
+    dst[dim] = sid[it];
+    for (int cc = dim + 1; cc < rs; ++cc) dst[cc] = 0;
   }
 }
 
@@ -819,7 +822,6 @@ size_t subtree_smem_bytes(int dim, int cap) {
 NodeOut node_out(Tree *t) {
   NodeOut o;
   o.pts = t->pts;
-  o.ids = t->ids;
   o.box = t->box;
   o.live = t->live_nodes;
   o.leaf_off = t->leaf_off;
@@ -921,7 +923,6 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
     const int TB = 256;
     for (size_t i = 0; i < cl.size(); ++i) {
       G.spts[i] = cl[i].pts;
-      G.sids[i] = cl[i].ids;
       G.ssize[i] = cl[i].size;
       G.sdst[i] = cl[i].dst;
       G.sblk[i] = blk;
@@ -1061,6 +1062,7 @@ int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<Cle
     { KScope ks_(kK_box_up, s);
     k_box_up<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(B); }
   }
+  for (auto &b : bt) launch_pack_nodes(b.tree, dim, s);
   int err = cuda_check(cudaGetLastError(), "build kernels");
   dev_free(f, block, total, s);
   return err;

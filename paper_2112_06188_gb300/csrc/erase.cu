@@ -66,11 +66,11 @@ __global__ void k_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *id
 }
 
 // K6a: split-block bloom filter over the live ids of one tree.
-__global__ void k_bloom_build(const int32_t *ids, int64_t size, uint32_t *bloom, int64_t blocks,
-                              uint64_t seed) {
+__global__ void k_bloom_build(const int32_t *pts, int64_t size, int dim, uint32_t *bloom,
+                              int64_t blocks, uint64_t seed) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= size) return;
-  int32_t id = ids[j];
+  int32_t id = pts[j * rec_ints(dim) + dim];
   if (id < 0) return;
   int64_t blk;
   uint64_t bits;
@@ -126,9 +126,11 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
         } else {
           atomicOr(F.err, kErrChild);
         }
+        const int rs = rec_ints(F.dim);
         for (int j = a; j < z; ++j) {
-          if (T.ids[j] == id) {
-            T.ids[j] = (int32_t)((uint32_t)id | kTomb);
+          int32_t *slot = T.pts + (int64_t)j * rs + F.dim;
+          if (*slot == id) {
+            *slot = (int32_t)((uint32_t)id | kTomb);
             found = true;
             break;
           }
@@ -183,10 +185,10 @@ __global__ void k_gather_roots(const ForestView F, int64_t *out) {
 
 // Ordered gather: mark the live ids of the given trees in a bitmap, then emit
 // them in increasing order through a prefix sum of per-word popcounts.
-__global__ void k_mark_ids(const int32_t *ids, int64_t size, uint32_t *bm) {
+__global__ void k_mark_ids(const int32_t *pts, int64_t size, int dim, uint32_t *bm) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= size) return;
-  int32_t id = ids[j];
+  int32_t id = pts[j * rec_ints(dim) + dim];
   if (id >= 0) atomicOr(&bm[id >> 5], 1u << (id & 31));
 }
 
@@ -299,10 +301,10 @@ void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int
   k_erase_mark<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(alive, next_id, ids, n, list, count); }
 }
 
-void launch_bloom_build(const Tree *t, uint64_t seed, cudaStream_t s) {
+void launch_bloom_build(const Tree *t, int f_dim, uint64_t seed, cudaStream_t s) {
   if (t->size <= 0) return;
   { KScope ks_(kK_bloom_build, s);
-  k_bloom_build<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->ids, t->size, t->bloom,
+  k_bloom_build<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->pts, t->size, f_dim, t->bloom,
                                                               t->bloom_blocks, seed); }
 }
 
@@ -340,7 +342,7 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
   cudaMemsetAsync(bm, 0, (size_t)nwords * 4, s);
   for (Tree *t : from) {
     { KScope ks_(kK_mark_ids, s);
-    k_mark_ids<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->ids, t->size, bm); }
+    k_mark_ids<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->pts, t->size, f->dim, bm); }
   }
   { KScope ks_(kK_popc_blocks, s);
   k_popc_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum); }

@@ -48,6 +48,8 @@ const char *const kKernelNames[kKernelCount] = {
     "k_scan_bsum",
     "k_emit_ids",
     "k_knn",
+    "k_pack_nodes",
+    "k_qsort",
 };
 
 // ---- live per-kernel timing (CUDA events on the launching stream) ----
@@ -170,11 +172,12 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   t->h = tree_height(size, f->cfg.leaf_size);
   t->nnodes = ((int64_t)2 << t->h) - 1;
   t->nleaves = (int64_t)1 << t->h;
-  size_t b_pts = a256((size_t)f->dim * size * 4), b_ids = a256((size_t)size * 4),
+  size_t b_pts = a256((size_t)rec_ints(f->dim) * size * 4),
          b_key = a256((size_t)t->nnodes * 8), b_child = a256((size_t)t->nnodes * 8),
          b_box = a256((size_t)t->nnodes * 2 * f->dim * 4), b_live = a256((size_t)t->nnodes * 4),
-         b_leaf = a256((size_t)(t->nleaves + 1) * 4);
-  t->bytes = b_pts + b_ids + b_key + b_child + b_box + b_live + b_leaf;
+         b_leaf = a256((size_t)(t->nleaves + 1) * 4),
+         b_pk = a256((size_t)(t->nleaves - 1) * packed_node_ints(f->dim) * 4);
+  t->bytes = b_pts + b_key + b_child + b_box + b_live + b_leaf + b_pk;
   int st = dev_alloc(f, &t->block, t->bytes, s);
   if (st) {
     delete t;
@@ -182,12 +185,12 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   }
   char *p = (char *)t->block;
   t->pts = (int32_t *)p; p += b_pts;
-  t->ids = (int32_t *)p; p += b_ids;
   t->key = (uint64_t *)p; p += b_key;
   t->child = (int2 *)p; p += b_child;
   t->box = (int32_t *)p; p += b_box;
   t->live_nodes = (int32_t *)p; p += b_live;
-  t->leaf_off = (int32_t *)p;
+  t->leaf_off = (int32_t *)p; p += b_leaf;
+  t->pk = (int32_t *)p;
   // unwritten children read as (-1, -1), i.e. leaf 0: never outside the arrays
   cudaMemsetAsync(t->child, 0xff, (size_t)t->nnodes * 8, s);
   *out = t;
@@ -208,13 +211,13 @@ ForestView forest_view(const bdl_forest *f) {
     if (!t) continue;
     TreeView &tv = v.tree[n++];
     tv.pts = t->pts;
-    tv.ids = t->ids;
     tv.key = t->key;
     tv.child = t->child;
     tv.box = t->box;
     tv.live = t->live_nodes;
     tv.leaf_off = t->leaf_off;
     tv.bloom = t->bloom;
+    tv.pk = t->pk;
     tv.bloom_blocks = t->bloom_blocks;
     tv.size = t->size;
     tv.nnodes = t->nnodes;
@@ -303,7 +306,7 @@ static int insert_pool(bdl_forest *f, const int32_t *arr, int64_t first, int64_t
       Tree *ct = f->trees[i];
       capsum += X << i;
       livesum += ct->live;
-      cl.push_back(ClearedSrc{ct->pts, ct->ids, ct->size, (int32_t)bt.size()});
+      cl.push_back(ClearedSrc{ct->pts, ct->size, (int32_t)bt.size()});
     }
     int64_t shortfall = (X << j) - capsum;
     Tree *nt = nullptr;
@@ -353,6 +356,8 @@ static int finish(bdl_forest *f, cudaStream_t s, int st) {
     return set_error(BDL_EINTERNAL, "device bounds check failed, code " + std::to_string(f->pinned[500]));
   return BDL_OK;
 }
+
+constexpr int64_t kSortMinQueries = 1 << 15;
 
 static int check_config(const bdl_config &c) {
   if (c.leaf_size < 2 || c.leaf_size > 64) return set_error(BDL_EINVAL, "leaf_size must be in 2..64");
@@ -531,12 +536,14 @@ int bdl_erase(bdl_forest *f, const int32_t *ids, int64_t n, int64_t *out_n, bdl_
     t->bloom_blocks = blocks;
     t->bloom_bytes = (size_t)blocks * 32;
     cudaMemsetAsync(t->bloom, 0, t->bloom_bytes, s);
-    launch_bloom_build(t, f->cfg.hash_seed, s);
+    launch_bloom_build(t, f->dim, f->cfg.hash_seed, s);
   }
   if (st) { dev_free(f, list, (size_t)n * 4, s); return st; }
   // 3. probe, descend, tombstone (Alg. 2 per tree, all trees in one launch)
   ForestView fv = forest_view(f);
   launch_erase_locate(fv, f->cfg.hash_seed, (const int32_t *)list, ne, s);
+  for (int i = 0; i < kMaxLevel; ++i)   // live counts changed: refresh the k-NN records
+    if (f->trees[i]) launch_pack_nodes(f->trees[i], f->dim, s);
   // 4. the buffer
   launch_buffer_compact(f->buf, f->nbuf, f->alive, f->dev_small, s);
   launch_gather_roots(fv, f->dev_small + 1, s);
@@ -591,9 +598,25 @@ int bdl_knn(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids,
   if (m == 0) return BDL_OK;
   if (!q || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL pointer");
   DeviceGuard g(f->device);
+  cudaStream_t s = (cudaStream_t)stream;
   ForestView fv = forest_view(f);
-  return finish(f, (cudaStream_t)stream,
-                launch_knn(fv, q, m, k, out_ids, out_d2, f->knn_stats, (cudaStream_t)stream));
+  // large batches run in spatial order so that neighbouring threads walk
+  // neighbouring paths; results are written back in input order
+  void *scratch = nullptr;
+  size_t sbytes = 0;
+  int32_t *perm = nullptr;
+  if (m >= kSortMinQueries) {
+    sbytes = query_sort_bytes(m, f->dim);
+    if (dev_alloc(f, &scratch, sbytes, s) == BDL_OK) {
+      perm = (int32_t *)scratch;
+      launch_query_sort(q, m, f->dim, (char *)scratch + ((size_t)m * 4 + 255) / 256 * 256, perm, s);
+    } else {
+      scratch = nullptr;   // fall back to input order (same results)
+    }
+  }
+  int st = launch_knn(fv, q, perm, m, k, out_ids, out_d2, f->knn_stats, s);
+  if (scratch) dev_free(f, scratch, sbytes, s);
+  return finish(f, s, st);
 }
 
 int bdl_size(const bdl_forest *f, int64_t *out) {
@@ -669,9 +692,17 @@ int bdl_tree_export(const bdl_forest *f, int level, int64_t *key, int32_t *child
   cp(box, t->box, (size_t)t->nnodes * 2 * f->dim * 4);
   cp(live, t->live_nodes, (size_t)t->nnodes * 4);
   cp(leaf_off, t->leaf_off, (size_t)(t->nleaves + 1) * 4);
-  cp(ids, t->ids, (size_t)t->size * 4);
+  std::vector<int32_t> recs;
+  const int rs = rec_ints(f->dim);
+  if (ids && !st) {
+    recs.resize((size_t)t->size * rs);
+    cp(recs.data(), t->pts, recs.size() * 4);
+  }
   if (st) return st;
-  return cuda_check(cudaStreamSynchronize(s), "sync");
+  st = cuda_check(cudaStreamSynchronize(s), "sync");
+  if (!st && ids)
+    for (int64_t j = 0; j < t->size; ++j) ids[j] = recs[(size_t)j * rs + f->dim];
+  return st;
 }
 
 int bdl_bloom_export(const bdl_forest *f, int level, uint32_t *words, bdl_stream_t stream) {
