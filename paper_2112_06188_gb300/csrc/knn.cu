@@ -92,7 +92,7 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, const int32_t *qs,
+__global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, const int32_t *qs,
                                                          const int32_t *perm, int64_t m, int k,
                                                          int32_t *out_ids, int64_t *out_d2,
                                                          unsigned long long *stats) {
@@ -100,16 +100,18 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
   extern __shared__ __align__(8) unsigned char knn_sm[];
   uint64_t *s_d = reinterpret_cast<uint64_t *>(knn_sm);
   int32_t *s_id = reinterpret_cast<int32_t *>(s_d + (size_t)k * kKnnThreads);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m) return;
-  const int64_t qi = perm ? perm[t] : t;
+  // whole warps stay resident (and converged) until every lane is done
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~(int64_t)31) >= m) return;
+  const bool active = t < m;
+  const int64_t qi = active ? (perm ? perm[t] : t) : 0;
   const int dim = D ? D : F.dim;
   const int rec = packed_node_ints(dim);
   const int rs = rec_ints(dim);
   int32_t q[D ? D : kMaxDim];
 #pragma unroll
   for (int c = 0; c < (D ? D : kMaxDim); ++c)
-    if (c < dim) q[c] = qs[qi * dim + c];
+    if (c < dim) q[c] = active ? qs[qi * dim + c] : 0;
   TopK best;
   best.init(s_d, s_id);
   unsigned long long nvisit = 0, npts = 0;
@@ -121,55 +123,69 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
     const TreeView &T = F.tree[ti];
     if (T.live[0] <= 0) continue;
     // code >= 0: internal node record; code < 0: leaf -1-code
-    int sp = 1;
-    sv[0] = T.h > 0 ? 0 : -1;
-    smd[0] = box_mindist_lb<D>(q, T.box, dim);
+    int sp = 0;
+    if (active) {
+      sv[0] = T.h > 0 ? 0 : -1;
+      smd[0] = box_mindist_lb<D>(q, T.box, dim);
+      sp = 1;
+    }
     const int32_t ninternal = (int32_t)(((int64_t)1 << T.h) - 1);
-    while (sp > 0) {
+    int pa = 0, pz = 0;
+    bool pending = false;   // a leaf [pa, pz) is due but not scanned yet
+    while (true) {
+      const unsigned wm = __ballot_sync(0xffffffffu, pending || sp > 0);
+      if (!wm) break;
+      const unsigned pm = __ballot_sync(0xffffffffu, pending);
+      if (2 * __popc(pm) >= __popc(wm)) {
+        // at least half of the working lanes have a leaf due: scan them together
+        if (pending) {
+          for (int j = pa; j < pz; ++j) {
+            const int32_t *src = T.pts + (int64_t)j * rs;
+            int32_t id;
+            uint64_t s = 0;
+            if (D) {
+              int32_t p[D ? rec_ints(D) : 4];
+#pragma unroll
+              for (int c4 = 0; c4 < (D ? rec_ints(D) : 4); c4 += 4) {
+                int4 v = *reinterpret_cast<const int4 *>(src + c4);
+                p[c4] = v.x;
+                p[c4 + 1] = v.y;
+                p[c4 + 2] = v.z;
+                p[c4 + 3] = v.w;
+              }
+              id = p[D ? D : 0];
+#pragma unroll
+              for (int c = 0; c < (D ? D : 1); ++c) {
+                int32_t g = q[c] - p[c];
+                s += (uint64_t)((int64_t)g * g);
+              }
+            } else {
+              id = src[dim];
+              for (int c = 0; c < dim; ++c) {
+                int32_t g = q[c] - src[c];
+                s += (uint64_t)((int64_t)g * g);
+              }
+            }
+            if (id < 0) continue;
+            npts++;
+            if (best.better(s, id)) best.insert(s, id, k);
+          }
+          pending = false;
+        }
+        continue;
+      }
+      // otherwise every lane without a due leaf takes one traversal step
+      if (pending || sp == 0) continue;
       --sp;
       const int code = sv[sp];
       if (best.prune(smd[sp])) continue;
       nvisit++;
+      int leaf = -1;
       if (code < 0) {
-        const int leaf = -1 - code;
-        if (leaf > ninternal) { atomicOr(F.err, kErrChild); continue; }
-        const int a = T.leaf_off[leaf], z = T.leaf_off[leaf + 1];
-        if (a < 0 || z > T.size || a > z) { atomicOr(F.err, kErrLeaf); continue; }
-        for (int j = a; j < z; ++j) {
-          int32_t p[D ? rec_ints(D) : 1];
-          const int32_t *src = T.pts + (int64_t)j * rs;
-          int32_t id;
-          uint64_t s = 0;
-          if (D) {
-#pragma unroll
-            for (int c4 = 0; c4 < (D ? rec_ints(D) : 1); c4 += 4) {
-              int4 v = *reinterpret_cast<const int4 *>(src + c4);
-              p[c4] = v.x;
-              if (c4 + 1 < (D ? rec_ints(D) : 1)) p[c4 + 1] = v.y;
-              if (c4 + 2 < (D ? rec_ints(D) : 1)) p[c4 + 2] = v.z;
-              if (c4 + 3 < (D ? rec_ints(D) : 1)) p[c4 + 3] = v.w;
-            }
-            id = p[D ? D : 0];
-            if (id < 0) continue;
-#pragma unroll
-            for (int c = 0; c < (D ? D : 1); ++c) {
-              int32_t g = q[c] - p[c];
-              s += (uint64_t)((int64_t)g * g);
-            }
-          } else {
-            id = src[dim];
-            if (id < 0) continue;
-            for (int c = 0; c < dim; ++c) {
-              int32_t g = q[c] - src[c];
-              s += (uint64_t)((int64_t)g * g);
-            }
-          }
-          npts++;
-          if (best.better(s, id)) best.insert(s, id, k);
-        }
+        leaf = -1 - code;
+      } else if (code >= ninternal || sp + 2 > kStack) {
+        atomicOr(F.err, code >= ninternal ? kErrChild : kErrStack);
       } else {
-        if (code >= ninternal) { atomicOr(F.err, kErrChild); continue; }
-        if (sp + 2 > kStack) { atomicOr(F.err, kErrStack); continue; }
         const int32_t *r = T.pk + (int64_t)code * rec;
         const int4 hdr = *reinterpret_cast<const int4 *>(r);
         const float ml = hdr.z > 0 ? box_mindist_lb<D>(q, r + 4, dim) : kInf;
@@ -178,10 +194,30 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
         const int vn = lfirst ? hdr.x : hdr.y, vf = lfirst ? hdr.y : hdr.x;
         const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
         if (mf != kInf && !best.prune(mf)) { sv[sp] = vf; smd[sp] = mf; sp++; }
-        if (mn != kInf && !best.prune(mn)) { sv[sp] = vn; smd[sp] = mn; sp++; }
+        if (mn != kInf && !best.prune(mn)) {
+          if (vn < 0) {          // nearer child is a leaf: due now
+            nvisit++;
+            leaf = -1 - vn;
+          } else {
+            sv[sp] = vn;
+            smd[sp] = mn;
+            sp++;
+          }
+        }
+      }
+      if (leaf >= 0) {
+        if (leaf > ninternal) {
+          atomicOr(F.err, kErrChild);
+        } else {
+          pa = T.leaf_off[leaf];
+          pz = T.leaf_off[leaf + 1];
+          if (pa < 0 || pz > T.size || pa > pz) atomicOr(F.err, kErrLeaf);
+          else pending = true;
+        }
       }
     }
   }
+  if (!active) return;
   // the buffer tree: exact scan of its points
   for (int64_t j = 0; j < F.nbuf; ++j) {
     const int32_t id = F.buf[j];
