@@ -173,6 +173,14 @@ __device__ inline uint32_t bloom_word_bit(uint64_t bits, int w) {
 // device views
 // ---------------------------------------------------------------------------
 
+// One tree node (16 bytes, one sector per visit): the split key of an
+// internal node and the slots of its children; a leaf has key 0 and
+// l = -1 - (leaf index), r = 0.
+struct __align__(16) Node {
+  uint64_t key;
+  int32_t l, r;
+};
+
 // Ints of one point record in a tree: dim coordinates, the id, padding to a
 // multiple of 16 bytes (so a 3-D point is one int4: x, y, z, id).
 __host__ __device__ constexpr int rec_ints(int dim) { return (dim + 1 + 3) / 4 * 4; }
@@ -183,13 +191,12 @@ __host__ __device__ constexpr int packed_node_ints(int dim) { return (4 + 4 * di
 
 struct TreeView {          // one static tree, device pointers
   int32_t *pts;            // [size][rec_ints(dim)]: coordinates, id (erased: id | kTomb)
-  const uint64_t *key;     // [nnodes]
-  const int2 *child;       // [nnodes]
+  const Node *node;        // [nnodes]
   const int32_t *box;      // [nnodes][2*dim]
   int32_t *live;           // [nnodes]
   const int32_t *leaf_off; // [2^h + 1]
   const uint32_t *bloom;   // [blocks * 8] or nullptr
-  const int32_t *pk;       // packed internal nodes for k-NN, vEB order of the h internal levels
+  int32_t *pk;             // packed internal nodes for k-NN, vEB order of the h internal levels
   int64_t size;
   int64_t nnodes;
   int64_t bloom_blocks;
@@ -230,8 +237,7 @@ struct Tree {
   size_t bytes = 0;
   int32_t *pts = nullptr;      // [size][rec_ints(dim)] in leaf order
   int32_t *box = nullptr, *live_nodes = nullptr, *leaf_off = nullptr;
-  uint64_t *key = nullptr;
-  int2 *child = nullptr;
+  Node *node = nullptr;        // [nnodes], vEB order
   int32_t *pk = nullptr;       // packed internal nodes (k-NN), (2^h - 1) records
   uint32_t *bloom = nullptr;   // separate allocation, built lazily
   int64_t bloom_blocks = 0;
@@ -262,6 +268,8 @@ struct bdl_forest {
   int32_t *buf = nullptr;        // [X] ascending ids
   int64_t nbuf = 0;
   bdl::Tree *trees[bdl::kMaxLevel] = {};
+  bdl::Tree *btree = nullptr;    // kd-tree over the buffer's points (k-NN only), built lazily
+  bool buf_dirty = true;         // the buffer changed since btree was built
   uint64_t F = 0;
   int64_t live = 0;              // host mirror of the live count
   int64_t bytes_in_use = 0;
@@ -323,6 +331,7 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
 int launch_knn(const ForestView &fv, const int32_t *q, const int32_t *perm, int64_t m, int k,
                int32_t *out_ids, int64_t *out_d2, unsigned long long *stats, cudaStream_t s);
 void launch_pack_nodes(const Tree *t, int dim, cudaStream_t s);
+void launch_pack_lives(const Tree *t, int dim, cudaStream_t s);
 // Spatial order of the queries (counting sort on a Morton prefix of their
 // coordinates): perm[m] gets query indices; scratch of query_sort_bytes().
 size_t query_sort_bytes(int64_t m, int dim);

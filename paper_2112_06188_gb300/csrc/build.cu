@@ -44,8 +44,7 @@ struct SegState {
 
 struct NodeOut {               // where a tree's arrays go
   int32_t *pts, *box, *live, *leaf_off;
-  uint64_t *key;
-  int2 *child;
+  Node *node;
 };
 
 struct LvTree {
@@ -353,8 +352,21 @@ __global__ void k_level_select(const LvParams P, int64_t nseg) {
     const NodeOut &o = P.out[T.slot];
     int l = T.h + 1;
     int64_t v = veb_slot(l, T.t, idx);
-    o.key[v] = med;
-    o.child[v] = make_int2((int)veb_slot(l, T.t + 1, 2 * idx), (int)veb_slot(l, T.t + 1, 2 * idx + 1));
+    o.node[v] = Node{med, (int32_t)veb_slot(l, T.t + 1, 2 * idx), (int32_t)veb_slot(l, T.t + 1, 2 * idx + 1)};
+  }
+}
+
+// Eight consecutive ints from x[p] (x + p is 32-byte aligned when p is a
+// multiple of 8); positions at or past `end` are not read.
+__device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, int32_t v[kItems]) {
+  if (p + kItems <= end) {
+    const int4 a = reinterpret_cast<const int4 *>(x + p)[0];
+    const int4 b = reinterpret_cast<const int4 *>(x + p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) v[j] = p + j < end ? x[p + j] : 0;
   }
 }
 
@@ -373,13 +385,17 @@ __global__ void k_level_partition(const LvParams P) {
   const int32_t *xi = P.src + P.dim * P.S + T.base;
   int64_t pb = g.p0 + (int64_t)threadIdx.x * kItems;
   int cls[kItems];
+  int32_t cv[kItems], iv[kItems];
+  load8(xc, pb, g.p1, cv);
+  load8(xi, pb, g.p1, iv);
   unsigned long long mine = 0;   // 4 x 16-bit class counts
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
     int64_t p = pb + j;
     cls[j] = -1;
     if (p < g.p1) {
       int w = p >= g.st1;
-      uint64_t k = comp_key(xc[p], xi[p]);
+      uint64_t k = comp_key(cv[j], iv[j]);
       int c = 2 * w + (k > (w ? med1 : med0));
       cls[j] = c;
       mine += 1ull << (16 * c);
@@ -428,10 +444,12 @@ __global__ void k_level_partition(const LvParams P) {
     dstp[j] = (int32_t)(st + rel);
   }
   for (int c = 0; c <= P.dim; ++c) {
-    const int32_t *x = P.src + c * P.S + T.base;
+    int32_t v[kItems];
+    load8(P.src + c * P.S + T.base, pb, g.p1, v);
     int32_t *y = P.dst + c * P.S + T.base;
+#pragma unroll
     for (int j = 0; j < kItems; ++j)
-      if (dstp[j] >= 0) y[dstp[j]] = x[pb + j];
+      if (dstp[j] >= 0) y[dstp[j]] = v[j];
   }
 }
 
@@ -597,8 +615,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
         int64_t bfs = (i0 << u) + s;
         int64_t v = veb_slot(l, t, bfs);
-        o.key[v] = s_res[s];
-        o.child[v] = make_int2((int)veb_slot(l, t + 1, 2 * bfs), (int)veb_slot(l, t + 1, 2 * bfs + 1));
+        o.node[v] = Node{s_res[s], (int32_t)veb_slot(l, t + 1, 2 * bfs), (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
       }
       // stable partition by a block scan of the left flags (positions blocked per thread)
       const int ipt = (cap + blockDim.x - 1) / blockDim.x;
@@ -693,8 +710,8 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         int64_t bfs = (i0 << u) + s;
         if ((va && ra == mr) || (vb && rb == mr)) {
           int64_t v = veb_slot(l, t, bfs);
-          o.key[v] = (va && ra == mr) ? ka : kb;
-          o.child[v] = make_int2((int)veb_slot(l, t + 1, 2 * bfs), (int)veb_slot(l, t + 1, 2 * bfs + 1));
+          o.node[v] = Node{(va && ra == mr) ? ka : kb, (int32_t)veb_slot(l, t + 1, 2 * bfs),
+                           (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
         }
       }
       __syncthreads();
@@ -711,8 +728,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     int a = (int)a64, z = (int)z64;
     int64_t leaf = (i0 << U) + lf;
     int64_t v = veb_slot(l, T.h, leaf);
-    o.key[v] = 0;
-    o.child[v] = make_int2((int)(-1 - leaf), 0);
+    o.node[v] = Node{0, (int32_t)(-1 - leaf), 0};
     o.live[v] = z;
     o.leaf_off[leaf] = (int32_t)(start0 + a);
     if (leaf == nleaves_tree - 1) o.leaf_off[nleaves_tree] = (int32_t)T.s;
@@ -825,8 +841,7 @@ NodeOut node_out(Tree *t) {
   o.box = t->box;
   o.live = t->live_nodes;
   o.leaf_off = t->leaf_off;
-  o.key = t->key;
-  o.child = t->child;
+  o.node = t->node;
   return o;
 }
 

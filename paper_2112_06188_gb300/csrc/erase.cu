@@ -106,18 +106,18 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
       }
       if (maybe) {
         int v = 0, depth = 0;
-        int2 ch;
+        Node nd;
         bool ok = true;
         while (true) {
           path[depth] = v;
-          ch = T.child[v];
-          if (ch.x < 0) break;
+          nd = T.node[v];
+          if (nd.l < 0) break;
           uint64_t key = comp_key(xq[depth % F.dim], id);
-          v = key <= T.key[v] ? ch.x : ch.y;
+          v = key > nd.key ? nd.r : nd.l;
           depth++;
           if (v < 0 || v >= T.nnodes || depth > T.h) { ok = false; break; }
         }
-        int leaf = -1 - ch.x;
+        int leaf = -1 - nd.l;
         int a = 0, z = 0;
         if (ok && leaf < ((int64_t)1 << T.h)) {
           a = T.leaf_off[leaf];

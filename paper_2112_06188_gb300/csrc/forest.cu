@@ -173,11 +173,11 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   t->nnodes = ((int64_t)2 << t->h) - 1;
   t->nleaves = (int64_t)1 << t->h;
   size_t b_pts = a256((size_t)rec_ints(f->dim) * size * 4),
-         b_key = a256((size_t)t->nnodes * 8), b_child = a256((size_t)t->nnodes * 8),
+         b_node = a256((size_t)t->nnodes * 16),
          b_box = a256((size_t)t->nnodes * 2 * f->dim * 4), b_live = a256((size_t)t->nnodes * 4),
          b_leaf = a256((size_t)(t->nleaves + 1) * 4),
          b_pk = a256((size_t)(t->nleaves - 1) * packed_node_ints(f->dim) * 4);
-  t->bytes = b_pts + b_key + b_child + b_box + b_live + b_leaf + b_pk;
+  t->bytes = b_pts + b_node + b_box + b_live + b_leaf + b_pk;
   int st = dev_alloc(f, &t->block, t->bytes, s);
   if (st) {
     delete t;
@@ -185,14 +185,13 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   }
   char *p = (char *)t->block;
   t->pts = (int32_t *)p; p += b_pts;
-  t->key = (uint64_t *)p; p += b_key;
-  t->child = (int2 *)p; p += b_child;
+  t->node = (Node *)p; p += b_node;
   t->box = (int32_t *)p; p += b_box;
   t->live_nodes = (int32_t *)p; p += b_live;
   t->leaf_off = (int32_t *)p; p += b_leaf;
   t->pk = (int32_t *)p;
-  // unwritten children read as (-1, -1), i.e. leaf 0: never outside the arrays
-  cudaMemsetAsync(t->child, 0xff, (size_t)t->nnodes * 8, s);
+  // unwritten nodes read as leaf 0 (children -1, -1): never outside the arrays
+  cudaMemsetAsync(t->node, 0xff, (size_t)t->nnodes * 16, s);
   *out = t;
   return BDL_OK;
 }
@@ -211,8 +210,7 @@ ForestView forest_view(const bdl_forest *f) {
     if (!t) continue;
     TreeView &tv = v.tree[n++];
     tv.pts = t->pts;
-    tv.key = t->key;
-    tv.child = t->child;
+    tv.node = t->node;
     tv.box = t->box;
     tv.live = t->live_nodes;
     tv.leaf_off = t->leaf_off;
@@ -286,6 +284,7 @@ static int insert_pool(bdl_forest *f, const int32_t *arr, int64_t first, int64_t
     launch_pool_tail(pool, f->nbuf, n, f->buf + f->nbuf, s);
     if (arr) launch_sort_small(f->buf, t, s);
     f->nbuf = t;
+    f->buf_dirty = true;
     return cuda_check(cudaGetLastError(), "buffer append");
   }
   const uint64_t Fnew = f->F + (uint64_t)q;
@@ -341,6 +340,7 @@ static int insert_pool(bdl_forest *f, const int32_t *arr, int64_t first, int64_t
   dev_free(f, f->buf, (size_t)X * 4, s);
   f->buf = (int32_t *)newbuf;
   f->nbuf = rem;
+  f->buf_dirty = true;
   f->F = Fnew;
   return cuda_check(cudaGetLastError(), "insert");
 }
@@ -543,13 +543,14 @@ int bdl_erase(bdl_forest *f, const int32_t *ids, int64_t n, int64_t *out_n, bdl_
   ForestView fv = forest_view(f);
   launch_erase_locate(fv, f->cfg.hash_seed, (const int32_t *)list, ne, s);
   for (int i = 0; i < kMaxLevel; ++i)   // live counts changed: refresh the k-NN records
-    if (f->trees[i]) launch_pack_nodes(f->trees[i], f->dim, s);
+    if (f->trees[i]) launch_pack_lives(f->trees[i], f->dim, s);
   // 4. the buffer
   launch_buffer_compact(f->buf, f->nbuf, f->alive, f->dev_small, s);
   launch_gather_roots(fv, f->dev_small + 1, s);
   st = sync_read(f, f->dev_small, 1 + fv.ntrees, s);
   dev_free(f, list, (size_t)n * 4, s);
   if (st) return st;
+  if (f->pinned[0] != f->nbuf) f->buf_dirty = true;
   f->nbuf = f->pinned[0];
   for (int j = 0; j < fv.ntrees; ++j) f->trees[fv.tree[j].level]->live = f->pinned[1 + j];
   // 5. trees below half capacity (Alg. 4 lines 3-4)
@@ -599,7 +600,39 @@ int bdl_knn(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids,
   if (!q || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL pointer");
   DeviceGuard g(f->device);
   cudaStream_t s = (cudaStream_t)stream;
+  // the buffer's points get a small kd-tree of their own (the paper's buffer
+  // tree), rebuilt here when the buffer changed; without it they are scanned
+  if (f->buf_dirty) {
+    free_tree(f, f->btree, s);
+    f->btree = nullptr;
+    if (f->nbuf > 0) {
+      Tree *bt = nullptr;
+      if (alloc_tree(f, kMaxLevel, f->nbuf, s, &bt) == BDL_OK) {
+        std::vector<BuildTree> b{BuildTree{bt, 0, f->nbuf, bt->h, 0}};
+        PoolSrc pool{f->buf, f->nbuf, nullptr, 0};
+        if (build_trees(f, b, {}, pool, {0, f->nbuf}, {0}, s) == BDL_OK) f->btree = bt;
+        else free_tree(f, bt, s);
+      }
+    }
+    f->buf_dirty = false;
+  }
   ForestView fv = forest_view(f);
+  if (f->btree && fv.ntrees < kMaxLevel) {
+    TreeView &tv = fv.tree[fv.ntrees++];
+    const Tree *t = f->btree;
+    memset(&tv, 0, sizeof(tv));
+    tv.pts = t->pts;
+    tv.node = t->node;
+    tv.box = t->box;
+    tv.live = t->live_nodes;
+    tv.leaf_off = t->leaf_off;
+    tv.pk = t->pk;
+    tv.size = t->size;
+    tv.nnodes = t->nnodes;
+    tv.h = t->h;
+    tv.level = t->level;
+    fv.nbuf = 0;
+  }
   // large batches run in spatial order so that neighbouring threads walk
   // neighbouring paths; results are written back in input order
   void *scratch = nullptr;
@@ -631,6 +664,7 @@ int bdl_destroy(bdl_forest *f) {
   cudaDeviceSynchronize();
   cudaStream_t s = 0;
   for (int i = 0; i < kMaxLevel; ++i) free_tree(f, f->trees[i], s);
+  free_tree(f, f->btree, s);
   if (f->id_cap) {
     dev_free(f, f->idtab, (size_t)f->id_cap * f->dim * 4, s);
     dev_free(f, f->alive, (size_t)f->id_cap / 8, s);
@@ -687,8 +721,11 @@ int bdl_tree_export(const bdl_forest *f, int level, int64_t *key, int32_t *child
   auto cp = [&](void *dst, const void *src, size_t bytes) {
     if (dst && !st) st = cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "copy");
   };
-  cp(key, t->key, (size_t)t->nnodes * 8);
-  cp(child, t->child, (size_t)t->nnodes * 8);
+  std::vector<Node> nodes;
+  if ((key || child) && !st) {
+    nodes.resize((size_t)t->nnodes);
+    cp(nodes.data(), t->node, nodes.size() * sizeof(Node));
+  }
   cp(box, t->box, (size_t)t->nnodes * 2 * f->dim * 4);
   cp(live, t->live_nodes, (size_t)t->nnodes * 4);
   cp(leaf_off, t->leaf_off, (size_t)(t->nleaves + 1) * 4);
@@ -702,6 +739,11 @@ int bdl_tree_export(const bdl_forest *f, int level, int64_t *key, int32_t *child
   st = cuda_check(cudaStreamSynchronize(s), "sync");
   if (!st && ids)
     for (int64_t j = 0; j < t->size; ++j) ids[j] = recs[(size_t)j * rs + f->dim];
+  if (!st && (key || child))
+    for (int64_t v = 0; v < t->nnodes; ++v) {
+      if (key) key[v] = (int64_t)nodes[(size_t)v].key;
+      if (child) { child[2 * v] = nodes[(size_t)v].l; child[2 * v + 1] = nodes[(size_t)v].r; }
+    }
   return st;
 }
 

@@ -91,7 +91,7 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
   return s * (1.0f - 3.814697265625e-06f);   // 1 - 2^-18
 }
 
-template <int D>
+template <int D, bool STATS>
 __global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, const int32_t *qs,
                                                          const int32_t *perm, int64_t m, int k,
                                                          int32_t *out_ids, int64_t *out_d2,
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, con
               }
             }
             if (id < 0) continue;
-            npts++;
+            if (STATS) npts++;
             if (best.better(s, id)) best.insert(s, id, k);
           }
           pending = false;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, con
       --sp;
       const int code = sv[sp];
       if (best.prune(smd[sp])) continue;
-      nvisit++;
+      if (STATS) nvisit++;
       int leaf = -1;
       if (code < 0) {
         leaf = -1 - code;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, con
         if (mf != kInf && !best.prune(mf)) { sv[sp] = vf; smd[sp] = mf; sp++; }
         if (mn != kInf && !best.prune(mn)) {
           if (vn < 0) {          // nearer child is a leaf: due now
-            nvisit++;
+            if (STATS) nvisit++;
             leaf = -1 - vn;
           } else {
             sv[sp] = vn;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, con
     oi[j] = ok ? best.id[j * kKnnThreads] : -1;
     od[j] = ok ? (int64_t)best.d[j * kKnnThreads] : INT64_MAX;
   }
-  if (stats) {
+  if (STATS) {
     atomicAdd(&stats[0], nvisit);
     atomicAdd(&stats[1], npts);
     atomicAdd(&stats[2], 1ull);
@@ -251,8 +251,11 @@ void launch_d(const ForestView &fv, const int32_t *q, const int32_t *perm, int64
               int32_t *oi, int64_t *od, unsigned long long *stats, cudaStream_t s) {
   const size_t smem = (size_t)k * kKnnThreads * 12;   // <= 48 KB for k <= 32
   KScope ks_(kK_knn, s);
-  k_knn<D><<<(unsigned)((m + kKnnThreads - 1) / kKnnThreads), kKnnThreads, smem, s>>>(
-      fv, q, perm, m, k, oi, od, stats);
+  const unsigned grid = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
+  if (stats)
+    k_knn<D, true><<<grid, kKnnThreads, smem, s>>>(fv, q, perm, m, k, oi, od, stats);
+  else
+    k_knn<D, false><<<grid, kKnnThreads, smem, s>>>(fv, q, perm, m, k, oi, od, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,7 +263,7 @@ void launch_d(const ForestView &fv, const int32_t *q, const int32_t *perm, int64
 // h internal levels (a complete tree of its own)
 // ---------------------------------------------------------------------------
 
-__global__ void k_pack_nodes(const int2 *child, const int32_t *box, const int32_t *live, int h,
+__global__ void k_pack_nodes(const Node *node, const int32_t *box, const int32_t *live, int h,
                              int dim, int32_t *pk) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nint = ((int64_t)1 << h) - 1;
@@ -272,7 +275,8 @@ __global__ void k_pack_nodes(const int2 *child, const int32_t *box, const int32_
   const int rec = packed_node_ints(dim);
   const int rs = rec_ints(dim);
   int32_t *r = pk + p * rec;
-  const int2 ch = child[v];
+  const Node nd = node[v];
+  const int2 ch = make_int2(nd.l, nd.r);
   int code[2];
   if (t + 1 < h) {
     code[0] = (int)veb_slot(h, t + 1, 2 * i);
@@ -404,8 +408,27 @@ void launch_pack_nodes(const Tree *t, int dim, cudaStream_t s) {
   int64_t nint = ((int64_t)1 << t->h) - 1;
   if (nint <= 0) return;
   KScope ks_(kK_pack_nodes, s);
-  k_pack_nodes<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(t->child, t->box, t->live_nodes, t->h,
+  k_pack_nodes<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(t->node, t->box, t->live_nodes, t->h,
                                                                dim, t->pk);
+}
+
+// After an erase only the live counts of the packed records change.
+__global__ void k_pack_lives(const Node *node, const int32_t *live, int h, int dim, int32_t *pk) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nint = ((int64_t)1 << h) - 1;
+  if (g >= nint) return;
+  const int t = 63 - __clzll(g + 1);
+  const int64_t i = g + 1 - ((int64_t)1 << t);
+  const Node nd = node[veb_slot(h + 1, t, i)];
+  int2 lv = make_int2(live[nd.l], live[nd.r]);
+  *reinterpret_cast<int2 *>(pk + veb_slot(h, t, i) * packed_node_ints(dim) + 2) = lv;
+}
+
+void launch_pack_lives(const Tree *t, int dim, cudaStream_t s) {
+  int64_t nint = ((int64_t)1 << t->h) - 1;
+  if (nint <= 0) return;
+  KScope ks_(kK_pack_nodes, s);
+  k_pack_lives<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(t->node, t->live_nodes, t->h, dim, t->pk);
 }
 
 size_t query_sort_bytes(int64_t m, int dim) {
