@@ -104,6 +104,27 @@ int bdl_erase(bdl_forest *f, const int32_t *ids_dev, int64_t n, int64_t *out_n_e
 int bdl_knn(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_ids_dev,
             int64_t *out_d2_dev, bdl_stream_t stream);
 
+/* kNN_L like bdl_knn, for callers that cannot allocate device memory while
+ * they query: for example a process whose free device memory is already held
+ * by another allocator, so that a new allocation would fail, or a request
+ * path that must not wait on a memory pool.  bdl_knn takes scratch for the
+ * query ordering from the library's pool, and it may rebuild the buffer's
+ * kd-tree.  This call does neither.  (The paper has no counterpart; it is an
+ * interface choice of this library.)
+ *  - Scratch lives in one fixed device array of 8 MiB + 4 KiB that every GPU
+ *    loading the library holds until the process exits.
+ *  - m is at most 1,048,576; larger batches return BDL_EINVAL.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind: calls
+ *    whose work can overlap on the GPU (other streams, other forests on the
+ *    same device) race with each other and must be ordered by the caller.
+ *  - If the buffer changed since the last bdl_knn, its points are scanned
+ *    instead of searched; results are the same as bdl_knn's. */
+int bdl_knn_noalloc(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_ids_dev,
+                    int64_t *out_d2_dev, bdl_stream_t stream);
+
 /* Number of live points (host-side count, no device access). */
 int bdl_size(const bdl_forest *f, int64_t *out_live_host);
 

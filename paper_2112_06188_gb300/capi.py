@@ -17,7 +17,7 @@ SYMBOLS = [
     "bdl_default_config", "bdl_create", "bdl_insert", "bdl_erase", "bdl_knn", "bdl_size",
     "bdl_destroy", "bdl_status_string", "bdl_last_error", "bdl_tree_mask", "bdl_buffer_ids",
     "bdl_tree_info", "bdl_tree_export", "bdl_bloom_export", "bdl_knn_stats", "bdl_launch_count",
-    "bdl_profile", "bdl_profile_read", "bdl_kernel_count", "bdl_kernel_name",
+    "bdl_profile", "bdl_profile_read", "bdl_kernel_count", "bdl_kernel_name", "bdl_knn_noalloc",
 ]
 
 
@@ -67,6 +67,7 @@ def load(path=None):
         "bdl_profile_read": (i32, [P, P, i32]),
         "bdl_kernel_count": (i32, []),
         "bdl_kernel_name": (ctypes.c_char_p, [i32]),
+        "bdl_knn_noalloc": (i32, [P, P, i64, i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -123,6 +124,11 @@ def bdl_erase(f, ids_dev, n, stream):
 
 def bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
     return load().bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream)
+
+
+def bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
+    """bdl_knn without device allocation (scratch in a fixed library array)."""
+    return load().bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream)
 
 
 def bdl_size(f):

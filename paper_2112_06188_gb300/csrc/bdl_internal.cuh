@@ -288,6 +288,13 @@ int cuda_check(cudaError_t e, const char *what);
 int dev_alloc(bdl_forest *f, void **p, size_t bytes, cudaStream_t s);
 void dev_free(bdl_forest *f, void *p, size_t bytes, cudaStream_t s);
 ForestView forest_view(const bdl_forest *f);
+// The view k-NN uses: the static trees plus the buffer's kd-tree.  With
+// build = true a stale buffer tree is rebuilt first (this allocates); with
+// build = false a stale one is left alone and the buffer is scanned instead.
+ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s);
+// BDL_DEBUG_CHECK: wait for the call's kernels and report a bounds-check hit.
+int finish_call(bdl_forest *f, cudaStream_t s, int status);
+constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input order
 int smem_subtree_capacity(int dim);
 
 // ---- build.cu ----

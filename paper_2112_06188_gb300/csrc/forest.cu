@@ -345,6 +345,43 @@ static int insert_pool(bdl_forest *f, const int32_t *arr, int64_t first, int64_t
   return cuda_check(cudaGetLastError(), "insert");
 }
 
+ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s) {
+  // the buffer's points get a small kd-tree of their own (the paper's buffer
+  // tree), rebuilt when the buffer changed; without it they are scanned
+  if (build && f->buf_dirty) {
+    free_tree(f, f->btree, s);
+    f->btree = nullptr;
+    if (f->nbuf > 0) {
+      Tree *bt = nullptr;
+      if (alloc_tree(f, kMaxLevel, f->nbuf, s, &bt) == BDL_OK) {
+        std::vector<BuildTree> b{BuildTree{bt, 0, f->nbuf, bt->h, 0}};
+        PoolSrc pool{f->buf, f->nbuf, nullptr, 0};
+        if (build_trees(f, b, {}, pool, {0, f->nbuf}, {0}, s) == BDL_OK) f->btree = bt;
+        else free_tree(f, bt, s);
+      }
+    }
+    f->buf_dirty = false;
+  }
+  ForestView fv = forest_view(f);
+  if (f->btree && !f->buf_dirty && fv.ntrees < kMaxLevel) {
+    TreeView &tv = fv.tree[fv.ntrees++];
+    const Tree *t = f->btree;
+    memset(&tv, 0, sizeof(tv));
+    tv.pts = t->pts;
+    tv.node = t->node;
+    tv.box = t->box;
+    tv.live = t->live_nodes;
+    tv.leaf_off = t->leaf_off;
+    tv.pk = t->pk;
+    tv.size = t->size;
+    tv.nnodes = t->nnodes;
+    tv.h = t->h;
+    tv.level = t->level;
+    fv.nbuf = 0;
+  }
+  return fv;
+}
+
 // With BDL_DEBUG_CHECK=1 every call waits for its kernels and fails with
 // BDL_EINTERNAL if one of them recorded an out-of-range index.
 static int finish(bdl_forest *f, cudaStream_t s, int st) {
@@ -357,7 +394,7 @@ static int finish(bdl_forest *f, cudaStream_t s, int st) {
   return BDL_OK;
 }
 
-constexpr int64_t kSortMinQueries = 1 << 15;
+int finish_call(bdl_forest *f, cudaStream_t s, int st) { return finish(f, s, st); }
 
 static int check_config(const bdl_config &c) {
   if (c.leaf_size < 2 || c.leaf_size > 64) return set_error(BDL_EINVAL, "leaf_size must be in 2..64");
@@ -600,39 +637,7 @@ int bdl_knn(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids,
   if (!q || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL pointer");
   DeviceGuard g(f->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // the buffer's points get a small kd-tree of their own (the paper's buffer
-  // tree), rebuilt here when the buffer changed; without it they are scanned
-  if (f->buf_dirty) {
-    free_tree(f, f->btree, s);
-    f->btree = nullptr;
-    if (f->nbuf > 0) {
-      Tree *bt = nullptr;
-      if (alloc_tree(f, kMaxLevel, f->nbuf, s, &bt) == BDL_OK) {
-        std::vector<BuildTree> b{BuildTree{bt, 0, f->nbuf, bt->h, 0}};
-        PoolSrc pool{f->buf, f->nbuf, nullptr, 0};
-        if (build_trees(f, b, {}, pool, {0, f->nbuf}, {0}, s) == BDL_OK) f->btree = bt;
-        else free_tree(f, bt, s);
-      }
-    }
-    f->buf_dirty = false;
-  }
-  ForestView fv = forest_view(f);
-  if (f->btree && fv.ntrees < kMaxLevel) {
-    TreeView &tv = fv.tree[fv.ntrees++];
-    const Tree *t = f->btree;
-    memset(&tv, 0, sizeof(tv));
-    tv.pts = t->pts;
-    tv.node = t->node;
-    tv.box = t->box;
-    tv.live = t->live_nodes;
-    tv.leaf_off = t->leaf_off;
-    tv.pk = t->pk;
-    tv.size = t->size;
-    tv.nnodes = t->nnodes;
-    tv.h = t->h;
-    tv.level = t->level;
-    fv.nbuf = 0;
-  }
+  ForestView fv = knn_view(f, true, s);
   // large batches run in spatial order so that neighbouring threads walk
   // neighbouring paths; results are written back in input order
   void *scratch = nullptr;

@@ -16,6 +16,8 @@
 //    Morton prefix) so that a warp's threads walk neighbouring paths.
 #include "bdl_internal.cuh"
 
+#include <mutex>
+
 namespace bdl {
 
 namespace {
@@ -453,3 +455,76 @@ void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int3
 }
 
 }  // namespace bdl
+
+// ---------------------------------------------------------------------------
+// k-NN without device allocation
+// ---------------------------------------------------------------------------
+//
+// bdl_knn takes scratch for the query ordering from the library's memory
+// pool.  Some callers cannot let a query allocate: a process whose device
+// memory is already fully reserved by another allocator (a framework's
+// caching allocator holding the free memory, say) would see the allocation
+// fail, and a latency-bound request path may not wait on the pool.  For them
+// bdl_knn_noalloc keeps that scratch in the fixed array below instead.  The
+// array exists on every GPU that loads the library, from load until exit.
+
+namespace bdl {
+namespace {
+
+constexpr int64_t kNoAllocMaxQueries = 1 << 20;
+constexpr size_t kNoAllocPermBytes = (size_t)kNoAllocMaxQueries * 4;   // query order
+constexpr size_t kNoAllocScratchBytes = kNoAllocPermBytes + ((size_t)4 << 20) + 4096;
+
+// query order [m], then the Morton histogram (<= 2^20 bins) and its block sums
+static __device__ __align__(256) unsigned char g_knn_scratch[kNoAllocScratchBytes];
+
+std::mutex g_knn_scratch_mu;
+void *g_knn_scratch_addr[128];   // device address of g_knn_scratch, per device
+
+// Device address of the array on the current device (looked up on first use;
+// in host code the array's name is only a stand-in, not a device address).
+int knn_scratch_address(int dev, void **out) {
+  std::lock_guard<std::mutex> lk(g_knn_scratch_mu);
+  if (dev < 0 || dev >= 128) return set_error(BDL_EINVAL, "device index out of range");
+  if (!g_knn_scratch_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetSymbolAddress(k-NN scratch)");
+    g_knn_scratch_addr[dev] = p;
+  }
+  *out = g_knn_scratch_addr[dev];
+  return BDL_OK;
+}
+
+}  // namespace
+}  // namespace bdl
+
+extern "C" int bdl_knn_noalloc(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids,
+                               int64_t *out_d2, bdl_stream_t stream) {
+  using namespace bdl;
+  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
+  if (k < 1 || k > kMaxK) return set_error(BDL_EINVAL, "k must be in 1..32");
+  if (m < 0) return set_error(BDL_EINVAL, "m < 0");
+  if (m > kNoAllocMaxQueries)
+    return set_error(BDL_EINVAL, "bdl_knn_noalloc takes at most 1,048,576 queries per call");
+  if (m == 0) return BDL_OK;
+  if (!q || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL pointer");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != f->device) cudaSetDevice(f->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  void *scratch = nullptr;
+  int st = knn_scratch_address(f->device, &scratch);
+  if (!st) {
+    ForestView fv = knn_view(f, false, s);   // never rebuilds (no allocation)
+    int32_t *perm = nullptr;
+    if (m >= kSortMinQueries) {
+      perm = (int32_t *)scratch;
+      launch_query_sort(q, m, f->dim, (char *)scratch + kNoAllocPermBytes, perm, s);
+    }
+    st = finish_call(f, s, launch_knn(fv, q, perm, m, k, out_ids, out_d2, f->knn_stats, s));
+  }
+  if (prev >= 0 && prev != f->device) cudaSetDevice(prev);
+  return st;
+}
+
