@@ -263,6 +263,26 @@ def run_ours(a, rank, world, dist):
     return res
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
+    when the summary is missing or the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s_3d_10M.md" % kernel)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines()
+                  if line.startswith(("kernel_source:", "source_sha256_16:", "dram_bytes_per_launch:")))
+    try:
+        src = open(os.path.join(ROOT, fields["kernel_source"].strip()), "rb").read()
+    except (KeyError, OSError):
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != fields.get("source_sha256_16", "").strip():
+        return None
+    return int(fields["dram_bytes_per_launch"])
+
+
 def roofline(a, res, peaks):
     """Dominant kernel of the timed region against the measured HBM peak."""
     prof = res["prof"]
@@ -284,8 +304,10 @@ def roofline(a, res, peaks):
         return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(name) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "when" in peaks else "fallback",
             "ms_per_launch": round(per_launch_ms, 4),
             "algorithmic_bytes_per_launch": int(algo),
             "knn_visits_per_query": {"nodes": round(nodes / nq, 2), "leaf_points": round(points / nq, 2)}}
