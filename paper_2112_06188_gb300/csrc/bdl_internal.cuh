@@ -344,6 +344,10 @@ void launch_pack_lives(const Tree *t, int dim, cudaStream_t s);
 size_t query_sort_bytes(int64_t m, int dim);
 void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,
                        cudaStream_t s);
+// The same order for the points named by ids[m] (coordinates in coords):
+// out[m] receives the ids themselves, reordered.
+void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int dim,
+                       void *scratch, int32_t *out, cudaStream_t s);
 
 }  // namespace bdl
 

@@ -203,42 +203,47 @@ __global__ void k_level_hist(const LvParams P) {
 }
 
 // One warp per segment: the bucket holding the median (rank ceil(m/2)).
+// Each lane sums a contiguous run of 64 bins (independent loads), a warp scan
+// of the run sums finds the run holding the rank, and that lane walks it.
 __global__ void k_level_bucket(const LvParams P, int64_t nseg) {
   int64_t gs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (gs >= nseg) return;
-  int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  constexpr int kRun = kHistBins / 32;
   const LvTree &T = P.tr[find_tree_by_seg(P, gs)];
   int64_t st, sz;
   seg_range(T.s, T.t, gs - T.seg_off, st, sz);
-  int64_t r = (sz + 1) >> 1;
-  const uint32_t *hh = P.hist + gs * kHistBins;
-  int64_t below = 0;
-  for (int base = 0; base < kHistBins; base += 32) {
-    uint32_t v = hh[base + lane];
-    uint32_t inc = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-    if (below + tot >= r) {
-      bool hit = (below + inc >= r) && (below + inc - v < r);
-      unsigned m = __ballot_sync(0xffffffffu, hit);
-      int src = __ffs(m) - 1;
-      uint32_t vv = __shfl_sync(0xffffffffu, v, src);
-      uint32_t ii = __shfl_sync(0xffffffffu, inc, src);
-      if (lane == 0) {
-        SegState &S = P.seg[gs];
-        S.bucket = base + src;
-        S.nbucket = (int32_t)vv;
-        S.rank = r - (below + ii - vv);
-        S.cand_n = 0;
-        S.lcur = 0;
-        S.rcur = 0;
-      }
+  const uint32_t r = (uint32_t)((sz + 1) >> 1);
+  const uint4 *run = reinterpret_cast<const uint4 *>(P.hist + gs * kHistBins + lane * kRun);
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kRun / 4; ++j) {
+    const uint4 v = run[j];
+    sum += v.x + v.y + v.z + v.w;
+  }
+  uint32_t inc = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const bool hit = inc >= r && inc - sum < r;
+  const unsigned m = __ballot_sync(0xffffffffu, hit);
+  if (!hit || lane != __ffs(m) - 1) return;
+  uint32_t below = inc - sum;
+  const uint32_t *bins = P.hist + gs * kHistBins + lane * kRun;
+  for (int j = 0; j < kRun; ++j) {
+    const uint32_t v = bins[j];
+    if (below + v >= r) {
+      SegState &S = P.seg[gs];
+      S.bucket = lane * kRun + j;
+      S.nbucket = (int32_t)v;
+      S.rank = (int64_t)(r - below);
+      S.cand_n = 0;
+      S.lcur = 0;
+      S.rcur = 0;
       return;
     }
-    below += tot;
+    below += v;
   }
 }
 
@@ -288,6 +293,7 @@ __global__ void k_level_select(const LvParams P, int64_t nseg) {
   __shared__ int64_t s_rank;
   __shared__ uint32_t s_cnt;
   __shared__ uint64_t s_found;
+  __shared__ uint32_t s_wsum[8];
   __shared__ uint64_t keys[2048];
   int64_t gs = blockIdx.x;
   if (gs >= nseg) return;
@@ -329,16 +335,27 @@ __global__ void k_level_select(const LvParams P, int64_t nseg) {
       if ((k >> shift) == (s_pre >> shift)) atomicAdd(&hist[(k >> ns) & ((1u << ww) - 1)], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t below = 0;
-      for (int j = 0; j < (1 << ww); ++j) {
-        if (below + hist[j] >= s_rank) {
-          s_pre |= (uint64_t)j << ns;
-          s_rank -= below;
-          s_cnt = hist[j];
-          break;
-        }
-        below += hist[j];
+    {
+      // block scan of the 256 bins (one per thread) to find the rank's bucket
+      const int j = threadIdx.x;
+      const uint32_t v = j < (1 << ww) ? hist[j] : 0;
+      uint32_t inc = v;
+      const int lane = j & 31, warp = j >> 5;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) s_wsum[warp] = inc;
+      __syncthreads();
+      uint32_t base = 0;
+      for (int w = 0; w < warp; ++w) base += s_wsum[w];
+      inc += base;
+      const int64_t rank = s_rank;
+      __syncthreads();
+      if ((int64_t)inc >= rank && (int64_t)(inc - v) < rank) {
+        s_pre |= (uint64_t)j << ns;
+        s_rank = rank - (inc - v);
+        s_cnt = v;
       }
     }
     shift = ns;
@@ -503,7 +520,8 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   uint32_t *ex = hist + kHistBins;                      // [2048]
   uint16_t *perm0 = (uint16_t *)(ex + kHistBins);       // [cap]
   uint16_t *perm1 = perm0 + cap;                        // [cap]
-  unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap]
+  unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap] segment of each position
+  unsigned char *segid_n = segid + cap;                   // [cap] the same for the next level
 
   const int32_t *src = P.stg[T.sel];
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
@@ -511,6 +529,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     sid[q] = src[dim * P.S + T.base + start0 + q];
     perm0[q] = (uint16_t)q;
     perm1[q] = (uint16_t)q;   // any slot a level leaves unwritten still names a record
+    segid[q] = 0;
   }
   __syncthreads();
 
@@ -538,10 +557,6 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         s_done[s] = 0;
         s_fnd[s] = 0;
         s_cnt[s] = 0;
-      }
-      for (int q = threadIdx.x; q < m0; q += blockDim.x) {
-        int64_t a, z;
-        segid[q] = (unsigned char)seg_of(m0, u, q, a, z);
       }
       __syncthreads();
       int shift = kKeyBits;
@@ -672,15 +687,18 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             int rrank = (q - s_st[s]) - lrank;
             bool left = (flags >> j) & 1;
             int dst = left ? s_st[s] + lrank : s_st[s] + half + rrank;
-            if (left ? (lrank < 0 || lrank >= half) : (rrank < 0 || rrank >= s_sz[s] - half))
+            if (left ? (lrank < 0 || lrank >= half) : (rrank < 0 || rrank >= s_sz[s] - half)) {
               atomicOr(P.err, kErrPartition);
-            else
+            } else {
               nxt[dst] = cur[q];
+              segid_n[dst] = (unsigned char)(2 * s + (left ? 0 : 1));   // child segment
+            }
             run += (flags >> j) & 1;
           }
         }
       }
       __syncthreads();
+      unsigned char *ts = segid; segid = segid_n; segid_n = ts;
     } else {
       // ---------------- warp mode: rank counting per segment --------------
       for (int s = warp; s < nseg; s += nwarps) {
@@ -832,7 +850,7 @@ __global__ void k_sort_small(int32_t *ids, int n, int np2) {
 constexpr size_t kSubtreeSmemMax = 212 * 1024;   // dynamic part; static part ~6 KB
 
 size_t subtree_smem_bytes(int dim, int cap) {
-  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + (size_t)cap;
+  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap;
 }
 
 NodeOut node_out(Tree *t) {

@@ -89,10 +89,11 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
   int32_t id = pending ? list[i] : 0;
   const int32_t *xq = F.idtab + (int64_t)id * F.dim;
   int32_t path[kMaxLevel + 2];
-  for (int ti = 0; ti < F.ntrees; ++ti) {
-    const TreeView &T = F.tree[ti];
-    bool found = false;
-    if (pending) {
+  // all bloom probes first: independent 32-byte loads, one per tree
+  uint64_t maybe_mask = 0;
+  if (pending) {
+    for (int ti = 0; ti < F.ntrees; ++ti) {
+      const TreeView &T = F.tree[ti];
       bool maybe = true;
       if (T.bloom) {
         int64_t blk;
@@ -104,7 +105,14 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
 #pragma unroll
         for (int w = 0; w < 8; ++w) maybe = maybe && (wv[w] & bloom_word_bit(bits, w));
       }
-      if (maybe) {
+      maybe_mask |= (uint64_t)maybe << ti;
+    }
+  }
+  for (int ti = 0; ti < F.ntrees; ++ti) {
+    const TreeView &T = F.tree[ti];
+    bool found = false;
+    if (pending) {
+      if ((maybe_mask >> ti) & 1) {
         int v = 0, depth = 0;
         Node nd;
         bool ok = true;

@@ -576,9 +576,24 @@ int bdl_erase(bdl_forest *f, const int32_t *ids, int64_t n, int64_t *out_n, bdl_
     launch_bloom_build(t, f->dim, f->cfg.hash_seed, s);
   }
   if (st) { dev_free(f, list, (size_t)n * 4, s); return st; }
-  // 3. probe, descend, tombstone (Alg. 2 per tree, all trees in one launch)
+  // 3. probe, descend, tombstone (Alg. 2 per tree, all trees in one launch);
+  //    large batches descend in spatial order so neighbouring threads share paths
   ForestView fv = forest_view(f);
-  launch_erase_locate(fv, f->cfg.hash_seed, (const int32_t *)list, ne, s);
+  const int32_t *order = (const int32_t *)list;
+  void *sorted = nullptr;
+  size_t sorted_bytes = 0;
+  if (ne >= kSortMinQueries) {
+    sorted_bytes = a256((size_t)ne * 4) + query_sort_bytes(ne, f->dim);
+    if (dev_alloc(f, &sorted, sorted_bytes, s) == BDL_OK) {
+      launch_point_sort(f->idtab, (const int32_t *)list, ne, f->dim,
+                        (char *)sorted + a256((size_t)ne * 4), (int32_t *)sorted, s);
+      order = (const int32_t *)sorted;
+    } else {
+      sorted = nullptr;   // same result in input order
+    }
+  }
+  launch_erase_locate(fv, f->cfg.hash_seed, order, ne, s);
+  if (sorted) dev_free(f, sorted, sorted_bytes, s);
   for (int i = 0; i < kMaxLevel; ++i)   // live counts changed: refresh the k-NN records
     if (f->trees[i]) launch_pack_lives(f->trees[i], f->dim, s);
   // 4. the buffer

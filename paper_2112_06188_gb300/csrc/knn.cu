@@ -94,7 +94,7 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
 }
 
 template <int D, bool STATS>
-__global__ void __launch_bounds__(kKnnThreads, 10) k_knn(const ForestView F, const int32_t *qs,
+__global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, const int32_t *qs,
                                                          const int32_t *perm, int64_t m, int k,
                                                          int32_t *out_ids, int64_t *out_d2,
                                                          unsigned long long *stats) {
@@ -318,9 +318,16 @@ __device__ __forceinline__ uint32_t morton_key(const int32_t *q, int dim, int B)
   return key;
 }
 
-__global__ void k_qkey_hist(const int32_t *q, int64_t m, int dim, int B, uint32_t *hist) {
+// Point i's coordinates: row i of `coords`, or row ids[i] when ids is given.
+__device__ __forceinline__ const int32_t *point_row(const int32_t *coords, const int32_t *ids,
+                                                    int64_t i, int dim) {
+  return coords + (ids ? (int64_t)ids[i] : i) * dim;
+}
+
+__global__ void k_qkey_hist(const int32_t *coords, const int32_t *ids, int64_t m, int dim, int B,
+                            uint32_t *hist) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) atomicAdd(&hist[morton_key(q + i * dim, dim, B)], 1u);
+  if (i < m) atomicAdd(&hist[morton_key(point_row(coords, ids, i, dim), dim, B)], 1u);
 }
 
 __device__ uint32_t block_scan_u32(uint32_t v, uint32_t *total) {
@@ -382,13 +389,14 @@ __global__ void k_scan_top(uint32_t *bsum, int64_t nb) {
   }
 }
 
-__global__ void k_qscatter(const int32_t *q, int64_t m, int dim, int B, uint32_t *offs,
-                           const uint32_t *bsum, int32_t *perm) {
+// out[pos] = i (query order) or ids[i] (the ids themselves, reordered)
+__global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m, int dim, int B,
+                           uint32_t *offs, const uint32_t *bsum, int32_t *out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  uint32_t key = morton_key(q + i * dim, dim, B);
+  uint32_t key = morton_key(point_row(coords, ids, i, dim), dim, B);
   uint32_t pos = bsum[key / kScanPer] + atomicAdd(&offs[key], 1u);
-  if (pos < m) perm[pos] = (int32_t)i;
+  if (pos < m) out[pos] = ids ? ids[i] : (int32_t)i;
 }
 
 }  // namespace
@@ -439,8 +447,8 @@ size_t query_sort_bytes(int64_t m, int dim) {
   return ((size_t)m * 4 + 255) / 256 * 256 + (size_t)nbins * 4 + 256 + (size_t)nb * 4 + 256;
 }
 
-void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,
-                       cudaStream_t s) {
+void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int dim,
+                       void *scratch, int32_t *out, cudaStream_t s) {
   const int B = morton_bits_per_dim(dim);
   const int64_t nbins = (int64_t)1 << (B * dim);
   const int64_t nb = (nbins + kScanPer - 1) / kScanPer;   // <= 256
@@ -448,10 +456,15 @@ void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int3
   uint32_t *bsum = (uint32_t *)((char *)scratch + ((size_t)nbins * 4 + 255) / 256 * 256);
   cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s);
   const unsigned g = (unsigned)((m + 255) / 256);
-  { KScope ks_(kK_qsort, s); k_qkey_hist<<<g, 256, 0, s>>>(q, m, dim, B, hist); }
+  { KScope ks_(kK_qsort, s); k_qkey_hist<<<g, 256, 0, s>>>(coords, ids, m, dim, B, hist); }
   { KScope ks_(kK_qsort, s); k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum); }
   { KScope ks_(kK_qsort, s); k_scan_top<<<1, 1024, 0, s>>>(bsum, nb); }
-  { KScope ks_(kK_qsort, s); k_qscatter<<<g, 256, 0, s>>>(q, m, dim, B, hist, bsum, perm); }
+  { KScope ks_(kK_qsort, s); k_qscatter<<<g, 256, 0, s>>>(coords, ids, m, dim, B, hist, bsum, out); }
+}
+
+void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,
+                       cudaStream_t s) {
+  launch_point_sort(q, nullptr, m, dim, scratch, perm, s);
 }
 
 }  // namespace bdl
