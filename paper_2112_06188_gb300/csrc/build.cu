@@ -393,6 +393,10 @@ __device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, 
 __global__ void k_level_partition(const LvParams P) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long cbase[4];
+  __shared__ int32_t stage[4096];          // one array of the tile, in output order
+  __shared__ int64_t gdst[4];              // global start of each class's run
+  __shared__ int coff[5];                  // start of each class's run in `stage`
+  __shared__ int cok[4];
   int b = blockIdx.x;
   const LvTree &T = P.tr[find_tree_by_tile(P, b)];
   TileSegs g = tile_segs(P, T, b);
@@ -430,6 +434,7 @@ __global__ void k_level_partition(const LvParams P) {
   if (threadIdx.x == 0) {
     unsigned long long acc = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { unsigned long long v = wsum[w]; wsum[w] = acc; acc += v; }
+    coff[0] = 0;
     for (int c = 0; c < 4; ++c) {
       unsigned long long tot = (acc >> (16 * c)) & 0xffff;
       cbase[c] = 0;
@@ -438,35 +443,44 @@ __global__ void k_level_partition(const LvParams P) {
         unsigned long long *cur = (c & 1) ? (unsigned long long *)&S.rcur : (unsigned long long *)&S.lcur;
         cbase[c] = atomicAdd(cur, tot);
       }
+      const int64_t st = (c >> 1) ? g.st1 : g.st0;
+      const int64_t sz = (c >> 1) ? g.sz1 : g.sz0;
+      const int64_t off = (c & 1) ? ((sz + 1) >> 1) : 0;
+      const int64_t lim = (c & 1) ? sz - ((sz + 1) >> 1) : ((sz + 1) >> 1);
+      gdst[c] = st + off + (int64_t)cbase[c];
+      cok[c] = (int64_t)(cbase[c] + tot) <= lim;   // else the median did not halve the segment
+      if (!cok[c]) atomicOr(P.err, kErrPartition);
+      coff[c + 1] = coff[c] + (int)tot;
     }
   }
   __syncthreads();
-  unsigned long long ex = inc - mine + wsum[warp];
-  int32_t dstp[kItems];
+  const unsigned long long ex = inc - mine + wsum[warp];
+  int spos[kItems];                 // position of each item in the tile's output order
   int run[4] = {0, 0, 0, 0};
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    int c = cls[j];
-    dstp[j] = -1;
+    const int c = cls[j];
+    spos[j] = -1;
     if (c < 0) continue;
-    int64_t st = (c >> 1) ? g.st1 : g.st0;
-    int64_t sz = (c >> 1) ? g.sz1 : g.sz0;
-    int64_t off = (c & 1) ? ((sz + 1) >> 1) : 0;
-    int64_t rel = off + (int64_t)cbase[c] + (int64_t)((ex >> (16 * c)) & 0xffff) + run[c];
+    spos[j] = coff[c] + (int)((ex >> (16 * c)) & 0xffff) + run[c];
     run[c]++;
-    int64_t lim = (c & 1) ? sz : ((sz + 1) >> 1);
-    if (rel >= lim) {               // the median did not split the segment in half
-      atomicOr(P.err, kErrPartition);
-      continue;
-    }
-    dstp[j] = (int32_t)(st + rel);
   }
+  // each array: scatter into shared memory, then write every class's run
+  // with consecutive threads on consecutive addresses
+  const int ntile = coff[4];
   for (int c = 0; c <= P.dim; ++c) {
     int32_t v[kItems];
     load8(P.src + c * P.S + T.base, pb, g.p1, v);
-    int32_t *y = P.dst + c * P.S + T.base;
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
-      if (dstp[j] >= 0) y[dstp[j]] = v[j];
+      if (spos[j] >= 0) stage[spos[j]] = v[j];
+    __syncthreads();
+    int32_t *y = P.dst + c * P.S + T.base;
+    for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
+      const int k = (i >= coff[1]) + (i >= coff[2]) + (i >= coff[3]);
+      if (cok[k]) y[gdst[k] + (i - coff[k])] = stage[i];
+    }
+    __syncthreads();
   }
 }
 

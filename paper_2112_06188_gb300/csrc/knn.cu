@@ -85,8 +85,9 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
 #pragma unroll
   for (int c = 0; c < (D ? D : kMaxDim); ++c) {
     if (c < dd) {
-      int32_t lo = box[c], hi = box[dd + c], x = q[c];
-      float g = (float)(x < lo ? lo - x : (x > hi ? x - hi : 0));
+      const int32_t x = q[c];
+      // at most one of the two gaps is positive
+      const float g = (float)(max(box[c] - x, 0) + max(x - box[dd + c], 0));
       s = fmaf(g, g, s);
     }
   }
@@ -189,9 +190,27 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
         atomicOr(F.err, code >= ninternal ? kErrChild : kErrStack);
       } else {
         const int32_t *r = T.pk + (int64_t)code * rec;
-        const int4 hdr = *reinterpret_cast<const int4 *>(r);
-        const float ml = hdr.z > 0 ? box_mindist_lb<D>(q, r + 4, dim) : kInf;
-        const float mr = hdr.w > 0 ? box_mindist_lb<D>(q, r + 4 + 2 * dim, dim) : kInf;
+        int4 hdr;
+        float ml, mr;
+        if (D) {
+          // the whole 32-byte-aligned record in 16-byte loads
+          int32_t rr[D ? packed_node_ints(D) : 4];
+#pragma unroll
+          for (int c4 = 0; c4 < (D ? packed_node_ints(D) : 4); c4 += 4) {
+            const int4 v = *reinterpret_cast<const int4 *>(r + c4);
+            rr[c4] = v.x;
+            rr[c4 + 1] = v.y;
+            rr[c4 + 2] = v.z;
+            rr[c4 + 3] = v.w;
+          }
+          hdr = make_int4(rr[0], rr[1], rr[2], rr[3]);
+          ml = hdr.z > 0 ? box_mindist_lb<D>(q, rr + 4, dim) : kInf;
+          mr = hdr.w > 0 ? box_mindist_lb<D>(q, rr + 4 + 2 * (D ? D : 1), dim) : kInf;
+        } else {
+          hdr = *reinterpret_cast<const int4 *>(r);
+          ml = hdr.z > 0 ? box_mindist_lb<D>(q, r + 4, dim) : kInf;
+          mr = hdr.w > 0 ? box_mindist_lb<D>(q, r + 4 + 2 * dim, dim) : kInf;
+        }
         const bool lfirst = ml <= mr;
         const int vn = lfirst ? hdr.x : hdr.y, vf = lfirst ? hdr.y : hdr.x;
         const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
