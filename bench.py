@@ -13,6 +13,21 @@ L2 is flushed (256 MB write) between steps, outside the timed events.
 
 --impl reference times the CPU oracle (oracle/) as it stands on the host
 cores, on a 1/10-scale sample of the same step.
+
+--workload forests runs the batched-forests workload instead: 512
+independent 2-D/3-D forests of log-uniform sizes in [1k, 200k]; one step gives
+every forest an insert batch of 5-20% of its size, a delete batch of 2-10% of
+its live ids and k = 8 queries (1-5k per forest).  The step runs once through
+the batched entry points (one call per operation for all forests) and once
+as per-forest calls on an identical second set of forests; both results must
+be identical, and both times are reported.
+
+--workload serve runs the serving workload: one resident 5-D forest growing
+from 1M to 50M points under a Poisson stream of insert (1k-1M points), erase
+(1k-500k live ids) and k-NN (1-100k queries, k in {1, 5, 10}) requests in a
+4:1:5 mix, served by the library's continuous-batching server under a fixed
+device-memory budget, and again by its one-request-at-a-time mode; p50/p99
+latency per request type and sustained updates/s and queries/s are reported.
 """
 import argparse
 import json
@@ -39,12 +54,19 @@ def parse():
     ap.add_argument("--n0", type=int, default=10_000_000)
     ap.add_argument("--batch", type=int, default=1_000_000)
     ap.add_argument("--queries", type=int, default=1_000_000)
-    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--k", type=int, default=None, help="default 10 (forest10m), 8 (forests)")
     ap.add_argument("--dim", type=int, default=3)
     ap.add_argument("--leaf", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="forest10m", choices=["forest10m", "forests", "serve"])
+    ap.add_argument("--rate", type=float, default=1000.0, help="serve: requests per second")
+    ap.add_argument("--n-final", type=int, default=50_000_000, help="serve: stop at this many points")
+    ap.add_argument("--forests", type=int, default=512)
+    a = ap.parse_args()
+    if a.k is None:
+        a.k = 8 if a.workload == "forests" else 10
+    return a
 
 
 def workload_config(a, n_gpus):
@@ -281,6 +303,407 @@ def run_ours(a, rank, world, dist):
     return res
 
 
+# ---------------------------------------------------------------------------
+# batched forests
+# ---------------------------------------------------------------------------
+
+def forests_config(a, n_gpus):
+    return {"workload": "%d independent forests, dim 2 or 3, sizes log-uniform in [1000, 200000], "
+                        "uniform int32 points; per step per forest insert 5-20%% of its size, erase "
+                        "2-10%% of its live ids, k=%d NN for 1000-5000 live-set queries" % (a.forests, a.k),
+            "forests": a.forests, "k": a.k, "leaf_size": 16, "buffer_size": 1024,
+            "l2": "flushed between steps (256 MB write), inputs resident in HBM",
+            "parallelism": "one independent set of forests per GPU" if n_gpus > 1 else "single GPU"}
+
+
+class FlatInputs:
+    """One step's per-forest inputs packed into flat device tensors, with the
+    pointer and size arrays the batched C entry points take."""
+
+    def __init__(self, step, k, dev):
+        import ctypes
+        import torch
+        self.n_ins = [len(i) for i, _, _ in step]
+        self.n_era = [len(e) for _, e, _ in step]
+        self.m = [len(q) for _, _, q in step]
+        self.ins = torch.from_numpy(np.concatenate([i.ravel() for i, _, _ in step])).to(dev)
+        self.era = torch.from_numpy(np.concatenate([e for _, e, _ in step])).to(dev)
+        self.q = torch.from_numpy(np.concatenate([q.ravel() for _, _, q in step])).to(dev)
+        M = sum(self.m)
+        self.oi = torch.empty(M * k, dtype=torch.int32, device=dev)
+        self.od = torch.empty(M * k, dtype=torch.int64, device=dev)
+
+        def ptrs(t, counts, width):
+            base, es, out, o = t.data_ptr(), t.element_size(), [], 0
+            for c, w in zip(counts, width):
+                out.append(base + o * es if c else None)
+                o += c * w
+            return out
+
+        dims = [i.shape[1] for i, _, _ in step]
+        self.p_ins = ptrs(self.ins, self.n_ins, dims)
+        self.p_era = ptrs(self.era, self.n_era, [1] * len(step))
+        self.p_q = ptrs(self.q, self.m, dims)
+        self.p_oi = ptrs(self.oi, self.m, [k] * len(step))
+        self.p_od = ptrs(self.od, self.m, [k] * len(step))
+        A = lambda xs, T=ctypes.c_void_p: (T * len(xs))(*xs)
+        self.c_ins, self.c_era, self.c_q = A(self.p_ins), A(self.p_era), A(self.p_q)
+        self.c_oi, self.c_od = A(self.p_oi), A(self.p_od)
+        self.c_nins, self.c_nera, self.c_m = (A(self.n_ins, ctypes.c_int64), A(self.n_era, ctypes.c_int64),
+                                              A(self.m, ctypes.c_int64))
+        self.c_null = A([None] * len(step))
+        self.c_erased = (ctypes.c_int64 * len(step))()
+        self.ops = sum(self.n_ins) + sum(self.n_era) + M
+
+
+def run_forests(a, rank, world, dist):
+    import ctypes
+    import torch
+    from paper_2112_06188_gb300 import capi, inputs
+    from paper_2112_06188_gb300.forest import Forest
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    L = capi.load()
+    stream = torch.cuda.Stream(dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    W = inputs.ForestsWorkload(nf=a.forests, seed=4 + 17 * rank)
+    nsteps = a.warmup + a.steps
+    steps = [W.step() for _ in range(nsteps)]
+    nf = a.forests
+    with torch.cuda.stream(stream):
+        A = [Forest(d, stream=stream, device=dev) for d in W.dims]
+        B = [Forest(d, stream=stream, device=dev) for d in W.dims]
+        hA = (ctypes.c_void_p * nf)(*[f._h for f in A])
+        hB = [f._h for f in B]
+        init = FlatInputs([(p, np.zeros(0, np.int32), np.zeros((0, p.shape[1]), np.int32))
+                           for p in W.initial], a.k, dev)
+        flat = [FlatInputs(st, a.k, dev) for st in steps]
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+    capi.check(L.bdl_insert_batch(hA, nf, init.c_ins, init.c_nins, init.c_null, sh), "bdl_insert_batch")
+    for i in range(nf):
+        capi.check(L.bdl_insert(hB[i], init.p_ins[i], init.n_ins[i], None, sh), "bdl_insert")
+    stream.synchronize()
+    del init
+
+    def batched(x):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        capi.check(L.bdl_insert_batch(hA, nf, x.c_ins, x.c_nins, x.c_null, sh), "bdl_insert_batch")
+        ev[1].record(stream)
+        capi.check(L.bdl_erase_batch(hA, nf, x.c_era, x.c_nera, x.c_erased, sh), "bdl_erase_batch")
+        ev[2].record(stream)
+        capi.check(L.bdl_knn_batch(hA, nf, x.c_q, x.c_m, a.k, x.c_oi, x.c_od, sh), "bdl_knn_batch")
+        ev[3].record(stream)
+        return ev
+
+    def per_forest(x, oi, od):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        n = ctypes.c_int64(0)
+        ev[0].record(stream)
+        for i in range(nf):
+            capi.check(L.bdl_insert(hB[i], x.p_ins[i], x.n_ins[i], None, sh), "bdl_insert")
+        ev[1].record(stream)
+        for i in range(nf):
+            capi.check(L.bdl_erase(hB[i], x.p_era[i], x.n_era[i], ctypes.byref(n), sh), "bdl_erase")
+        ev[2].record(stream)
+        for i in range(nf):
+            capi.check(L.bdl_knn(hB[i], x.p_q[i], x.m[i], a.k, oi[i], od[i], sh), "bdl_knn")
+        ev[3].record(stream)
+        return ev
+
+    # per-forest outputs go to their own buffers so that the arms can be compared
+    outB = []
+    for x in flat:
+        oi = torch.empty_like(x.oi)
+        od = torch.empty_like(x.od)
+        off, pi, pd = 0, [], []
+        for m in x.m:
+            pi.append(oi.data_ptr() + off * a.k * 4 if m else None)
+            pd.append(od.data_ptr() + off * a.k * 8 if m else None)
+            off += m
+        outB.append((oi, od, pi, pd))
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    for i in range(a.warmup):
+        flush_l2()
+        batched(flat[i])
+        flush_l2()
+        per_forest(flat[i], outB[i][2], outB[i][3])
+    stream.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    capi.bdl_profile(True)
+    l0 = capi.bdl_launch_count()
+    evA = []
+    for i in range(a.warmup, nsteps):
+        flush_l2()
+        evA.append(batched(flat[i]))
+    torch.cuda.synchronize(dev)
+    launchesA = capi.bdl_launch_count() - l0
+    prof = capi.bdl_profile_read()
+    capi.bdl_profile(False)
+    l0 = capi.bdl_launch_count()
+    evB = []
+    for i in range(a.warmup, nsteps):
+        flush_l2()
+        evB.append(per_forest(flat[i], outB[i][2], outB[i][3]))
+    torch.cuda.synchronize(dev)
+    launchesB = capi.bdl_launch_count() - l0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+
+    def phases(evs):
+        t = [[e[j].elapsed_time(e[j + 1]) for e in evs] for j in range(3)]
+        ms = {"insert": sum(t[0]) / len(evs), "erase": sum(t[1]) / len(evs), "knn": sum(t[2]) / len(evs)}
+        ms["step"] = ms["insert"] + ms["erase"] + ms["knn"]
+        return ms
+
+    msA, msB = phases(evA), phases(evB)
+    if dist:
+        msA, msB = max_over_ranks(msA, dist, dev), max_over_ranks(msB, dist, dev)
+    identical = all(torch.equal(flat[i].oi, outB[i][0]) and torch.equal(flat[i].od, outB[i][1])
+                    for i in range(a.warmup, nsteps))
+    identical = identical and all(f.size() == g.size() and f.tree_mask() == g.tree_mask()
+                                  for f, g in zip(A, B))
+    x = flat[-1]
+    res = {"msA": msA, "msB": msB, "launchesA": launchesA // a.steps, "launchesB": launchesB // a.steps,
+           "prof": prof, "clocks": clk, "identical": bool(identical),
+           "ops": sum(flat[i].ops for i in range(a.warmup, nsteps)) / a.steps,
+           "inserted": sum(x.n_ins), "erased": sum(x.n_era), "queries": sum(x.m),
+           "points": int(sum(f.size() for f in A))}
+    for f in A + B:
+        f.close()
+    return res
+
+
+def forests_cpu_sample(a, nsample=16):
+    """The oracle on the first `nsample` forests of the same workload, one step."""
+    from oracle.oracle import OracleForest
+    from paper_2112_06188_gb300 import inputs
+    W = inputs.ForestsWorkload(nf=a.forests, seed=4)
+    step = W.step()
+    os_ = []
+    for i in range(nsample):
+        o = OracleForest(W.dims[i], leaf_size=16, buffer_size=1024)
+        o.insert(W.initial[i])
+        os_.append(o)
+    t0 = time.perf_counter()
+    ops = 0
+    for i in range(nsample):
+        ins, era, q = step[i]
+        os_[i].insert(ins)
+        os_[i].erase(era)
+        os_[i].knn(q, a.k)
+        ops += len(ins) + len(era) + len(q)
+    dt = time.perf_counter() - t0
+    sample = "one step on the first %d of the %d forests, one host core" % (nsample, a.forests)
+    return ops / dt, sample
+
+
+def report_forests(a, res, world):
+    msA, msB = res["msA"], res["msB"]
+    value = res["ops"] * world / (msA["step"] * 1e-3)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "ops/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(msA["step"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": forests_config(a, world),
+        "phase_ms": {k: round(v, 3) for k, v in msA.items()},
+        "per_forest_calls": {"value": round(res["ops"] * world / (msB["step"] * 1e-3), 1), "unit": "ops/s",
+                             "phase_ms": {k: round(v, 3) for k, v in msB.items()},
+                             "gpu_launches": res["launchesB"]},
+        "speedup_vs_per_forest": round(msB["step"] / msA["step"], 2),
+        "identical_results": res["identical"],
+        "per_step": {"inserted": res["inserted"], "erased": res["erased"], "queries": res["queries"],
+                     "live_points_after": res["points"]},
+        "gpu_launches": res["launchesA"],
+        "kernel_ms": {k: [round(v[0] / a.steps, 4), v[1] // a.steps] for k, v in
+                      sorted(res["prof"].items(), key=lambda kv: -kv[1][0])},
+        "clocks": res["clocks"],
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        v, sample = forests_cpu_sample(a)
+        out["cpu_baseline"] = {"value": round(v, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
+                               "sample": sample}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+SERVE_HBM_BUDGET = 24 << 30       # the forest's own device memory
+SERVE_STAGING = 2 << 30           # requests' buffers in flight
+
+
+def serve_config(a):
+    return {"workload": "serving: one 5-D forest growing from 1M to %d uniform int32 points under "
+                        "Poisson arrivals (%.0f requests/s) of inserts (1k-1M points), erases (1k-500k "
+                        "live ids) and k-NN (1-100k queries, k in {1,5,10}) in a 4:1:5 mix, sizes "
+                        "log-uniform" % (a.n_final, a.rate),
+            "dim": 5, "n0": 1_000_000, "n_final": a.n_final, "rate_per_s": a.rate,
+            "hbm_budget_bytes": SERVE_HBM_BUDGET, "staging_budget_bytes": SERVE_STAGING,
+            "leaf_size": 16, "buffer_size": 1024, "l2": "not flushed (requests stream continuously)",
+            "parallelism": "single GPU"}
+
+
+def serve_once(a, reqs, initial, serial, paced, dev):
+    """Run the request list through a server; returns per-request results,
+    the makespan (s) and the number of device groups."""
+    import threading
+    import torch
+    from paper_2112_06188_gb300.forest import Forest
+    from paper_2112_06188_gb300.serve import Server
+    f = Forest(5, leaf_size=16, buffer_size=1024, hbm_budget_bytes=SERVE_HBM_BUDGET, device=dev)
+    f.insert(torch.from_numpy(initial).to(dev))
+    torch.cuda.synchronize(dev)
+    srv = Server(f, serial=serial, staging_budget_bytes=SERVE_STAGING, max_inflight=256)
+    tickets = [None] * len(reqs)
+    lateness = []
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, (t, kind, payload, k) in enumerate(reqs):
+            if paced:
+                dt = t - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                lateness.append(time.perf_counter() - t0 - t)
+            if kind == "insert":
+                tickets[i] = srv.insert(payload)
+            elif kind == "erase":
+                tickets[i] = srv.erase(payload)
+            else:
+                tickets[i] = srv.knn(payload, k)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    res = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    groups = srv.groups()
+    srv.close()
+    live = f.size()
+    f.close()
+    return res, makespan, groups, live, lateness
+
+
+def latency_summary(reqs, res):
+    out = {}
+    for kind in ("insert", "erase", "knn"):
+        lat = [r["t_done_ms"] - r["t_submit_ms"] for (_, kd, _, _), r in zip(reqs, res) if kd == kind]
+        if lat:
+            out[kind] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat, 99)), 3), "count": len(lat)}
+    return out
+
+
+def run_serve(a):
+    import torch
+    from paper_2112_06188_gb300 import capi, inputs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    capi.load()
+    W = inputs.ServeWorkload(dim=5, n0=1_000_000, n_final=a.n_final, rate=a.rate, seed=5)
+    reqs = [(t, kind, torch.from_numpy(np.ascontiguousarray(p)).pin_memory(), k)
+            for t, kind, p, k in W.requests()]
+    initial = W.initial
+    n_ins = sum(p.shape[0] for _, kd, p, _ in reqs if kd == "insert")
+    n_era = sum(p.shape[0] for _, kd, p, _ in reqs if kd == "erase")
+    n_q = sum(p.shape[0] for _, kd, p, _ in reqs if kd == "knn")
+    # warm-up: a short prefix, not timed
+    serve_once(a, reqs[:20], initial, serial=False, paced=False, dev=dev)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    l0 = capi.bdl_launch_count()
+    res, span, groups, live, late = serve_once(a, reqs, initial, serial=False, paced=True, dev=dev)
+    launches = capi.bdl_launch_count() - l0
+    clk = clocks.stop()
+    res_s, span_s, groups_s, live_s, _ = serve_once(a, reqs, initial, serial=True, paced=True, dev=dev)
+    # saturated: every request queued at once (sustained throughput)
+    res_b, span_b, groups_b, _, _ = serve_once(a, reqs, initial, serial=False, paced=False, dev=dev)
+    res_bs, span_bs, _, _, _ = serve_once(a, reqs, initial, serial=True, paced=False, dev=dev)
+
+    def same(r1, r2):
+        for (_, kind, _, _), x, y in zip(reqs, r1, r2):
+            if x["status"] != y["status"] or x["n_done"] != y["n_done"]:
+                return False
+            if kind == "knn" and not (torch.equal(x["ids"], y["ids"]) and torch.equal(x["d2"], y["d2"])):
+                return False
+            if kind == "insert" and not torch.equal(x["ids"], y["ids"]):
+                return False
+        return True
+
+    identical = same(res, res_s) and same(res, res_b) and same(res, res_bs)
+    ok = all(r["status"] == 0 for r in res)
+    ops = n_ins + n_era + n_q
+    value = ops / span_b
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "ops/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": round(span_b * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": serve_config(a),
+        "requests": {"total": len(reqs), "insert": sum(1 for r in reqs if r[1] == "insert"),
+                     "erase": sum(1 for r in reqs if r[1] == "erase"),
+                     "knn": sum(1 for r in reqs if r[1] == "knn"),
+                     "points_inserted": n_ins, "ids_erased": n_era, "queries": n_q,
+                     "live_points_after": live},
+        "sustained": {"updates_per_s": round((n_ins + n_era) / span_b, 1), "queries_per_s": round(n_q / span_b, 1),
+                      "makespan_s": round(span_b, 4), "device_groups": groups_b,
+                      "one_at_a_time": {"updates_per_s": round((n_ins + n_era) / span_bs, 1),
+                                        "queries_per_s": round(n_q / span_bs, 1),
+                                        "makespan_s": round(span_bs, 4)}},
+        "latency": {"continuous_batching": latency_summary(reqs, res),
+                    "one_at_a_time": latency_summary(reqs, res_s),
+                    "offered_span_s": round(reqs[-1][0], 4), "served_span_s": round(span, 4),
+                    "served_span_one_at_a_time_s": round(span_s, 4),
+                    "device_groups": groups, "device_groups_one_at_a_time": groups_s,
+                    "submit_lateness_p99_ms": round(float(np.percentile(late, 99)) * 1e3, 3) if late else None},
+        "identical_results": bool(identical), "all_ok": bool(ok),
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        out["cpu_baseline"] = serve_cpu_sample(a)
+    return out
+
+
+def serve_cpu_sample(a, n_req=40):
+    """The oracle replaying the first requests of the same stream on a forest
+    of 1/10 the initial size (requests at 1/10 scale), one host core."""
+    from oracle.oracle import OracleForest
+    from paper_2112_06188_gb300 import inputs
+    W = inputs.ServeWorkload(dim=5, n0=100_000, n_final=10 ** 9, rate=a.rate, seed=5,
+                             ins=(100, 100_000), dele=(100, 50_000), knn=(1, 10_000), max_requests=n_req)
+    o = OracleForest(5, leaf_size=16, buffer_size=1024)
+    o.insert(W.initial)
+    ops, t = 0, 0.0
+    for _, kind, p, k in W.requests():
+        t0 = time.perf_counter()
+        if kind == "insert":
+            o.insert(p)
+        elif kind == "erase":
+            o.erase(p)
+        else:
+            o.knn(p, k)
+        t += time.perf_counter() - t0
+        ops += len(p)
+    return {"value": round(ops / t, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d requests of the same stream at 1/10 scale (forest of 100k points), "
+                      "one host core" % n_req}
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when the summary is missing or the kernel source changed since the capture."""
@@ -359,6 +782,31 @@ def oracle_sample(a, nsteps, seed=2):
 def run_reference(a, rank):
     if rank != 0:
         return
+    if a.workload == "serve":
+        cb = serve_cpu_sample(a)
+        out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ops/s",
+               "n_gpus": a.gpus, "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+               "config": serve_config(a), "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": "ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+    if a.workload == "forests":
+        vals = []
+        for _ in range(max(1, a.steps)):
+            v, sample = forests_cpu_sample(a)
+            vals.append(v)
+        value = statistics.median(vals)
+        out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ops/s",
+               "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": None,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+               "data": "synthetic", "config": forests_config(a, a.gpus),
+               "cpu_baseline": {"value": round(value, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": round(value, 1), "unit": "ops/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
     W = a.warmup
     times, ops, sample = oracle_sample(a, W + a.steps)
     t = times[W:]
@@ -389,6 +837,19 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
+    if a.workload == "serve":
+        if rank == 0:
+            print(json.dumps(run_serve(a)), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if a.workload == "forests":
+        res = run_forests(a, rank, world, dist)
+        if rank == 0:
+            print(json.dumps(report_forests(a, res, world)), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     res = run_ours(a, rank, world, dist)
     if rank != 0:
         if dist:

@@ -125,6 +125,119 @@ int bdl_knn(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_
 int bdl_knn_noalloc(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_ids_dev,
                     int64_t *out_d2_dev, bdl_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Batched forests: one call runs the same operation on nf independent
+ * forests (nf >= 0) of possibly different sizes, sharing kernel launches and
+ * host synchronisations instead of issuing nf separate calls.  Forest i gets
+ * exactly the result the single-forest call on it would give.  The arrays
+ * (forests, per-forest pointers, sizes) are host arrays of length nf; the
+ * pointers in them are device pointers as in the single-forest calls.  All
+ * forests must live on the same device and (insert, erase) be distinct.
+ * Forests of different dimensions may be mixed (one launch per dimension).
+ * (The paper treats one forest; batching many is an interface choice of
+ * this library.)
+ * --------------------------------------------------------------------- */
+
+/* bdl_insert on every forest i with pts_dev[i][n[i]][dim_i] and
+ * out_ids_dev[i] (NULL entries allowed).  All or nothing: on BDL_EINVAL (a
+ * coordinate off the grid anywhere, a bad size, a repeated forest) or
+ * BDL_ENOMEM no forest changes.  Synchronises `stream` once. */
+int bdl_insert_batch(bdl_forest *const *forests, int nf, const int32_t *const *pts_dev,
+                     const int64_t *n, int32_t *const *out_ids_dev, bdl_stream_t stream);
+
+/* bdl_erase on every forest i with ids_dev[i][n[i]]; out_n_erased_host[i]
+ * (array may be NULL) receives forest i's count.  Argument errors change no
+ * forest; a failed reinsertion behaves as in bdl_erase for the forests it
+ * hits and the call returns the first such status. */
+int bdl_erase_batch(bdl_forest *const *forests, int nf, const int32_t *const *ids_dev,
+                    const int64_t *n, int64_t *out_n_erased_host, bdl_stream_t stream);
+
+/* bdl_knn on every forest i with q_dev[i][m[i]][dim_i] into
+ * out_ids_dev[i][m[i]][k] / out_d2_dev[i][m[i]][k]; one k for all.  A forest
+ * may appear more than once. */
+int bdl_knn_batch(bdl_forest *const *forests, int nf, const int32_t *const *q_dev, const int64_t *m,
+                  int k, int32_t *const *out_ids_dev, int64_t *const *out_d2_dev,
+                  bdl_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: a request server that keeps one forest resident and takes
+ * insert / erase / k-NN requests from host memory as they arrive.
+ * Requests take effect in submission order with exactly the results the
+ * plain calls give when issued one by one in that order; the server batches
+ * them for the device as they arrive (continuous batching):
+ *  - consecutive k-NN requests with the same k go out as one k-NN launch;
+ *  - consecutive inserts go out as one Insert_L of their concatenated points
+ *    (same ids, same live set);
+ *  - erases run one by one.
+ * A request is admitted -- its device buffers allocated and its input
+ * copied in -- only while fewer than max_inflight requests are in flight and
+ * their buffers fit in staging_budget_bytes; inputs of later requests and
+ * outputs of earlier ones are copied while the current group computes (use
+ * pinned host buffers for that overlap).  The forest's own memory stays
+ * capped by its bdl_config.hbm_budget_bytes.  While a server is alive the
+ * caller must not use its forest directly.  (The paper has no serving layer;
+ * this interface is a choice of this library.)
+ * --------------------------------------------------------------------- */
+
+typedef struct bdl_server bdl_server;        /* opaque, library-owned */
+
+typedef enum { BDL_REQ_INSERT = 0, BDL_REQ_ERASE = 1, BDL_REQ_KNN = 2 } bdl_request_kind;
+
+typedef struct {
+    int32_t kind;               /* bdl_request_kind */
+    int32_t k;                  /* k-NN: 1..32 */
+    int64_t n;                  /* points, ids or queries */
+    const int32_t *in_host;     /* insert: [n][dim] points; erase: [n] ids; k-NN: [n][dim]
+                                   queries.  Read until the request completes. */
+    int32_t *out_ids_host;      /* insert: [n] new ids (may be NULL); k-NN: [n][k] */
+    int64_t *out_d2_host;       /* k-NN: [n][k] */
+} bdl_request;
+
+typedef struct {
+    int32_t status;             /* bdl_status of the request */
+    int32_t kind;
+    int32_t done;               /* 1 once completed */
+    int32_t pad_;
+    uint64_t ticket;
+    int64_t n_done;             /* insert: points inserted; erase: points erased; k-NN: queries */
+    int64_t group;              /* index of the device group it ran in */
+    double t_submit_ms;         /* host clock, ms since the server was created */
+    double t_start_ms;          /* its group started on the host */
+    double t_done_ms;           /* its outputs were in host memory */
+} bdl_result;
+
+typedef struct {
+    int32_t max_inflight;       /* admitted, not completed; default 64 */
+    int32_t serial;             /* 1 = one request at a time, no batching (comparison path) */
+    int64_t staging_budget_bytes; /* device bytes of the requests in flight; default 1 GiB */
+    int64_t max_group_queries;  /* k-NN queries per launch; default 2^20 */
+    int64_t max_group_points;   /* points per merged insert; default 2^21 */
+} bdl_server_config;
+
+/* Fill *cfg with the defaults above. */
+void bdl_server_default_config(bdl_server_config *cfg);
+
+/* Start a server on forest f (cfg NULL = defaults); it runs host threads of
+ * its own and three CUDA streams on f's device. */
+int bdl_server_create(bdl_forest *f, const bdl_server_config *cfg, bdl_server **out);
+
+/* Queue a request (never blocks on the device); *out_ticket identifies it.
+ * The request struct is copied; the buffers it points to are not. */
+int bdl_server_submit(bdl_server *s, const bdl_request *req, uint64_t *out_ticket);
+
+/* Wait for a request to complete and collect its result (once per ticket). */
+int bdl_server_wait(bdl_server *s, uint64_t ticket, bdl_result *out_host);
+
+/* Wait until every submitted request has completed. */
+int bdl_server_drain(bdl_server *s);
+
+/* Device groups run so far. */
+int bdl_server_stats(const bdl_server *s, int64_t *out_groups_host);
+
+/* Finish every submitted request, stop the threads and free the server (not
+ * the forest).  NULL is a no-op. */
+int bdl_server_destroy(bdl_server *s);
+
 /* Number of live points (host-side count, no device access). */
 int bdl_size(const bdl_forest *f, int64_t *out_live_host);
 

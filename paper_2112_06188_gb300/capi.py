@@ -18,13 +18,37 @@ SYMBOLS = [
     "bdl_destroy", "bdl_status_string", "bdl_last_error", "bdl_tree_mask", "bdl_buffer_ids",
     "bdl_tree_info", "bdl_tree_export", "bdl_bloom_export", "bdl_knn_stats", "bdl_launch_count",
     "bdl_profile", "bdl_profile_read", "bdl_kernel_count", "bdl_kernel_name", "bdl_knn_noalloc",
+    "bdl_insert_batch", "bdl_erase_batch", "bdl_knn_batch",
+    "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
+    "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy",
 ]
+
+BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
 
 
 class BdlConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("buffer_size", ctypes.c_int32),
                 ("bloom_bits_per_key", ctypes.c_int32), ("bloom_hashes", ctypes.c_int32),
                 ("hash_seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class BdlRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("in_host", ctypes.c_void_p), ("out_ids_host", ctypes.c_void_p),
+                ("out_d2_host", ctypes.c_void_p)]
+
+
+class BdlResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("done", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("ticket", ctypes.c_uint64), ("n_done", ctypes.c_int64),
+                ("group", ctypes.c_int64), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+class BdlServerConfig(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("serial", ctypes.c_int32),
+                ("staging_budget_bytes", ctypes.c_int64), ("max_group_queries", ctypes.c_int64),
+                ("max_group_points", ctypes.c_int64)]
 
 
 class BdlError(RuntimeError):
@@ -68,6 +92,16 @@ def load(path=None):
         "bdl_kernel_count": (i32, []),
         "bdl_kernel_name": (ctypes.c_char_p, [i32]),
         "bdl_knn_noalloc": (i32, [P, P, i64, i32, P, P, P]),
+        "bdl_insert_batch": (i32, [P, i32, P, P, P, P]),
+        "bdl_erase_batch": (i32, [P, i32, P, P, P, P]),
+        "bdl_knn_batch": (i32, [P, i32, P, P, i32, P, P, P]),
+        "bdl_server_default_config": (None, [P]),
+        "bdl_server_create": (i32, [P, P, P]),
+        "bdl_server_submit": (i32, [P, P, P]),
+        "bdl_server_wait": (i32, [P, u64, P]),
+        "bdl_server_drain": (i32, [P]),
+        "bdl_server_stats": (i32, [P, P]),
+        "bdl_server_destroy": (i32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -129,6 +163,74 @@ def bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
 def bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
     """bdl_knn without device allocation (scratch in a fixed library array)."""
     return load().bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream)
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * max(len(xs), 1))(*[x or None for x in xs])
+
+
+def _i64_array(xs):
+    return (ctypes.c_int64 * max(len(xs), 1))(*xs)
+
+
+def bdl_insert_batch(forests, pts_dev, n, out_ids_dev, stream):
+    """Insert_L on len(forests) forests; lists of handles / device pointers / sizes."""
+    return load().bdl_insert_batch(_ptr_array(forests), len(forests), _ptr_array(pts_dev),
+                                   _i64_array(n), _ptr_array(out_ids_dev), stream)
+
+
+def bdl_erase_batch(forests, ids_dev, n, stream):
+    """Returns (status, [number erased per forest])."""
+    out = (ctypes.c_int64 * max(len(forests), 1))()
+    st = load().bdl_erase_batch(_ptr_array(forests), len(forests), _ptr_array(ids_dev),
+                                _i64_array(n), out, stream)
+    return st, [int(out[i]) for i in range(len(forests))]
+
+
+def bdl_knn_batch(forests, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
+    return load().bdl_knn_batch(_ptr_array(forests), len(forests), _ptr_array(q_dev), _i64_array(m),
+                                k, _ptr_array(out_ids_dev), _ptr_array(out_d2_dev), stream)
+
+
+def bdl_server_default_config():
+    cfg = BdlServerConfig()
+    load().bdl_server_default_config(_ref(cfg))
+    return cfg
+
+
+def bdl_server_create(f, cfg):
+    """Returns (status, server handle)."""
+    h = ctypes.c_void_p()
+    st = load().bdl_server_create(f, _ref(cfg) if cfg is not None else None, _ref(h))
+    return st, h.value
+
+
+def bdl_server_submit(s, req):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64(0)
+    st = load().bdl_server_submit(s, _ref(req), _ref(t))
+    return st, t.value
+
+
+def bdl_server_wait(s, ticket):
+    """Returns (status, BdlResult)."""
+    r = BdlResult()
+    st = load().bdl_server_wait(s, ticket, _ref(r))
+    return st, r
+
+
+def bdl_server_drain(s):
+    return load().bdl_server_drain(s)
+
+
+def bdl_server_stats(s):
+    g = ctypes.c_int64(0)
+    st = load().bdl_server_stats(s, _ref(g))
+    return st, g.value
+
+
+def bdl_server_destroy(s):
+    return load().bdl_server_destroy(s)
 
 
 def bdl_size(f):

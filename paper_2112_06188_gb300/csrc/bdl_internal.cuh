@@ -37,16 +37,11 @@ enum KernelId : int {
   kK_level_partition,
   kK_subtree,
   kK_box_up,
-  kK_pool_tail,
   kK_sort_small,
-  kK_append_validate,
-  kK_set_alive,
-  kK_iota,
   kK_erase_mark,
   kK_bloom_build,
   kK_erase_locate,
   kK_buffer_compact,
-  kK_gather_roots,
   kK_mark_ids,
   kK_popc_blocks,
   kK_scan_bsum,
@@ -54,6 +49,9 @@ enum KernelId : int {
   kK_knn,
   kK_pack_nodes,
   kK_qsort,
+  kK_fill,
+  kK_pack_lives,
+  kK_put_blob,
   kKernelCount
 };
 extern const char *const kKernelNames[kKernelCount];
@@ -244,13 +242,30 @@ struct Tree {
   size_t bloom_bytes = 0;
 };
 
-// One tree to build: where its input points are and where its arrays go.
+// Where a pool of point ids comes from (Sec. IV-B1): the forest's sorted
+// buffer ids, then either an explicit id array or a range of new ids.
+struct PoolSrc {
+  const int32_t *buf;      // sorted buffer ids (nbuf of them)
+  int64_t nbuf;
+  const int32_t *arr;      // explicit ids, or nullptr for a range
+  int64_t first;           // first id of the range
+};
+
+// One tree to build: its outputs and where its input points come from --
+// the live records of cleared trees (from_cleared of them, listed as
+// ClearedSrc entries) followed by entries [pool_lo, pool_lo + s - from_cleared)
+// of its forest's pool.  Trees of different forests can share one build.
 struct BuildTree {
   Tree *tree;
-  int64_t base;            // first position in the staging arrays (multiple of 8)
   int64_t s;
   int h;
-  int g;                   // levels split by the global kernels
+  int64_t from_cleared;
+  PoolSrc pool;
+  int64_t pool_lo;
+  const int32_t *idtab;    // the forest's id table
+  unsigned long long *err; // the forest's error word
+  int64_t base = 0;        // set by build_trees: first staging position
+  int g = 0;               // set by build_trees: levels split by the global kernels
 };
 
 struct Scratch;            // allocation helper (forest.cu)
@@ -287,6 +302,10 @@ int set_error(int status, const std::string &msg);
 int cuda_check(cudaError_t e, const char *what);
 int dev_alloc(bdl_forest *f, void **p, size_t bytes, cudaStream_t s);
 void dev_free(bdl_forest *f, void *p, size_t bytes, cudaStream_t s);
+// Copy a launch table from host memory (any kind) to 16-byte aligned device
+// memory, ordered on `s`, without making the host wait for the stream; the
+// source may be reused when this returns.  Legal while `s` is capturing.
+int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s);
 ForestView forest_view(const bdl_forest *f);
 // The view k-NN uses: the static trees plus the buffer's kd-tree.  With
 // build = true a stale buffer tree is rebuilt first (this allocates); with
@@ -298,47 +317,131 @@ constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input o
 int smem_subtree_capacity(int dim);
 
 // ---- build.cu ----
-// Gather the points of the new trees into staging and build them.
-struct PoolSrc {
-  const int32_t *buf;      // sorted buffer ids (nbuf of them)
-  int64_t nbuf;
-  const int32_t *arr;      // explicit ids, or nullptr for a range
-  int64_t first;           // first id of the range
-};
 struct ClearedSrc {        // a cleared tree whose live points join a new tree
   const int32_t *pts;      // point records
   int64_t size;
   int32_t dst;             // index into the BuildTree list
 };
-int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<ClearedSrc> &cl,
-                const PoolSrc &pool, const std::vector<int64_t> &pool_lo,
-                const std::vector<int64_t> &from_cleared, cudaStream_t s);
-int build_scratch_bytes(const bdl_forest *f, const std::vector<BuildTree> &bt, size_t *bytes);
-void launch_pool_tail(const PoolSrc &pool, int64_t from, int64_t count, int32_t *dst,
-                      cudaStream_t s);
+// Gather the points of the new trees (of any number of forests with the same
+// dim) into staging and build all of them in shared launches.  Scratch is
+// charged to forest `af`.
+int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
+                const std::vector<ClearedSrc> &cl, cudaStream_t s);
 void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s);
 
 // ---- erase.cu ----
-void launch_append_validate(const int32_t *pts, int64_t n, int dim, int32_t *idtab_dst,
-                            int64_t *flag, cudaStream_t s);
-void launch_set_alive(uint32_t *alive, int64_t first, int64_t n, cudaStream_t s);
-void launch_iota(int32_t *out, int64_t first, int64_t n, cudaStream_t s);
-void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
-                       int32_t *list, int64_t *count, cudaStream_t s);
-void launch_bloom_build(const Tree *t, int dim, uint64_t seed, cudaStream_t s);
-void launch_erase_locate(const ForestView &fv, uint64_t seed, const int32_t *list, int64_t n,
-                         cudaStream_t s);
-void launch_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n,
-                           cudaStream_t s);
-void launch_gather_roots(const ForestView &fv, int64_t *out, cudaStream_t s);
+// One forest's deduplicated erase list in an erase launch.
+struct EraseCall {
+  const ForestView *fv;
+  const int32_t *list;     // ids to erase (each live, each once)
+  int64_t n;
+  uint64_t seed;           // the forest's bloom hash seed
+};
+struct EraseJob {          // device form of an EraseCall
+  const TreeView *trees;
+  int32_t ntrees, dim;
+  const int32_t *idtab;
+  unsigned long long *err;
+  const int32_t *list;
+  int64_t n;
+  uint64_t seed;
+};
+size_t erase_table_bytes(const std::vector<EraseCall> &calls);
+// Bloom probe, descent and tombstone for every call in one launch; the job
+// table goes to `table` (erase_table_bytes of device memory).
+int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
+                      cudaStream_t s);
 int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n,
                         int32_t *out, cudaStream_t s);
 
+// Table-driven helpers (one launch for many forests or trees).
+enum FillKind : int32_t { kFillAppend = 0, kFillPoolTail = 1, kFillIota = 2, kFillAlive = 3 };
+struct FillSeg {           // `count` work items of one kind
+  int32_t kind, pad_;
+  int64_t count;
+  const int32_t *src;      // append: coordinates in
+  int32_t *dst;            // append / pool tail / iota: out
+  unsigned long long *flag;  // append: set to 1 on a coordinate off the grid
+  const int32_t *buf;      // pool tail: the forest's pool ...
+  int64_t nbuf;
+  const int32_t *arr;
+  int64_t first;           // pool tail: range start; iota / alive: first id
+  int64_t from;            // pool tail: first pool entry copied
+  uint32_t *alive;         // alive: the forest's bitmap
+};
+struct MarkSeg {           // one forest's erase batch
+  uint32_t *alive;
+  int64_t next_id;
+  const int32_t *ids;
+  int64_t n;
+  int32_t *list;           // out: owned ids
+  int64_t *count;          // out: how many
+};
+struct TreeSeg {           // one tree: bloom builds, record packing, live refreshes
+  const int32_t *pts;
+  int64_t size;
+  int32_t dim, h;
+  uint32_t *bloom;
+  int64_t blocks;
+  const Node *node;
+  const int32_t *box;
+  const int32_t *live;
+  int32_t *pk;
+  uint64_t seed;           // bloom hash seed (bloom builds)
+};
+struct BufSeg {            // one forest's buffer and roots
+  int32_t *buf;
+  int64_t nbuf;
+  const uint32_t *alive;
+  int64_t *out;            // out[0] = new nbuf, out[1 + t] = live count of tree t
+  int32_t ntrees, pad_;
+  const int32_t *roots[kMaxLevel];
+};
+size_t table_bytes(size_t nseg, size_t seg_size);
+int launch_fill_many(const std::vector<FillSeg> &segs, void *table, cudaStream_t s);
+int launch_erase_mark_many(const std::vector<MarkSeg> &segs, void *table, cudaStream_t s);
+int launch_bloom_build_many(const std::vector<TreeSeg> &segs, void *table,
+                            cudaStream_t s);
+int launch_pack_lives_many(const std::vector<TreeSeg> &segs, void *table, cudaStream_t s);
+int launch_buffer_compact_many(const std::vector<BufSeg> &segs, void *table, cudaStream_t s);
+
 // ---- knn.cu ----
-int launch_knn(const ForestView &fv, const int32_t *q, const int32_t *perm, int64_t m, int k,
-               int32_t *out_ids, int64_t *out_d2, unsigned long long *stats, cudaStream_t s);
-void launch_pack_nodes(const Tree *t, int dim, cudaStream_t s);
-void launch_pack_lives(const Tree *t, int dim, cudaStream_t s);
+// One forest's query batch in a k-NN launch.
+struct KnnCall {
+  const ForestView *fv;
+  const int32_t *q;        // [m][dim]
+  const int32_t *perm;     // processing order, or nullptr
+  int64_t m;
+  int32_t *oi;             // [m][k]
+  int64_t *od;
+};
+// Device form of a KnnCall (the kernel reads these from a table).
+struct KnnJob {
+  const TreeView *trees;
+  int32_t ntrees, dim;
+  const int32_t *idtab;
+  const int32_t *buf;
+  int64_t nbuf;
+  unsigned long long *err;
+  const int32_t *q;
+  const int32_t *perm;
+  int64_t m;
+  int32_t *oi;
+  int64_t *od;
+};
+// Device bytes the job table of `calls` needs (0 for a single call, whose job
+// travels as kernel parameters; `table` may then be null).
+size_t knn_table_bytes(const std::vector<KnnCall> &calls);
+// k-NN for every call (all of dimension `dim`) in one launch; the job table
+// is uploaded to `table` (knn_table_bytes of device memory) on stream s.
+int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,
+                    unsigned long long *stats, cudaStream_t s);
+// The packed k-NN records of many trees (Sec. V-B's per-node data, laid out
+// for the query kernel): table entries and their work prefix ...
+void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<TreeSeg> &segs,
+                        std::vector<int64_t> &pre);
+// ... and one launch over a device copy of them (pre[nseg] = total).
+void launch_pack_nodes(const TreeSeg *segs, const int64_t *pre, int nseg, int64_t total, cudaStream_t s);
 // Spatial order of the queries (counting sort on a Morton prefix of their
 // coordinates): perm[m] gets query indices; scratch of query_sort_bytes().
 size_t query_sort_bytes(int64_t m, int dim);

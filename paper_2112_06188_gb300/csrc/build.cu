@@ -47,34 +47,69 @@ struct NodeOut {               // where a tree's arrays go
   Node *node;
 };
 
-struct LvTree {
-  int64_t base, s, seg_off, tile_off;
-  int32_t t, c, h, slot;
+// One tree of a build, as the kernels see it (in device memory).  The trees
+// of one build may come from different forests: each carries its own pool,
+// id table and error word.
+struct DTree {
+  int64_t base, s;             // first staging position, points
+  int32_t h, g;                // split levels, levels split by the global kernels
+  int32_t sel, pad_;           // staging buffer holding the tree after its global levels
+  NodeOut out;
+  int64_t from_cleared;        // records gathered from cleared trees (they come first)
+  int64_t pool_lo;             // first pool entry of the tree's chunk
+  const int32_t *pbuf;         // owning forest's pool: sorted buffer ids ...
+  int64_t pnbuf;
+  const int32_t *parr;         // ... then explicit ids, or a range from pfirst
+  int64_t pfirst;
+  const int32_t *idtab;        // owning forest's id table
+  unsigned long long *err;     // owning forest's error word
 };
 
-struct LvParams {
-  int ntrees, dim, tile;
+struct DCleared {              // a cleared tree whose live records join tree `dst`
+  const int32_t *pts;
+  int64_t size;
+  int32_t dst, pad_;
+};
+
+// Largest j in [0, n) with pre[j] <= x, for a prefix array pre[0..n] that
+// starts at 0 and has pre[n] > x (empty entries are skipped).
+__device__ __forceinline__ int find_le(const int64_t *pre, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct LvTree {                // one tree at one global level
+  int64_t base, s, seg_off, tile_off;
+  int32_t t, c, h;
+  NodeOut out;
+  unsigned long long *err;
+};
+
+struct LvParams {              // one global level
+  int nact, dim, tile, it;
   int64_t S;
   const int32_t *src;
   int32_t *dst;
   uint32_t *hist;
   SegState *seg;
   uint64_t *cand;
-  unsigned long long *err;
-  LvTree tr[kMaxLevel];
-  NodeOut out[kMaxLevel];
+  LvTree one;                  // the level's tree when nact == 1 (no memory lookups)
+  const LvTree *lt;            // [nact] the level's trees
+  const int64_t *act_seg;      // [nact + 1] segment prefix
+  const int64_t *act_tile;     // [nact + 1] tile prefix
 };
 
-__device__ __forceinline__ int find_tree_by_tile(const LvParams &P, int64_t b) {
-  int j = 0;
-  while (j + 1 < P.ntrees && P.tr[j + 1].tile_off <= b) j++;
-  return j;
+__device__ __forceinline__ LvTree tree_by_tile(const LvParams &P, int64_t b) {
+  return P.nact == 1 ? P.one : P.lt[find_le(P.act_tile, P.nact, b)];
 }
 
-__device__ __forceinline__ int find_tree_by_seg(const LvParams &P, int64_t g) {
-  int j = 0;
-  while (j + 1 < P.ntrees && P.tr[j + 1].seg_off <= g) j++;
-  return j;
+__device__ __forceinline__ LvTree tree_by_seg(const LvParams &P, int64_t g) {
+  return P.nact == 1 ? P.one : P.lt[find_le(P.act_seg, P.nact, g)];
 }
 
 // ---------------------------------------------------------------------------
@@ -85,23 +120,11 @@ struct GatherParams {
   int nsrc, ntrees, dim;
   int64_t S;
   int32_t *stg;                       // staging A: [dim+1][S]
-  unsigned long long *cursor;         // per new tree: records placed from cleared trees
-  unsigned long long *err;
-  // cleared sources
-  const int32_t *spts[kMaxLevel];     // point records of the cleared trees
-  int64_t ssize[kMaxLevel];
-  int64_t sblk[kMaxLevel + 1];        // block prefix
-  int32_t sdst[kMaxLevel];
-  // new trees
-  int64_t base[kMaxLevel];
-  int64_t from_cleared[kMaxLevel];
-  int64_t pool_lo[kMaxLevel + 1];     // pool chunk of tree j: [pool_lo[j], pool_lo[j+1])
-  // pool
-  const int32_t *pbuf;
-  int64_t pnbuf;
-  const int32_t *parr;
-  int64_t pfirst;
-  const int32_t *idtab;
+  unsigned long long *cursor;         // per tree: records placed from cleared trees
+  const DTree *tree;
+  const DCleared *cl;
+  const int64_t *cl_blk;              // [nsrc + 1] block prefix of the cleared sources
+  const int64_t *pool_off;            // [ntrees + 1] prefix of the pool chunk sizes
 };
 
 __device__ __forceinline__ int32_t pool_id(const int32_t *buf, int64_t nbuf, const int32_t *arr,
@@ -114,12 +137,12 @@ __global__ void k_gather_cleared(const GatherParams P) {
   __shared__ int wsum[32];
   __shared__ unsigned long long sbase;
   int b = blockIdx.x;
-  int src = 0;
-  while (src + 1 < P.nsrc && P.sblk[src + 1] <= b) src++;
-  int64_t p = (int64_t)(b - P.sblk[src]) * blockDim.x + threadIdx.x;
-  bool ok = p < P.ssize[src];
+  const int src = find_le(P.cl_blk, P.nsrc, b);
+  const DCleared C = P.cl[src];
+  int64_t p = (int64_t)(b - P.cl_blk[src]) * blockDim.x + threadIdx.x;
+  bool ok = p < C.size;
   const int rs = rec_ints(P.dim);
-  int32_t id = ok ? P.spts[src][p * rs + P.dim] : -1;
+  int32_t id = ok ? C.pts[p * rs + P.dim] : -1;
   bool live = ok && id >= 0;
   // block-exclusive count of live records
   unsigned bal = __ballot_sync(0xffffffffu, live);
@@ -130,29 +153,30 @@ __global__ void k_gather_cleared(const GatherParams P) {
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { int v = wsum[w]; wsum[w] = acc; acc += v; }
-    sbase = atomicAdd(&P.cursor[P.sdst[src]], (unsigned long long)acc);
+    sbase = atomicAdd(&P.cursor[C.dst], (unsigned long long)acc);
   }
   __syncthreads();
   if (!live) return;
-  int j = P.sdst[src];
+  const DTree &T = P.tree[C.dst];
   int64_t rel = (int64_t)sbase + wsum[warp] + wpre;
-  if (rel >= P.from_cleared[j]) {   // more live records than the plan counted
-    atomicOr(P.err, kErrGather);
+  if (rel >= T.from_cleared) {   // more live records than the plan counted
+    atomicOr(T.err, kErrGather);
     return;
   }
-  int64_t dst = P.base[j] + rel;
-  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = P.spts[src][p * rs + c];
+  int64_t dst = T.base + rel;
+  for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = C.pts[p * rs + c];
   P.stg[P.dim * P.S + dst] = id;
 }
 
 __global__ void k_gather_pool(const GatherParams P, int64_t total) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= total) return;
-  int j = 0;
-  while (j + 1 < P.ntrees && P.pool_lo[j + 1] <= k) j++;
-  int32_t id = pool_id(P.pbuf, P.pnbuf, P.parr, P.pfirst, k);
-  int64_t dst = P.base[j] + P.from_cleared[j] + (k - P.pool_lo[j]);
-  const int32_t *src = P.idtab + (int64_t)id * P.dim;
+  const int j = find_le(P.pool_off, P.ntrees, k);
+  const DTree &T = P.tree[j];
+  const int64_t i = k - P.pool_off[j];
+  int32_t id = pool_id(T.pbuf, T.pnbuf, T.parr, T.pfirst, T.pool_lo + i);
+  int64_t dst = T.base + T.from_cleared + i;
+  const int32_t *src = T.idtab + (int64_t)id * P.dim;
   for (int c = 0; c < P.dim; ++c) P.stg[c * P.S + dst] = src[c];
   P.stg[P.dim * P.S + dst] = id;
 }
@@ -181,7 +205,7 @@ __device__ __forceinline__ TileSegs tile_segs(const LvParams &P, const LvTree &T
 __global__ void k_level_hist(const LvParams P) {
   __shared__ uint32_t h[2][kHistBins];
   int b = blockIdx.x;
-  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  const LvTree T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -210,7 +234,7 @@ __global__ void k_level_bucket(const LvParams P, int64_t nseg) {
   if (gs >= nseg) return;
   const int lane = threadIdx.x & 31;
   constexpr int kRun = kHistBins / 32;
-  const LvTree &T = P.tr[find_tree_by_seg(P, gs)];
+  const LvTree T = tree_by_seg(P, gs);
   int64_t st, sz;
   seg_range(T.s, T.t, gs - T.seg_off, st, sz);
   const uint32_t r = (uint32_t)((sz + 1) >> 1);
@@ -253,7 +277,7 @@ __global__ void k_level_collect(const LvParams P) {
   __shared__ unsigned cnt[2];
   __shared__ unsigned long long basev[2];
   int b = blockIdx.x;
-  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  const LvTree T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -297,7 +321,7 @@ __global__ void k_level_select(const LvParams P, int64_t nseg) {
   __shared__ uint64_t keys[2048];
   int64_t gs = blockIdx.x;
   if (gs >= nseg) return;
-  const LvTree &T = P.tr[find_tree_by_seg(P, gs)];
+  const LvTree T = tree_by_seg(P, gs);
   int64_t idx = gs - T.seg_off;
   int64_t st, sz;
   seg_range(T.s, T.t, idx, st, sz);
@@ -366,7 +390,7 @@ __global__ void k_level_select(const LvParams P, int64_t nseg) {
     uint32_t coord = ((uint32_t)S.bucket << kHistShift) | (uint32_t)(k40 >> 31);
     uint64_t med = comp_key((int32_t)coord, (int32_t)(k40 & 0x7fffffffu));
     S.median = med;
-    const NodeOut &o = P.out[T.slot];
+    const NodeOut &o = T.out;
     int l = T.h + 1;
     int64_t v = veb_slot(l, T.t, idx);
     o.node[v] = Node{med, (int32_t)veb_slot(l, T.t + 1, 2 * idx), (int32_t)veb_slot(l, T.t + 1, 2 * idx + 1)};
@@ -398,7 +422,7 @@ __global__ void k_level_partition(const LvParams P) {
   __shared__ int coff[5];                  // start of each class's run in `stage`
   __shared__ int cok[4];
   int b = blockIdx.x;
-  const LvTree &T = P.tr[find_tree_by_tile(P, b)];
+  const LvTree T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   const SegState *s0 = &P.seg[T.seg_off + g.idx0];
   uint64_t med0 = s0[0].median, med1 = g.sz1 ? s0[1].median : 0;
@@ -449,7 +473,7 @@ __global__ void k_level_partition(const LvParams P) {
       const int64_t lim = (c & 1) ? sz - ((sz + 1) >> 1) : ((sz + 1) >> 1);
       gdst[c] = st + off + (int64_t)cbase[c];
       cok[c] = (int64_t)(cbase[c] + tot) <= lim;   // else the median did not halve the segment
-      if (!cok[c]) atomicOr(P.err, kErrPartition);
+      if (!cok[c]) atomicOr(T.err, kErrPartition);
       coff[c + 1] = coff[c] + (int)tot;
     }
   }
@@ -488,18 +512,12 @@ __global__ void k_level_partition(const LvParams P) {
 // K1-K4 on chip: one CTA builds a whole subtree of <= cap records
 // ---------------------------------------------------------------------------
 
-struct SubTree {
-  int64_t base, s, blk_off;
-  int32_t h, t0, sel, slot;
-};
-
 struct SubParams {
   int ntrees, dim, cap;
   int64_t S;
   const int32_t *stg[2];
-  unsigned long long *err;
-  SubTree tr[kMaxLevel];
-  NodeOut out[kMaxLevel];
+  const DTree *tree;
+  const int64_t *sub_blk;      // [ntrees + 1] prefix of 2^g subtrees per tree
 };
 
 __device__ __forceinline__ uint64_t skey(const int32_t *sc, const int32_t *sid, int cap, int c,
@@ -518,13 +536,13 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
 
   const int cap = P.cap, dim = P.dim;
   int b = blockIdx.x;
-  int tj = 0;
-  while (tj + 1 < P.ntrees && P.tr[tj + 1].blk_off <= b) tj++;
-  const SubTree &T = P.tr[tj];
-  const NodeOut &o = P.out[T.slot];
-  int64_t i0 = b - T.blk_off;
+  const int tj = find_le(P.sub_blk, P.ntrees, b);
+  const DTree &T = P.tree[tj];
+  const NodeOut o = T.out;
+  const int t0 = T.g;
+  int64_t i0 = b - P.sub_blk[tj];
   int64_t start0, m64;
-  seg_range(T.s, T.t0, i0, start0, m64);
+  seg_range(T.s, t0, i0, start0, m64);
   const int m0 = (int)m64;
   const int l = T.h + 1;
 
@@ -547,12 +565,12 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   }
   __syncthreads();
 
-  const int U = T.h - T.t0;
+  const int U = T.h - t0;
   uint16_t *cur = perm0, *nxt = perm1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
   for (int u = 0; u < U; ++u) {
-    const int t = T.t0 + u;
+    const int t = t0 + u;
     const int c = t % dim;
     const int nseg = 1 << u;
     int64_t st_, sz_;
@@ -702,7 +720,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             bool left = (flags >> j) & 1;
             int dst = left ? s_st[s] + lrank : s_st[s] + half + rrank;
             if (left ? (lrank < 0 || lrank >= half) : (rrank < 0 || rrank >= s_sz[s] - half)) {
-              atomicOr(P.err, kErrPartition);
+              atomicOr(T.err, kErrPartition);
             } else {
               nxt[dst] = cur[q];
               segid_n[dst] = (unsigned char)(2 * s + (left ? 0 : 1));   // child segment
@@ -720,7 +738,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         seg_range(m0, u, s, a64, z64);
         int a = (int)a64, z = (int)z64;
         bool va = lane < z, vb = lane + 32 < z;
-        if (z > 64) { if (lane == 0) atomicOr(P.err, kErrPartition); continue; }
+        if (z > 64) { if (lane == 0) atomicOr(T.err, kErrPartition); continue; }
         uint64_t ka = va ? skey(sc, sid, cap, c, cur[a + lane]) : ~0ull;
         uint64_t kb = vb ? skey(sc, sid, cap, c, cur[a + 32 + lane]) : ~0ull;
         int ra = 0, rb = 0;
@@ -780,7 +798,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     __syncthreads();
     for (int s = threadIdx.x; s < (1 << u); s += blockDim.x) {
       int64_t bfs = (i0 << u) + s;
-      int t = T.t0 + u;
+      int t = t0 + u;
       int64_t v = veb_slot(l, t, bfs);
       int64_t vl = veb_slot(l, t + 1, 2 * bfs), vr = veb_slot(l, t + 1, 2 * bfs + 1);
       o.live[v] = o.live[vl] + o.live[vr];
@@ -807,21 +825,20 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
 // ---------------------------------------------------------------------------
 
 struct BoxParams {
-  int ntrees, dim, t;
-  int64_t off[kMaxLevel + 1];
-  int32_t h[kMaxLevel];
-  int32_t slot[kMaxLevel];
-  NodeOut out[kMaxLevel];
+  int nact, dim, t;
+  const DTree *tree;
+  const int32_t *act;          // [nact] trees with global levels below depth t
+  const int64_t *node;         // [nact + 1] prefix of 2^t nodes per tree
 };
 
 __global__ void k_box_up(const BoxParams P) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.off[P.ntrees]) return;
-  int j = 0;
-  while (j + 1 < P.ntrees && P.off[j + 1] <= g) j++;
-  const NodeOut &o = P.out[P.slot[j]];
-  int l = P.h[j] + 1, t = P.t, dim = P.dim;
-  int64_t i = g - P.off[j];
+  if (g >= P.node[P.nact]) return;
+  const int j = find_le(P.node, P.nact, g);
+  const DTree &D = P.tree[P.act[j]];
+  const NodeOut o = D.out;
+  int l = D.h + 1, t = P.t, dim = P.dim;
+  int64_t i = g - P.node[j];
   int64_t v = veb_slot(l, t, i), vl = veb_slot(l, t + 1, 2 * i), vr = veb_slot(l, t + 1, 2 * i + 1);
   o.live[v] = o.live[vl] + o.live[vr];
   for (int c = 0; c < dim; ++c) {
@@ -833,12 +850,6 @@ __global__ void k_box_up(const BoxParams P) {
 // ---------------------------------------------------------------------------
 // buffer helpers
 // ---------------------------------------------------------------------------
-
-__global__ void k_pool_tail(const int32_t *buf, int64_t nbuf, const int32_t *arr, int64_t first,
-                            int64_t from, int64_t count, int32_t *dst) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < count) dst[k] = pool_id(buf, nbuf, arr, first, from + k);
-}
 
 // Single-CTA bitonic sort of n <= 16384 ids.
 __global__ void k_sort_small(int32_t *ids, int n, int np2) {
@@ -879,45 +890,21 @@ NodeOut node_out(Tree *t) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-struct BuildLayout {
-  int cap, tile;
-  int64_t S;              // staging stride (multiple of 8)
-  int64_t nseg_max;       // segments of the widest global level
-  size_t stg_bytes, cand_bytes, hist_bytes, seg_bytes, cursor_bytes;
-};
-
-BuildLayout layout_of(const bdl_forest *f, std::vector<BuildTree> &bt) {
-  BuildLayout L;
-  L.cap = smem_subtree_capacity(f->dim);
-  L.tile = std::min(4096, L.cap);
-  int64_t S = 0;
-  int gmax = 0;
-  for (auto &b : bt) {
-    b.base = S;
-    S += (b.s + 7) / 8 * 8;
-    int g = 0;
-    while (g < b.h && ceil_div(b.s, (int64_t)1 << g) > L.cap) g++;
-    b.g = g;
-    gmax = std::max(gmax, g);
-  }
-  L.S = std::max<int64_t>(S, 8);
-  int64_t nmax = 0;
-  for (int it = 0; it < gmax; ++it) {
-    int64_t n = 0;
-    for (auto &b : bt)
-      if (b.g > it) n += (int64_t)1 << it;
-    nmax = std::max(nmax, n);
-  }
-  L.nseg_max = nmax;
-  L.stg_bytes = (size_t)(f->dim + 1) * L.S * 4;
-  L.cand_bytes = gmax ? (size_t)L.S * 8 : 0;
-  L.hist_bytes = (size_t)nmax * kHistBins * 4;
-  L.seg_bytes = (size_t)nmax * sizeof(SegState);
-  L.cursor_bytes = kMaxLevel * 8;
-  return L;
-}
-
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Host image of a build plan: every per-tree, per-level and per-source array
+// the kernels read, serialized into one buffer that is uploaded with a single
+// copy.
+struct PlanImage {
+  std::vector<unsigned char> bytes;
+  template <class T>
+  size_t put(const std::vector<T> &v) {
+    size_t off = align256(bytes.size());
+    bytes.resize(off + std::max<size_t>(v.size() * sizeof(T), 8));
+    if (!v.empty()) memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
 
 }  // namespace
 
@@ -927,200 +914,237 @@ int smem_subtree_capacity(int dim) {
   return 2048;
 }
 
-int build_scratch_bytes(const bdl_forest *f, const std::vector<BuildTree> &bt0, size_t *bytes) {
-  std::vector<BuildTree> bt = bt0;
-  BuildLayout L = layout_of(f, bt);
-  *bytes = 2 * align256(L.stg_bytes) + align256(L.cand_bytes) + align256(L.hist_bytes) +
-           align256(L.seg_bytes) + align256(L.cursor_bytes);
-  return BDL_OK;
-}
-
-int build_trees(bdl_forest *f, std::vector<BuildTree> &bt, const std::vector<ClearedSrc> &cl,
-                const PoolSrc &pool, const std::vector<int64_t> &pool_lo,
-                const std::vector<int64_t> &from_cleared, cudaStream_t s) {
+int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
+                const std::vector<ClearedSrc> &cl, cudaStream_t s) {
   if (bt.empty()) return BDL_OK;
-  const int dim = f->dim;
-  BuildLayout L = layout_of(f, bt);
-  size_t total = 2 * align256(L.stg_bytes) + align256(L.cand_bytes) + align256(L.hist_bytes) +
-                 align256(L.seg_bytes) + align256(L.cursor_bytes);
+  const int ntree = (int)bt.size();
+  const int cap = smem_subtree_capacity(dim);
+  const int tile = std::min(4096, cap);
+
+  // ---- layout: staging bases and global levels per tree ----
+  int64_t S = 0;
+  int gmax = 0;
+  for (auto &b : bt) {
+    b.base = S;
+    S += (b.s + 7) / 8 * 8;
+    int g = 0;
+    while (g < b.h && ceil_div(b.s, (int64_t)1 << g) > cap) g++;
+    b.g = g;
+    gmax = std::max(gmax, g);
+  }
+  S = std::max<int64_t>(S, 8);
+
+  // ---- plan arrays ----
+  std::vector<DTree> dt(ntree);
+  std::vector<int64_t> pool_off(ntree + 1, 0), sub_blk(ntree + 1, 0);
+  for (int j = 0; j < ntree; ++j) {
+    const BuildTree &b = bt[j];
+    DTree &d = dt[j];
+    memset(&d, 0, sizeof(d));
+    d.base = b.base;
+    d.s = b.s;
+    d.h = b.h;
+    d.g = b.g;
+    d.sel = b.g & 1;
+    d.out = node_out(b.tree);
+    d.from_cleared = b.from_cleared;
+    d.pool_lo = b.pool_lo;
+    d.pbuf = b.pool.buf;
+    d.pnbuf = b.pool.nbuf;
+    d.parr = b.pool.arr;
+    d.pfirst = b.pool.first;
+    d.idtab = b.idtab;
+    d.err = b.err;
+    pool_off[j + 1] = pool_off[j] + (b.s - b.from_cleared);
+    sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << b.g);
+  }
+  const int TB = 256;
+  std::vector<DCleared> dc(cl.size());
+  std::vector<int64_t> cl_blk(cl.size() + 1, 0);
+  for (size_t i = 0; i < cl.size(); ++i) {
+    dc[i].pts = cl[i].pts;
+    dc[i].size = cl[i].size;
+    dc[i].dst = cl[i].dst;
+    dc[i].pad_ = 0;
+    cl_blk[i + 1] = cl_blk[i] + ceil_div(cl[i].size, TB);
+  }
+  // per global level: the trees still above the on-chip size, with segment
+  // and tile prefixes; the same trees get their global nodes boxed bottom-up
+  struct LevelHost { int nact; size_t act, seg, tile, node, lt; int64_t nseg, ntile; };
+  std::vector<LevelHost> lv(gmax);
+  std::vector<int32_t> act_all;
+  std::vector<LvTree> lt_all;
+  std::vector<int64_t> pre_all;
+  std::vector<std::pair<size_t, size_t>> act_pos(gmax), seg_pos(gmax), tile_pos(gmax), node_pos(gmax);
+  int64_t nseg_max = 0;
+  for (int it = 0; it < gmax; ++it) {
+    LevelHost &L = lv[it];
+    L.act = act_all.size();
+    L.lt = lt_all.size();
+    int64_t segs = 0, tiles = 0;
+    std::vector<int64_t> sp{0}, tp{0}, np{0};
+    for (int j = 0; j < ntree; ++j) {
+      if (bt[j].g <= it) continue;
+      act_all.push_back(j);
+      LvTree T;
+      T.base = bt[j].base;
+      T.s = bt[j].s;
+      T.h = bt[j].h;
+      T.t = it;
+      T.c = it % dim;
+      T.seg_off = segs;
+      T.tile_off = tiles;
+      T.out = dt[j].out;
+      T.err = dt[j].err;
+      lt_all.push_back(T);
+      segs += (int64_t)1 << it;
+      tiles += ceil_div(bt[j].s, tile);
+      sp.push_back(segs);
+      tp.push_back(tiles);
+      np.push_back(segs);      // 2^it nodes per tree at depth it, same prefix as segments
+    }
+    L.nact = (int)(act_all.size() - L.act);
+    L.nseg = segs;
+    L.ntile = tiles;
+    L.seg = pre_all.size(); pre_all.insert(pre_all.end(), sp.begin(), sp.end());
+    L.tile = pre_all.size(); pre_all.insert(pre_all.end(), tp.begin(), tp.end());
+    L.node = pre_all.size(); pre_all.insert(pre_all.end(), np.begin(), np.end());
+    nseg_max = std::max(nseg_max, segs);
+  }
+  PlanImage img;
+  const size_t o_dt = img.put(dt), o_dc = img.put(dc), o_clb = img.put(cl_blk),
+               o_pool = img.put(pool_off), o_sub = img.put(sub_blk), o_act = img.put(act_all),
+               o_pre = img.put(pre_all), o_lt = img.put(lt_all);
+  std::vector<TreeSeg> pk_segs;
+  std::vector<int64_t> pk_pre;
+  {
+    std::vector<Tree *> trees;
+    for (auto &b : bt) trees.push_back(b.tree);
+    pack_nodes_entries(trees, dim, pk_segs, pk_pre);
+  }
+  const size_t o_pk = img.put(pk_segs), o_pkpre = img.put(pk_pre);
+
+  // ---- one device block: scratch + plan ----
+  const size_t stg_bytes = align256((size_t)(dim + 1) * S * 4);
+  const size_t cand_bytes = gmax ? align256((size_t)S * 8) : 0;
+  const size_t hist_bytes = align256((size_t)nseg_max * kHistBins * 4);
+  const size_t seg_bytes = align256((size_t)nseg_max * sizeof(SegState));
+  const size_t cursor_bytes = align256((size_t)ntree * 8);
+  const size_t plan_bytes = align256(img.bytes.size());
+  const size_t total = 2 * stg_bytes + cand_bytes + hist_bytes + seg_bytes + cursor_bytes + plan_bytes;
   void *block = nullptr;
-  int st = dev_alloc(f, &block, total, s);
+  int st = dev_alloc(af, &block, total, s);
   if (st) return st;
   unsigned char *p = (unsigned char *)block;
   int32_t *stg[2];
-  stg[0] = (int32_t *)p; p += align256(L.stg_bytes);
-  stg[1] = (int32_t *)p; p += align256(L.stg_bytes);
-  uint64_t *cand = (uint64_t *)p; p += align256(L.cand_bytes);
-  uint32_t *hist = (uint32_t *)p; p += align256(L.hist_bytes);
-  SegState *seg = (SegState *)p; p += align256(L.seg_bytes);
-  unsigned long long *cursor = (unsigned long long *)p;
+  stg[0] = (int32_t *)p; p += stg_bytes;
+  stg[1] = (int32_t *)p; p += stg_bytes;
+  uint64_t *cand = (uint64_t *)p; p += cand_bytes;
+  uint32_t *hist = (uint32_t *)p; p += hist_bytes;
+  SegState *seg = (SegState *)p; p += seg_bytes;
+  unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;
+  unsigned char *plan = p;
+  st = h2d(plan, img.bytes.data(), img.bytes.size(), s);
+  if (!st) st = cuda_check(cudaMemsetAsync(cursor, 0, cursor_bytes, s), "memset");
+  if (st) {
+    dev_free(af, block, total, s);
+    return st;
+  }
+  const DTree *d_tree = (const DTree *)(plan + o_dt);
+  const int32_t *d_act = (const int32_t *)(plan + o_act);
+  const int64_t *d_pre = (const int64_t *)(plan + o_pre);
 
   // ---- K5 gather ----
   {
     GatherParams G;
-    memset(&G, 0, sizeof(G));
     G.nsrc = (int)cl.size();
-    G.ntrees = (int)bt.size();
+    G.ntrees = ntree;
     G.dim = dim;
-    G.S = L.S;
+    G.S = S;
     G.stg = stg[0];
     G.cursor = cursor;
-    G.err = f->err;
-    int64_t blk = 0;
-    const int TB = 256;
-    for (size_t i = 0; i < cl.size(); ++i) {
-      G.spts[i] = cl[i].pts;
-      G.ssize[i] = cl[i].size;
-      G.sdst[i] = cl[i].dst;
-      G.sblk[i] = blk;
-      blk += ceil_div(cl[i].size, TB);
+    G.tree = d_tree;
+    G.cl = (const DCleared *)(plan + o_dc);
+    G.cl_blk = (const int64_t *)(plan + o_clb);
+    G.pool_off = (const int64_t *)(plan + o_pool);
+    if (cl_blk.back()) {
+      KScope ks_(kK_gather_cleared, s);
+      k_gather_cleared<<<(unsigned)cl_blk.back(), TB, 0, s>>>(G);
     }
-    G.sblk[cl.size()] = blk;
-    for (size_t j = 0; j < bt.size(); ++j) {
-      G.base[j] = bt[j].base;
-      G.from_cleared[j] = from_cleared[j];
-      G.pool_lo[j] = pool_lo[j];
-    }
-    G.pool_lo[bt.size()] = pool_lo[bt.size()];
-    G.pbuf = pool.buf;
-    G.pnbuf = pool.nbuf;
-    G.parr = pool.arr;
-    G.pfirst = pool.first;
-    G.idtab = f->idtab;
-    if (cudaMemsetAsync(cursor, 0, L.cursor_bytes, s) != cudaSuccess) return cuda_check(cudaGetLastError(), "memset");
-    if (blk) {
-      { KScope ks_(kK_gather_cleared, s);
-      k_gather_cleared<<<(unsigned)blk, TB, 0, s>>>(G); }
-    }
-    int64_t np = pool_lo[bt.size()];
-    if (np) {
-      { KScope ks_(kK_gather_pool, s);
-      k_gather_pool<<<(unsigned)ceil_div(np, 256), 256, 0, s>>>(G, np); }
+    if (pool_off.back()) {
+      KScope ks_(kK_gather_pool, s);
+      k_gather_pool<<<(unsigned)ceil_div(pool_off.back(), 256), 256, 0, s>>>(G, pool_off.back());
     }
   }
 
-  std::vector<NodeOut> outs(bt.size());
-  for (size_t j = 0; j < bt.size(); ++j) outs[j] = node_out(bt[j].tree);
-
   // ---- global levels ----
-  int gmax = 0;
-  for (auto &b : bt) gmax = std::max(gmax, b.g);
-  std::vector<int> sel(bt.size(), 0);
   for (int it = 0; it < gmax; ++it) {
+    const LevelHost &L = lv[it];
     LvParams P;
-    memset(&P, 0, sizeof(P));
+    P.nact = L.nact;
     P.dim = dim;
-    P.tile = L.tile;
-    P.S = L.S;
+    P.tile = tile;
+    P.it = it;
+    P.S = S;
     P.src = stg[it & 1];
     P.dst = stg[(it & 1) ^ 1];
     P.hist = hist;
     P.seg = seg;
     P.cand = cand;
-    P.err = f->err;
-    int n = 0;
-    int64_t segs = 0, tiles = 0;
-    for (size_t j = 0; j < bt.size(); ++j) {
-      if (bt[j].g <= it) continue;
-      LvTree &T = P.tr[n];
-      T.base = bt[j].base;
-      T.s = bt[j].s;
-      T.t = it;
-      T.c = it % dim;
-      T.h = bt[j].h;
-      T.slot = n;
-      T.seg_off = segs;
-      T.tile_off = tiles;
-      P.out[n] = outs[j];
-      segs += (int64_t)1 << it;
-      tiles += ceil_div(bt[j].s, L.tile);
-      sel[j] = (it + 1) & 1;
-      n++;
-    }
-    P.ntrees = n;
-    if (cudaMemsetAsync(hist, 0, (size_t)segs * kHistBins * 4, s) != cudaSuccess)
-      return cuda_check(cudaGetLastError(), "memset hist");
-    { KScope ks_(kK_level_hist, s);
-    k_level_hist<<<(unsigned)tiles, 512, 0, s>>>(P); }
+    P.one = lt_all[L.lt];
+    P.lt = (const LvTree *)(plan + o_lt) + L.lt;
+    P.act_seg = d_pre + L.seg;
+    P.act_tile = d_pre + L.tile;
+    cudaMemsetAsync(hist, 0, (size_t)L.nseg * kHistBins * 4, s);
+    { KScope ks_(kK_level_hist, s); k_level_hist<<<(unsigned)L.ntile, 512, 0, s>>>(P); }
     { KScope ks_(kK_level_bucket, s);
-    k_level_bucket<<<(unsigned)ceil_div(segs, 8), 256, 0, s>>>(P, segs); }
-    { KScope ks_(kK_level_collect, s);
-    k_level_collect<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P); }
-    { KScope ks_(kK_level_select, s);
-    k_level_select<<<(unsigned)segs, 256, 0, s>>>(P, segs); }
+      k_level_bucket<<<(unsigned)ceil_div(L.nseg, 8), 256, 0, s>>>(P, L.nseg); }
+    { KScope ks_(kK_level_collect, s); k_level_collect<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
+    { KScope ks_(kK_level_select, s); k_level_select<<<(unsigned)L.nseg, 256, 0, s>>>(P, L.nseg); }
     { KScope ks_(kK_level_partition, s);
-    k_level_partition<<<(unsigned)tiles, L.tile / kItems, 0, s>>>(P); }
+      k_level_partition<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
   }
 
   // ---- subtrees on chip ----
   {
     SubParams P;
-    memset(&P, 0, sizeof(P));
-    P.ntrees = (int)bt.size();
+    P.ntrees = ntree;
     P.dim = dim;
-    P.cap = L.cap;
-    P.S = L.S;
+    P.cap = cap;
+    P.S = S;
     P.stg[0] = stg[0];
     P.stg[1] = stg[1];
-    P.err = f->err;
-    int64_t blocks = 0;
-    for (size_t j = 0; j < bt.size(); ++j) {
-      SubTree &T = P.tr[j];
-      T.base = bt[j].base;
-      T.s = bt[j].s;
-      T.h = bt[j].h;
-      T.t0 = bt[j].g;
-      T.sel = bt[j].g ? sel[j] : 0;
-      T.slot = (int)j;
-      T.blk_off = blocks;
-      P.out[j] = outs[j];
-      blocks += (int64_t)1 << bt[j].g;
-    }
-    size_t smem = subtree_smem_bytes(dim, L.cap);
+    P.tree = d_tree;
+    P.sub_blk = (const int64_t *)(plan + o_sub);
+    size_t smem = subtree_smem_bytes(dim, cap);
     cudaError_t e = cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSubtreeSmemMax);
     if (e != cudaSuccess) {
-      dev_free(f, block, total, s);
+      dev_free(af, block, total, s);
       return cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
     }
-    { KScope ks_(kK_subtree, s);
-    k_subtree<<<(unsigned)blocks, kSubThreads, smem, s>>>(P); }
+    KScope ks_(kK_subtree, s);
+    k_subtree<<<(unsigned)sub_blk.back(), kSubThreads, smem, s>>>(P);
   }
 
-  // ---- boxes of the global-level nodes ----
+  // ---- boxes and live counts of the global-level nodes, deepest first ----
   for (int t = gmax - 1; t >= 0; --t) {
+    const LevelHost &L = lv[t];
     BoxParams B;
-    memset(&B, 0, sizeof(B));
+    B.nact = L.nact;
     B.dim = dim;
     B.t = t;
-    int n = 0;
-    int64_t off = 0;
-    for (size_t j = 0; j < bt.size(); ++j) {
-      if (bt[j].g <= t) continue;
-      B.off[n] = off;
-      B.h[n] = bt[j].h;
-      B.slot[n] = n;
-      B.out[n] = outs[j];
-      off += (int64_t)1 << t;
-      n++;
-    }
-    B.off[n] = off;
-    B.ntrees = n;
-    { KScope ks_(kK_box_up, s);
-    k_box_up<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(B); }
+    B.tree = d_tree;
+    B.act = d_act + L.act;
+    B.node = d_pre + L.node;
+    KScope ks_(kK_box_up, s);
+    k_box_up<<<(unsigned)ceil_div(L.nseg, 256), 256, 0, s>>>(B);
   }
-  for (auto &b : bt) launch_pack_nodes(b.tree, dim, s);
+  launch_pack_nodes((const TreeSeg *)(plan + o_pk), (const int64_t *)(plan + o_pkpre), (int)pk_segs.size(),
+                    pk_pre.back(), s);
   int err = cuda_check(cudaGetLastError(), "build kernels");
-  dev_free(f, block, total, s);
+  dev_free(af, block, total, s);
   return err;
-}
-
-void launch_pool_tail(const PoolSrc &pool, int64_t from, int64_t count, int32_t *dst,
-                      cudaStream_t s) {
-  if (count <= 0) return;
-  { KScope ks_(kK_pool_tail, s);
-  k_pool_tail<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(pool.buf, pool.nbuf, pool.arr,
-                                                              pool.first, from, count, dst); }
 }
 
 void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s) {

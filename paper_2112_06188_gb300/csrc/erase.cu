@@ -16,89 +16,38 @@ namespace {
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-__global__ void k_append_validate(const int32_t *pts, int64_t n, int32_t *dst, int64_t *flag) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool bad = false;
-  if (i < n) {
-    int32_t v = pts[i];
-    bad = v < 0 || v >= (1 << kCoordBits);
-    dst[i] = v;
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long *)flag, 1ull);
-}
-
-__global__ void k_set_alive(uint32_t *alive, int64_t first, int64_t n) {
-  int64_t w = (first >> 5) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t last = first + n;  // exclusive
-  if ((w << 5) >= last) return;
-  uint32_t m = 0xffffffffu;
-  if ((w << 5) < first) m &= 0xffffffffu << (first & 31);
-  if (((w + 1) << 5) > last) m &= 0xffffffffu >> (32 - (last & 31));
-  atomicOr(&alive[w], m);
-}
-
-__global__ void k_iota(int32_t *out, int64_t first, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (int32_t)(first + i);
-}
-
-// Clear the alive bit of every live id in the batch; the thread that clears
-// it owns the erase of that id (repeats and dead ids drop out here).
-__global__ void k_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
-                             int32_t *list, int64_t *count) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool own = false;
-  int32_t id = -1;
-  if (i < n) {
-    id = ids[i];
-    if (id >= 0 && id < next_id) {
-      uint32_t bit = 1u << (id & 31);
-      own = (atomicAnd(&alive[id >> 5], ~bit) & bit) != 0;
-    }
-  }
-  unsigned m = __ballot_sync(0xffffffffu, own);
-  if (!m) return;
-  int lane = threadIdx.x & 31;
-  unsigned long long base = 0;
-  if (lane == __ffs(m) - 1) base = atomicAdd((unsigned long long *)count, (unsigned long long)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-  if (own) list[base + __popc(m & ((1u << lane) - 1))] = id;
-}
-
-// K6a: split-block bloom filter over the live ids of one tree.
-__global__ void k_bloom_build(const int32_t *pts, int64_t size, int dim, uint32_t *bloom,
-                              int64_t blocks, uint64_t seed) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= size) return;
-  int32_t id = pts[j * rec_ints(dim) + dim];
-  if (id < 0) return;
-  int64_t blk;
-  uint64_t bits;
-  bloom_hash(seed, blocks, id, blk, bits);
-  for (int w = 0; w < 8; ++w) atomicOr(&bloom[blk * 8 + w], bloom_word_bit(bits, w));
-}
-
 // K6b + K7: for each erased id and each tree (largest first) probe the bloom
 // filter (one 32-byte sector); on a hit descend by the composite key to the
 // unique leaf, find the id, tombstone it and decrement the live counts along
 // the path.  A live id that no tree holds is in the buffer.
-__global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t *list, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, int njobs) {
+  // every warp belongs to one job (one forest's erase list): the per-tree
+  // loop below is warp-synchronous
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= job_warp[njobs]) return;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (job_warp[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  const EraseJob &F = jobs[lo];
   const int lane = threadIdx.x & 31;
-  bool pending = i < n;
-  int32_t id = pending ? list[i] : 0;
+  const int64_t i = (w - job_warp[lo]) * 32 + lane;
+  bool pending = i < F.n;
+  int32_t id = pending ? F.list[i] : 0;
   const int32_t *xq = F.idtab + (int64_t)id * F.dim;
   int32_t path[kMaxLevel + 2];
   // all bloom probes first: independent 32-byte loads, one per tree
   uint64_t maybe_mask = 0;
   if (pending) {
     for (int ti = 0; ti < F.ntrees; ++ti) {
-      const TreeView &T = F.tree[ti];
+      const TreeView &T = F.trees[ti];
       bool maybe = true;
       if (T.bloom) {
         int64_t blk;
         uint64_t bits;
-        bloom_hash(seed, T.bloom_blocks, id, blk, bits);
+        bloom_hash(F.seed, T.bloom_blocks, id, blk, bits);
         const uint4 *bw = reinterpret_cast<const uint4 *>(T.bloom + blk * 8);
         uint4 a = bw[0], b = bw[1];
         uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -109,7 +58,7 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
     }
   }
   for (int ti = 0; ti < F.ntrees; ++ti) {
-    const TreeView &T = F.tree[ti];
+    const TreeView &T = F.trees[ti];
     bool found = false;
     if (pending) {
       if ((maybe_mask >> ti) & 1) {
@@ -155,40 +104,6 @@ __global__ void k_erase_locate(const ForestView F, uint64_t seed, const int32_t 
       pending = false;
     }
   }
-}
-
-// Keep the buffer ids that are still alive, in order (one CTA).
-__global__ void k_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t a = 0; a < nbuf; a += blockDim.x) {
-    int64_t j = a + threadIdx.x;
-    int32_t id = j < nbuf ? buf[j] : -1;
-    bool keep = j < nbuf && ((alive[id >> 5] >> (id & 31)) & 1);
-    unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) wsum[warp] = __popc(m);
-    __syncthreads();
-    int pre = 0, tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (w < warp) pre += wsum[w];
-      tot += wsum[w];
-    }
-    int dst = base + pre + __popc(m & ((1u << lane) - 1));
-    __syncthreads();   // every read of buf[a..] is done before anyone writes
-    if (keep) buf[dst] = id;
-    __syncthreads();
-    if (threadIdx.x == 0) base += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out_n = base;
-}
-
-__global__ void k_gather_roots(const ForestView F, int64_t *out) {
-  int t = threadIdx.x;
-  if (t < F.ntrees) out[t] = F.tree[t].live[0];
 }
 
 // Ordered gather: mark the live ids of the given trees in a bitmap, then emit
@@ -281,58 +196,44 @@ __global__ void k_emit_ids(const uint32_t *bm, int64_t nwords, const int64_t *bs
 
 }  // namespace
 
-void launch_append_validate(const int32_t *pts, int64_t n, int dim, int32_t *idtab_dst,
-                            int64_t *flag, cudaStream_t s) {
-  int64_t tot = n * dim;
-  if (tot <= 0) return;
-  { KScope ks_(kK_append_validate, s);
-  k_append_validate<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(pts, tot, idtab_dst, flag); }
+size_t erase_table_bytes(const std::vector<EraseCall> &calls) {
+  size_t n = calls.size(), views = 0;
+  for (const auto &c : calls) views += (size_t)c.fv->ntrees;
+  return n * sizeof(EraseJob) + (n + 1) * 8 + views * sizeof(TreeView) + 64;
 }
 
-void launch_set_alive(uint32_t *alive, int64_t first, int64_t n, cudaStream_t s) {
-  if (n <= 0) return;
-  int64_t words = ((first + n - 1) >> 5) - (first >> 5) + 1;
-  { KScope ks_(kK_set_alive, s);
-  k_set_alive<<<(unsigned)cdiv(words, 256), 256, 0, s>>>(alive, first, n); }
-}
-
-void launch_iota(int32_t *out, int64_t first, int64_t n, cudaStream_t s) {
-  if (n <= 0 || !out) return;
-  { KScope ks_(kK_iota, s);
-  k_iota<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, first, n); }
-}
-
-void launch_erase_mark(uint32_t *alive, int64_t next_id, const int32_t *ids, int64_t n,
-                       int32_t *list, int64_t *count, cudaStream_t s) {
-  if (n <= 0) return;
-  { KScope ks_(kK_erase_mark, s);
-  k_erase_mark<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(alive, next_id, ids, n, list, count); }
-}
-
-void launch_bloom_build(const Tree *t, int f_dim, uint64_t seed, cudaStream_t s) {
-  if (t->size <= 0) return;
-  { KScope ks_(kK_bloom_build, s);
-  k_bloom_build<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->pts, t->size, f_dim, t->bloom,
-                                                              t->bloom_blocks, seed); }
-}
-
-void launch_erase_locate(const ForestView &fv, uint64_t seed, const int32_t *list, int64_t n,
-                         cudaStream_t s) {
-  if (n <= 0 || fv.ntrees == 0) return;
-  { KScope ks_(kK_erase_locate, s);
-  k_erase_locate<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(fv, seed, list, n); }
-}
-
-void launch_buffer_compact(int32_t *buf, int64_t nbuf, const uint32_t *alive, int64_t *out_n,
-                           cudaStream_t s) {
-  { KScope ks_(kK_buffer_compact, s);
-  k_buffer_compact<<<1, 1024, 0, s>>>(buf, nbuf, alive, out_n); }
-}
-
-void launch_gather_roots(const ForestView &fv, int64_t *out, cudaStream_t s) {
-  if (fv.ntrees == 0) return;
-  { KScope ks_(kK_gather_roots, s);
-  k_gather_roots<<<1, 64, 0, s>>>(fv, out); }
+int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
+                      cudaStream_t s) {
+  const size_t n = calls.size();
+  std::vector<unsigned char> img(erase_table_bytes(calls));
+  EraseJob *jobs = (EraseJob *)img.data();
+  int64_t *warp = (int64_t *)(img.data() + n * sizeof(EraseJob));
+  const size_t views_off = n * sizeof(EraseJob) + (n + 1) * 8;
+  TreeView *views = (TreeView *)(img.data() + views_off);
+  size_t v = 0;
+  warp[0] = 0;
+  for (size_t j = 0; j < n; ++j) {
+    const EraseCall &c = calls[j];
+    EraseJob &J = jobs[j];
+    memset(&J, 0, sizeof(J));
+    J.trees = (const TreeView *)((char *)table + views_off) + v;
+    J.ntrees = c.fv->ntrees;
+    J.dim = c.fv->dim;
+    J.idtab = c.fv->idtab;
+    J.err = c.fv->err;
+    J.list = c.list;
+    J.seed = c.seed;
+    J.n = c.fv->ntrees ? c.n : 0;
+    for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
+    warp[j + 1] = warp[j] + (J.n + 31) / 32;
+  }
+  if (warp[n] == 0) return BDL_OK;
+  int st = h2d(table, img.data(), img.size(), s);
+  if (st) return st;
+  KScope ks_(kK_erase_locate, s);
+  k_erase_locate<<<(unsigned)cdiv(warp[n] * 32, 128), 128, 0, s>>>(
+      (const EraseJob *)table, (const int64_t *)((char *)table + n * sizeof(EraseJob)), (int)n);
+  return cuda_check(cudaGetLastError(), "erase kernel");
 }
 
 int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n, int32_t *out,
@@ -361,6 +262,219 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
   int err = cuda_check(cudaGetLastError(), "collect_sorted_live");
   dev_free(f, blk, bytes, s);
   return err;
+}
+
+}  // namespace bdl
+
+// ---------------------------------------------------------------------------
+// Table-driven helpers: one launch serves many forests (or trees).  Each
+// table entry owns a contiguous range of the launch's work items; a thread
+// finds its entry by binary search over the range prefix.
+// ---------------------------------------------------------------------------
+
+namespace bdl {
+
+namespace {
+
+__device__ __forceinline__ int seg_find(const int64_t *pre, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int32_t pool_entry(const FillSeg &g, int64_t k) {
+  if (k < g.nbuf) return g.buf[k];
+  return g.arr ? g.arr[k - g.nbuf] : (int32_t)(g.first + (k - g.nbuf));
+}
+
+__global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[nseg]) return;
+  const int j = seg_find(pre, nseg, x);
+  const FillSeg &g = segs[j];
+  const int64_t i = x - pre[j];
+  switch (g.kind) {
+    case kFillAppend: {            // copy coordinates into the id table, check the grid
+      const int32_t v = g.src[i];
+      g.dst[i] = v;
+      if (v < 0 || v >= (1 << kCoordBits)) atomicOr(g.flag, 1ull);
+      break;
+    }
+    case kFillPoolTail: g.dst[i] = pool_entry(g, g.from + i); break;
+    case kFillIota: g.dst[i] = (int32_t)(g.first + i); break;
+    case kFillAlive: {
+      const int64_t id = g.first + i;
+      atomicOr(&g.alive[id >> 5], 1u << (id & 31));
+      break;
+    }
+  }
+}
+
+// Erase marking for many forests: entries are warp-aligned, so the warp's
+// aggregated append stays inside one forest's list.
+__global__ void k_erase_mark_many(const MarkSeg *segs, const int64_t *pre_warp, int nseg) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= pre_warp[nseg]) return;
+  const int j = seg_find(pre_warp, nseg, w);
+  const MarkSeg &g = segs[j];
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (w - pre_warp[j]) * 32 + lane;
+  bool own = false;
+  int32_t id = -1;
+  if (i < g.n) {
+    id = g.ids[i];
+    if (id >= 0 && id < g.next_id) {
+      const uint32_t bit = 1u << (id & 31);
+      own = (atomicAnd(&g.alive[id >> 5], ~bit) & bit) != 0;
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, own);
+  if (!m) return;
+  unsigned long long base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd((unsigned long long *)g.count, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+  if (own) g.list[base + __popc(m & ((1u << lane) - 1))] = id;
+}
+
+__global__ void k_bloom_build_many(const TreeSeg *segs, const int64_t *pre, int nseg) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[nseg]) return;
+  const int j = seg_find(pre, nseg, x);
+  const TreeSeg &g = segs[j];
+  const int32_t id = g.pts[(x - pre[j]) * rec_ints(g.dim) + g.dim];
+  if (id < 0) return;
+  int64_t blk;
+  uint64_t bits;
+  bloom_hash(g.seed, g.blocks, id, blk, bits);
+  for (int w = 0; w < 8; ++w) atomicOr(&g.bloom[blk * 8 + w], bloom_word_bit(bits, w));
+}
+
+__global__ void k_pack_lives_many(const TreeSeg *segs, const int64_t *pre, int nseg) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[nseg]) return;
+  const int j = seg_find(pre, nseg, x);
+  const TreeSeg &g = segs[j];
+  const int64_t gi = x - pre[j];                 // g-th internal node in BFS order
+  const int t = 63 - __clzll(gi + 1);
+  const int64_t i = gi + 1 - ((int64_t)1 << t);
+  const Node nd = g.node[veb_slot(g.h + 1, t, i)];
+  const int2 lv = make_int2(g.live[nd.l], g.live[nd.r]);
+  *reinterpret_cast<int2 *>(g.pk + veb_slot(g.h, t, i) * packed_node_ints(g.dim) + 2) = lv;
+}
+
+// One CTA per forest: keep its buffer ids that are still alive, in order;
+// then the live counts of its tree roots.
+__global__ void k_buffer_compact_many(const BufSeg *segs) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const BufSeg &g = segs[blockIdx.x];
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t a = 0; a < g.nbuf; a += blockDim.x) {
+    const int64_t j = a + threadIdx.x;
+    const int32_t id = j < g.nbuf ? g.buf[j] : -1;
+    const bool keep = j < g.nbuf && ((g.alive[id >> 5] >> (id & 31)) & 1);
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int pre = 0, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) pre += wsum[w];
+      tot += wsum[w];
+    }
+    const int dst = base + pre + __popc(m & ((1u << lane) - 1));
+    __syncthreads();
+    if (keep) g.buf[dst] = id;
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) g.out[0] = base;
+  for (int t = threadIdx.x; t < g.ntrees; t += blockDim.x) g.out[1 + t] = g.roots[t][0];
+}
+
+template <class T>
+int upload_table(const std::vector<T> &segs, const std::vector<int64_t> &pre, void *dev,
+                 cudaStream_t s) {
+  std::vector<unsigned char> img(table_bytes(segs.size(), sizeof(T)));
+  memcpy(img.data(), segs.data(), segs.size() * sizeof(T));
+  memcpy(img.data() + (segs.size() * sizeof(T) + 255) / 256 * 256, pre.data(), pre.size() * 8);
+  return h2d(dev, img.data(), img.size(), s);
+}
+
+template <class T>
+const int64_t *table_pre(const std::vector<T> &segs, const void *dev) {
+  return (const int64_t *)((const char *)dev + (segs.size() * sizeof(T) + 255) / 256 * 256);
+}
+
+}  // namespace
+
+size_t table_bytes(size_t nseg, size_t seg_size) {
+  return (nseg * seg_size + 255) / 256 * 256 + (nseg + 1) * 8 + 64;
+}
+
+int launch_fill_many(const std::vector<FillSeg> &segs, void *table, cudaStream_t s) {
+  std::vector<int64_t> pre(segs.size() + 1, 0);
+  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + segs[j].count;
+  if (pre.back() == 0) return BDL_OK;
+  int st = upload_table(segs, pre, table, s);
+  if (st) return st;
+  KScope ks_(kK_fill, s);
+  k_fill_many<<<(unsigned)cdiv(pre.back(), 256), 256, 0, s>>>((const FillSeg *)table,
+                                                               table_pre(segs, table), (int)segs.size());
+  return cuda_check(cudaGetLastError(), "fill kernel");
+}
+
+int launch_erase_mark_many(const std::vector<MarkSeg> &segs, void *table, cudaStream_t s) {
+  std::vector<int64_t> pre(segs.size() + 1, 0);
+  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + (segs[j].n + 31) / 32;
+  if (pre.back() == 0) return BDL_OK;
+  int st = upload_table(segs, pre, table, s);
+  if (st) return st;
+  KScope ks_(kK_erase_mark, s);
+  k_erase_mark_many<<<(unsigned)cdiv(pre.back() * 32, 256), 256, 0, s>>>(
+      (const MarkSeg *)table, table_pre(segs, table), (int)segs.size());
+  return cuda_check(cudaGetLastError(), "erase mark kernel");
+}
+
+int launch_bloom_build_many(const std::vector<TreeSeg> &segs, void *table,
+                            cudaStream_t s) {
+  std::vector<int64_t> pre(segs.size() + 1, 0);
+  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + segs[j].size;
+  if (pre.back() == 0) return BDL_OK;
+  int st = upload_table(segs, pre, table, s);
+  if (st) return st;
+  KScope ks_(kK_bloom_build, s);
+  k_bloom_build_many<<<(unsigned)cdiv(pre.back(), 256), 256, 0, s>>>(
+      (const TreeSeg *)table, table_pre(segs, table), (int)segs.size());
+  return cuda_check(cudaGetLastError(), "bloom kernel");
+}
+
+int launch_pack_lives_many(const std::vector<TreeSeg> &segs, void *table, cudaStream_t s) {
+  std::vector<int64_t> pre(segs.size() + 1, 0);
+  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + (((int64_t)1 << segs[j].h) - 1);
+  if (pre.back() == 0) return BDL_OK;
+  int st = upload_table(segs, pre, table, s);
+  if (st) return st;
+  KScope ks_(kK_pack_lives, s);
+  k_pack_lives_many<<<(unsigned)cdiv(pre.back(), 256), 256, 0, s>>>(
+      (const TreeSeg *)table, table_pre(segs, table), (int)segs.size());
+  return cuda_check(cudaGetLastError(), "pack lives kernel");
+}
+
+int launch_buffer_compact_many(const std::vector<BufSeg> &segs, void *table, cudaStream_t s) {
+  if (segs.empty()) return BDL_OK;
+  std::vector<int64_t> pre(segs.size() + 1, 0);
+  int st = upload_table(segs, pre, table, s);
+  if (st) return st;
+  KScope ks_(kK_buffer_compact, s);
+  k_buffer_compact_many<<<(unsigned)segs.size(), 1024, 0, s>>>((const BufSeg *)table);
+  return cuda_check(cudaGetLastError(), "buffer compact kernel");
 }
 
 }  // namespace bdl

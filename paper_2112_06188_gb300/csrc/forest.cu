@@ -33,16 +33,11 @@ const char *const kKernelNames[kKernelCount] = {
     "k_level_partition",
     "k_subtree",
     "k_box_up",
-    "k_pool_tail",
     "k_sort_small",
-    "k_append_validate",
-    "k_set_alive",
-    "k_iota",
     "k_erase_mark",
     "k_bloom_build",
     "k_erase_locate",
     "k_buffer_compact",
-    "k_gather_roots",
     "k_mark_ids",
     "k_popc_blocks",
     "k_scan_bsum",
@@ -50,6 +45,9 @@ const char *const kKernelNames[kKernelCount] = {
     "k_knn",
     "k_pack_nodes",
     "k_qsort",
+    "k_fill",
+    "k_pack_lives",
+    "k_put_blob",
 };
 
 // ---- live per-kernel timing (CUDA events on the launching stream) ----
@@ -157,6 +155,115 @@ void dev_free(bdl_forest *f, void *p, size_t bytes, cudaStream_t s) {
 
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
+// ---------------------------------------------------------------------------
+// Host -> device copies of small launch tables
+// ---------------------------------------------------------------------------
+//
+// A copy from pageable memory may make the host wait for the stream, and a
+// stream that is being captured into a CUDA graph cannot take it at all.  So
+// tables go through a pinned ring (one per device; a region is reused only
+// after the event recorded behind its copy has completed), and while the
+// stream is capturing they travel as kernel parameters instead, which the
+// graph keeps by value.
+
+namespace {
+
+constexpr size_t kRingBytes = (size_t)16 << 20;
+constexpr int kBlobWords = 1024;                      // 16 KB of parameters
+
+struct Blob {
+  uint4 w[kBlobWords];
+};
+
+__global__ void k_put_blob(const Blob b, unsigned char *dst, int bytes) {
+  const int full = bytes / 16;
+  uint4 *d = (uint4 *)dst;
+  for (int i = threadIdx.x; i < full; i += blockDim.x) d[i] = b.w[i];
+  const unsigned char *src = (const unsigned char *)b.w;
+  for (int i = full * 16 + threadIdx.x; i < bytes; i += blockDim.x) dst[i] = src[i];
+}
+
+struct Ring {
+  unsigned char *base = nullptr;
+  size_t head = 0;
+  struct Use {
+    size_t off, len;
+    cudaEvent_t ev;
+  };
+  std::vector<Use> busy;
+  std::vector<cudaEvent_t> spare;
+};
+std::mutex g_ring_mu;
+Ring g_ring[128];
+
+}  // namespace
+
+int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BDL_OK;
+  if (((uintptr_t)dst & 15) != 0) return set_error(BDL_EINTERNAL, "table not 16-byte aligned");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  int st = cuda_check(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+  if (st) return st;
+  if (cs != cudaStreamCaptureStatusNone) {
+    for (size_t o = 0; o < bytes; o += sizeof(Blob)) {
+      Blob b;
+      const size_t n = std::min(sizeof(Blob), bytes - o);
+      memcpy(b.w, (const unsigned char *)src + o, n);
+      KScope ks_(kK_put_blob, s);
+      k_put_blob<<<1, 256, 0, s>>>(b, (unsigned char *)dst + o, (int)n);
+    }
+    return cuda_check(cudaGetLastError(), "table upload");
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 128) return set_error(BDL_EINVAL, "device index out of range");
+  const size_t len = a256(bytes);
+  if (len > kRingBytes)   // larger than the ring: plain copy
+    return cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "table upload");
+  std::lock_guard<std::mutex> lk(g_ring_mu);
+  Ring &R = g_ring[dev];
+  if (!R.base) {
+    st = cuda_check(cudaMallocHost((void **)&R.base, kRingBytes), "cudaMallocHost(table ring)");
+    if (st) return st;
+  }
+  if (R.head + len > kRingBytes) R.head = 0;
+  const size_t lo = R.head, hi = R.head + len;
+  for (size_t i = 0; i < R.busy.size();) {   // wait for the copies that used this region
+    const Ring::Use &u = R.busy[i];
+    if (u.off < hi && lo < u.off + u.len) {
+      st = cuda_check(cudaEventSynchronize(u.ev), "cudaEventSynchronize(table ring)");
+      if (st) return st;
+      R.spare.push_back(u.ev);
+      R.busy.erase(R.busy.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+  memcpy(R.base + lo, src, bytes);
+  st = cuda_check(cudaMemcpyAsync(dst, R.base + lo, bytes, cudaMemcpyHostToDevice, s), "table upload");
+  if (st) return st;
+  cudaEvent_t ev = nullptr;
+  if (!R.spare.empty()) {
+    ev = R.spare.back();
+    R.spare.pop_back();
+  } else {
+    st = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+    if (st) {
+      cudaStreamSynchronize(s);   // no event to guard the region: wait here instead
+      return st;
+    }
+  }
+  st = cuda_check(cudaEventRecord(ev, s), "cudaEventRecord");
+  if (st) {
+    cudaStreamSynchronize(s);
+    R.spare.push_back(ev);
+    return st;
+  }
+  R.busy.push_back(Ring::Use{lo, len, ev});
+  R.head = hi;
+  return BDL_OK;
+}
+
 static void free_tree(bdl_forest *f, Tree *t, cudaStream_t s) {
   if (!t) return;
   dev_free(f, t->block, t->bytes, s);
@@ -240,13 +347,6 @@ struct DeviceGuard {
   }
 };
 
-static int sync_read(bdl_forest *f, const int64_t *dev, int64_t n, cudaStream_t s) {
-  int st = cuda_check(cudaMemcpyAsync(f->pinned, dev, (size_t)n * 8, cudaMemcpyDeviceToHost, s),
-                      "cudaMemcpyAsync");
-  if (st) return st;
-  return cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-}
-
 static int ensure_id_capacity(bdl_forest *f, int64_t need, cudaStream_t s) {
   if (need <= f->id_cap) return BDL_OK;
   int64_t cap = std::max<int64_t>(f->id_cap, 1024);
@@ -273,95 +373,233 @@ static int ensure_id_capacity(bdl_forest *f, int64_t need, cudaStream_t s) {
   return cuda_check(cudaGetLastError(), "id table growth");
 }
 
-// Insert_L (Alg. 3) of the pool = sorted buffer ++ P, with n = |P|.
-static int insert_pool(bdl_forest *f, const int32_t *arr, int64_t first, int64_t n, cudaStream_t s) {
-  if (n == 0) return BDL_OK;
-  const int64_t X = f->cfg.buffer_size;
-  const int64_t t = f->nbuf + n, q = t / X, rem = t % X;
-  PoolSrc pool{f->buf, f->nbuf, arr, first};
-  if (q == 0) {
-    // everything fits in the buffer
-    launch_pool_tail(pool, f->nbuf, n, f->buf + f->nbuf, s);
-    if (arr) launch_sort_small(f->buf, t, s);
-    f->nbuf = t;
-    f->buf_dirty = true;
-    return cuda_check(cudaGetLastError(), "buffer append");
-  }
-  const uint64_t Fnew = f->F + (uint64_t)q;
-  const uint64_t newt = Fnew & ~f->F, cleared = f->F & ~Fnew;
-  if (Fnew >> kMaxLevel) return set_error(BDL_EINVAL, "forest too large");
+// ---------------------------------------------------------------------------
+// Insert_L (Alg. 3), planned per forest, built for many forests at once
+// ---------------------------------------------------------------------------
 
-  std::vector<BuildTree> bt;
-  std::vector<ClearedSrc> cl;
-  std::vector<int64_t> pool_lo, from_cleared;
+// One forest's Insert_L of the pool = sorted buffer ++ P (|P| = n).
+struct InsertPlan {
+  bdl_forest *f = nullptr;
+  PoolSrc pool{};
+  int64_t n = 0, t = 0, q = 0, rem = 0;
+  uint64_t Fnew = 0, cleared = 0;
+  std::vector<Tree *> built;     // new trees, allocated, built by build_trees
+  void *newbuf = nullptr;        // the new buffer (q > 0)
+};
+
+// Plan the carry and allocate the new trees; their BuildTree / ClearedSrc
+// entries are appended to bt / cl (indices of cl.dst refer to bt).
+static int plan_insert(bdl_forest *f, const PoolSrc &pool, int64_t n, InsertPlan &ip,
+                       std::vector<BuildTree> &bt, std::vector<ClearedSrc> &cl, cudaStream_t s) {
+  const int64_t X = f->cfg.buffer_size;
+  ip.f = f;
+  ip.pool = pool;
+  ip.n = n;
+  ip.t = f->nbuf + n;
+  ip.q = ip.t / X;
+  ip.rem = ip.t % X;
+  if (ip.q == 0) return BDL_OK;                 // everything fits in the buffer
+  ip.Fnew = f->F + (uint64_t)ip.q;
+  const uint64_t newt = ip.Fnew & ~f->F;
+  ip.cleared = f->F & ~ip.Fnew;
+  if (ip.Fnew >> kMaxLevel) return set_error(BDL_EINVAL, "forest too large");
   int64_t pos = 0;
   int prev = -1;
-  int st = BDL_OK;
-  for (int j = 0; j < kMaxLevel && !st; ++j) {
+  for (int j = 0; j < kMaxLevel; ++j) {
     if (!((newt >> j) & 1)) continue;
     int64_t capsum = 0, livesum = 0;
+    const int32_t dst = (int32_t)bt.size();
     for (int i = prev + 1; i < j; ++i) {
-      if (!((cleared >> i) & 1)) continue;
+      if (!((ip.cleared >> i) & 1)) continue;
       Tree *ct = f->trees[i];
       capsum += X << i;
       livesum += ct->live;
-      cl.push_back(ClearedSrc{ct->pts, ct->size, (int32_t)bt.size()});
+      cl.push_back(ClearedSrc{ct->pts, ct->size, dst});
     }
-    int64_t shortfall = (X << j) - capsum;
+    const int64_t shortfall = (X << j) - capsum;
     Tree *nt = nullptr;
-    st = alloc_tree(f, j, livesum + shortfall, s, &nt);
-    if (st) break;
-    bt.push_back(BuildTree{nt, 0, livesum + shortfall, nt->h, 0});
-    pool_lo.push_back(pos);
-    from_cleared.push_back(livesum);
+    int st = alloc_tree(f, j, livesum + shortfall, s, &nt);
+    if (st) return st;
+    ip.built.push_back(nt);
+    BuildTree b;
+    b.tree = nt;
+    b.s = livesum + shortfall;
+    b.h = nt->h;
+    b.from_cleared = livesum;
+    b.pool = pool;
+    b.pool_lo = pos;
+    b.idtab = f->idtab;
+    b.err = f->err;
+    bt.push_back(b);
     pos += shortfall;
     prev = j;
   }
-  void *newbuf = nullptr;
-  if (!st) st = dev_alloc(f, &newbuf, (size_t)X * 4, s);
-  if (!st && pos != q * X) st = set_error(BDL_EINTERNAL, "planner: pool split mismatch");
-  if (!st) {
-    pool_lo.push_back(pos);
-    st = build_trees(f, bt, cl, pool, pool_lo, from_cleared, s);
+  if (pos != ip.q * X) return set_error(BDL_EINTERNAL, "planner: pool split mismatch");
+  return dev_alloc(f, &ip.newbuf, (size_t)X * 4, s);
+}
+
+// Undo a plan that will not be committed.
+static void drop_plan(InsertPlan &ip, cudaStream_t s) {
+  for (Tree *t : ip.built) free_tree(ip.f, t, s);
+  ip.built.clear();
+  if (ip.newbuf) dev_free(ip.f, ip.newbuf, (size_t)ip.f->cfg.buffer_size * 4, s);
+  ip.newbuf = nullptr;
+}
+
+// The new buffer (the pool's tail, Sec. IV-B1) as a fill segment.
+static FillSeg tail_fill(const InsertPlan &ip) {
+  FillSeg g;
+  memset(&g, 0, sizeof(g));
+  g.kind = kFillPoolTail;
+  g.buf = ip.pool.buf;
+  g.nbuf = ip.pool.nbuf;
+  g.arr = ip.pool.arr;
+  g.first = ip.pool.first;
+  if (ip.q == 0) {               // append P after the buffer
+    g.from = ip.f->nbuf;
+    g.count = ip.n;
+    g.dst = ip.f->buf + ip.f->nbuf;
+  } else {
+    g.from = ip.q * ip.f->cfg.buffer_size;
+    g.count = ip.rem;
+    g.dst = (int32_t *)ip.newbuf;
   }
-  if (st) {
-    for (auto &b : bt) free_tree(f, b.tree, s);
-    dev_free(f, newbuf, (size_t)X * 4, s);
+  return g;
+}
+
+// After the build and the tail fill: free cleared trees and the old buffer,
+// install the new trees.
+static void commit_insert(InsertPlan &ip, cudaStream_t s) {
+  bdl_forest *f = ip.f;
+  const int64_t X = f->cfg.buffer_size;
+  if (ip.pool.arr) {             // reinserted ids: keep the buffer sorted
+    if (ip.q == 0) launch_sort_small(f->buf, ip.t, s);
+    else if (ip.rem > 1) launch_sort_small((int32_t *)ip.newbuf, ip.rem, s);
+  }
+  if (ip.q == 0) {
+    f->nbuf = ip.t;
+  } else {
+    for (int i = 0; i < kMaxLevel; ++i)
+      if ((ip.cleared >> i) & 1) {
+        free_tree(f, f->trees[i], s);
+        f->trees[i] = nullptr;
+      }
+    for (Tree *t : ip.built) f->trees[t->level] = t;
+    dev_free(f, f->buf, (size_t)X * 4, s);
+    f->buf = (int32_t *)ip.newbuf;
+    f->nbuf = ip.rem;
+    f->F = ip.Fnew;
+  }
+  f->buf_dirty = true;
+  ip.built.clear();
+  ip.newbuf = nullptr;
+}
+
+// Per-call device scratch for small tables, charged to one forest.
+struct Temp {
+  bdl_forest *f;
+  cudaStream_t s;
+  std::vector<std::pair<void *, size_t>> blocks;
+  Temp(bdl_forest *f_, cudaStream_t s_) : f(f_), s(s_) {}
+  int get(size_t bytes, void **p) {
+    int st = dev_alloc(f, p, bytes, s);
+    if (!st) blocks.push_back({*p, bytes});
     return st;
   }
-  launch_pool_tail(pool, q * X, rem, (int32_t *)newbuf, s);
-  if (arr && rem > 1) launch_sort_small((int32_t *)newbuf, rem, s);
-  for (int i = 0; i < kMaxLevel; ++i)
-    if ((cleared >> i) & 1) {
-      free_tree(f, f->trees[i], s);
-      f->trees[i] = nullptr;
+  ~Temp() {
+    for (auto &b : blocks) dev_free(f, b.first, b.second, s);
+  }
+};
+
+// Build the planned trees of many forests, grouped by dimension, then fill
+// the new buffers and commit.  Plans with q == 0 only fill.
+static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTree> &bt,
+                            std::vector<ClearedSrc> &cl, std::vector<int> &bt_plan,
+                            std::vector<FillSeg> extra_fills, Temp &tmp, cudaStream_t s) {
+  int st = BDL_OK;
+  // one build per dimension present
+  std::vector<int> dims;
+  for (auto &b : bt) {
+    int d = plans[bt_plan[&b - bt.data()]].f->dim;
+    if (std::find(dims.begin(), dims.end(), d) == dims.end()) dims.push_back(d);
+  }
+  for (int d : dims) {
+    if (st) break;
+    std::vector<BuildTree> g;
+    std::vector<int> remap(bt.size(), -1);
+    bdl_forest *charge = nullptr;
+    for (size_t j = 0; j < bt.size(); ++j) {
+      bdl_forest *f = plans[bt_plan[j]].f;
+      if (f->dim != d) continue;
+      if (!charge) charge = f;
+      remap[j] = (int)g.size();
+      g.push_back(bt[j]);
     }
-  for (auto &b : bt) f->trees[b.tree->level] = b.tree;
-  dev_free(f, f->buf, (size_t)X * 4, s);
-  f->buf = (int32_t *)newbuf;
-  f->nbuf = rem;
-  f->buf_dirty = true;
-  f->F = Fnew;
-  return cuda_check(cudaGetLastError(), "insert");
+    std::vector<ClearedSrc> gc;
+    for (auto &c : cl)
+      if (remap[c.dst] >= 0) gc.push_back(ClearedSrc{c.pts, c.size, remap[c.dst]});
+    st = build_trees(charge, d, g, gc, s);
+  }
+  std::vector<FillSeg> fills = std::move(extra_fills);
+  for (auto &ip : plans)
+    if (ip.f && (ip.q > 0 ? ip.rem > 0 : ip.n > 0)) fills.push_back(tail_fill(ip));
+  void *table = nullptr;
+  if (!st && !fills.empty()) st = tmp.get(table_bytes(fills.size(), sizeof(FillSeg)), &table);
+  if (!st && !fills.empty()) st = launch_fill_many(fills, table, s);
+  if (st) {
+    for (auto &ip : plans) drop_plan(ip, s);
+    return st;
+  }
+  for (auto &ip : plans)
+    if (ip.f) commit_insert(ip, s);
+  return BDL_OK;
+}
+
+// The buffer's points get a small kd-tree of their own for k-NN (the paper's
+// buffer tree), rebuilt when the buffer changed -- for many forests in shared
+// build launches.  A forest whose rebuild cannot get memory keeps scanning.
+static void refresh_btrees(bdl_forest *const *F, int nf, cudaStream_t s) {
+  std::vector<BuildTree> bt;
+  std::vector<int> owner;
+  for (int i = 0; i < nf; ++i) {
+    bdl_forest *f = F[i];
+    if (!f->buf_dirty) continue;
+    free_tree(f, f->btree, s);
+    f->btree = nullptr;
+    f->buf_dirty = false;
+    if (f->nbuf == 0) continue;
+    Tree *t = nullptr;
+    if (alloc_tree(f, kMaxLevel, f->nbuf, s, &t) != BDL_OK) continue;
+    BuildTree b;
+    b.tree = t;
+    b.s = f->nbuf;
+    b.h = t->h;
+    b.from_cleared = 0;
+    b.pool = PoolSrc{f->buf, f->nbuf, nullptr, 0};
+    b.pool_lo = 0;
+    b.idtab = f->idtab;
+    b.err = f->err;
+    bt.push_back(b);
+    owner.push_back(i);
+  }
+  std::vector<int> dims;
+  for (size_t j = 0; j < bt.size(); ++j)
+    if (std::find(dims.begin(), dims.end(), F[owner[j]]->dim) == dims.end()) dims.push_back(F[owner[j]]->dim);
+  for (int d : dims) {
+    std::vector<BuildTree> g;
+    std::vector<int> who;
+    for (size_t j = 0; j < bt.size(); ++j)
+      if (F[owner[j]]->dim == d) { g.push_back(bt[j]); who.push_back(owner[j]); }
+    const bool ok = build_trees(F[who[0]], d, g, {}, s) == BDL_OK;
+    for (size_t j = 0; j < g.size(); ++j) {
+      if (ok) F[who[j]]->btree = g[j].tree;
+      else free_tree(F[who[j]], g[j].tree, s);
+    }
+  }
 }
 
 ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s) {
-  // the buffer's points get a small kd-tree of their own (the paper's buffer
-  // tree), rebuilt when the buffer changed; without it they are scanned
-  if (build && f->buf_dirty) {
-    free_tree(f, f->btree, s);
-    f->btree = nullptr;
-    if (f->nbuf > 0) {
-      Tree *bt = nullptr;
-      if (alloc_tree(f, kMaxLevel, f->nbuf, s, &bt) == BDL_OK) {
-        std::vector<BuildTree> b{BuildTree{bt, 0, f->nbuf, bt->h, 0}};
-        PoolSrc pool{f->buf, f->nbuf, nullptr, 0};
-        if (build_trees(f, b, {}, pool, {0, f->nbuf}, {0}, s) == BDL_OK) f->btree = bt;
-        else free_tree(f, bt, s);
-      }
-    }
-    f->buf_dirty = false;
-  }
+  if (build && f->buf_dirty) refresh_btrees(&f, 1, s);
   ForestView fv = forest_view(f);
   if (f->btree && !f->buf_dirty && fv.ntrees < kMaxLevel) {
     TreeView &tv = fv.tree[fv.ntrees++];
@@ -382,6 +620,401 @@ ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s) {
   return fv;
 }
 
+static bool same_device(bdl_forest *const *F, int nf) {
+  for (int i = 1; i < nf; ++i)
+    if (!F[i] || F[i]->device != F[0]->device) return false;
+  return true;
+}
+
+static bool distinct(bdl_forest *const *F, int nf) {
+  std::vector<bdl_forest *> v(F, F + nf);
+  std::sort(v.begin(), v.end());
+  return std::adjacent_find(v.begin(), v.end()) == v.end();
+}
+
+// Insert_L on nf forests: one validation pass and one host sync for all, one
+// build per dimension for every new tree, table-driven fills.  All or nothing:
+// on EINVAL / ENOMEM no forest changes.
+static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, const int64_t *n,
+                       int32_t *const *out_ids, cudaStream_t s) {
+  for (int i = 0; i < nf; ++i) {
+    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
+    if (n[i] < 0) return set_error(BDL_EINVAL, "n < 0");
+    if (n[i] > 0 && !pts[i]) return set_error(BDL_EINVAL, "pts is NULL");
+    if (F[i]->next_id + n[i] > (int64_t)INT32_MAX)
+      return set_error(BDL_EINVAL, "id space (2^31 - 1) exhausted");
+  }
+  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
+  if (!distinct(F, nf)) return set_error(BDL_EINVAL, "a forest appears twice");
+  int st = BDL_OK;
+  for (int i = 0; i < nf && !st; ++i)
+    if (n[i] > 0) st = ensure_id_capacity(F[i], F[i]->next_id + n[i], s);
+  if (st) return st;
+  Temp tmp(F[0], s);
+  // 1. append the coordinates to the id tables and check them (one pass)
+  std::vector<FillSeg> app;
+  for (int i = 0; i < nf; ++i) {
+    if (n[i] == 0) continue;
+    FillSeg g;
+    memset(&g, 0, sizeof(g));
+    g.kind = kFillAppend;
+    g.count = n[i] * F[i]->dim;
+    g.src = pts[i];
+    g.dst = F[i]->idtab + F[i]->next_id * F[i]->dim;
+    app.push_back(g);
+  }
+  if (app.empty()) return BDL_OK;
+  void *flags = nullptr, *table = nullptr;
+  st = tmp.get(app.size() * 8, &flags);
+  if (!st) st = tmp.get(table_bytes(app.size(), sizeof(FillSeg)), &table);
+  if (st) return st;
+  for (size_t j = 0; j < app.size(); ++j) app[j].flag = (unsigned long long *)flags + j;
+  cudaMemsetAsync(flags, 0, app.size() * 8, s);
+  st = launch_fill_many(app, table, s);
+  std::vector<unsigned long long> hf(app.size());
+  if (!st) st = cuda_check(cudaMemcpyAsync(hf.data(), flags, hf.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (st) return st;
+  for (auto v : hf)
+    if (v) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
+  // 2. plan every forest (Alg. 3), allocating the new trees
+  std::vector<InsertPlan> plans(nf);
+  std::vector<BuildTree> bt;
+  std::vector<ClearedSrc> cl;
+  std::vector<int> bt_plan;
+  for (int i = 0; i < nf && !st; ++i) {
+    if (n[i] == 0) continue;
+    st = plan_insert(F[i], PoolSrc{F[i]->buf, F[i]->nbuf, nullptr, F[i]->next_id}, n[i], plans[i], bt, cl, s);
+    bt_plan.resize(bt.size(), i);
+  }
+  if (st) {
+    for (auto &ip : plans)
+      if (ip.f) drop_plan(ip, s);
+    return st;
+  }
+  // 3. build, new buffers, alive bits and ids out, commit
+  std::vector<FillSeg> post;
+  for (int i = 0; i < nf; ++i) {
+    if (n[i] == 0) continue;
+    FillSeg g;
+    memset(&g, 0, sizeof(g));
+    g.kind = kFillAlive;
+    g.first = F[i]->next_id;
+    g.count = n[i];
+    g.alive = F[i]->alive;
+    post.push_back(g);
+    if (out_ids[i]) {
+      g.kind = kFillIota;
+      g.dst = out_ids[i];
+      g.alive = nullptr;
+      post.push_back(g);
+    }
+  }
+  st = build_and_commit(plans, bt, cl, bt_plan, post, tmp, s);
+  if (st) return st;
+  for (int i = 0; i < nf; ++i) {
+    F[i]->next_id += n[i];
+    F[i]->live += n[i];
+  }
+  return cuda_check(cudaGetLastError(), "insert");
+}
+
+static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s);
+
+// Erase_L on nf forests: one marking pass and one host sync to learn what was
+// erased, lazily built blooms, one descent launch, one live-count refresh,
+// one buffer compaction, one more sync for the counts; reinsertion of trees
+// below half then runs per forest (Alg. 4).
+static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, const int64_t *n,
+                      int64_t *out_n, cudaStream_t s) {
+  for (int i = 0; i < nf; ++i) {
+    if (out_n) out_n[i] = 0;
+    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
+    if (n[i] < 0) return set_error(BDL_EINVAL, "n < 0");
+    if (n[i] > 0 && !ids[i]) return set_error(BDL_EINVAL, "ids is NULL");
+  }
+  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
+  if (!distinct(F, nf)) return set_error(BDL_EINVAL, "a forest appears twice");
+  Temp tmp(F[0], s);
+  // 1. dedup against the live sets
+  std::vector<MarkSeg> mk;
+  std::vector<int> mk_forest;
+  int64_t total = 0;
+  for (int i = 0; i < nf; ++i)
+    if (n[i] > 0 && F[i]->next_id > 0) total += n[i], mk_forest.push_back(i);
+  if (mk_forest.empty()) return BDL_OK;
+  void *lists = nullptr, *counts = nullptr, *table = nullptr;
+  int st = tmp.get((size_t)total * 4, &lists);
+  if (!st) st = tmp.get(mk_forest.size() * 8, &counts);
+  if (!st) st = tmp.get(table_bytes(mk_forest.size(), sizeof(MarkSeg)), &table);
+  if (st) return st;
+  int64_t off = 0;
+  for (size_t j = 0; j < mk_forest.size(); ++j) {
+    bdl_forest *f = F[mk_forest[j]];
+    MarkSeg g{f->alive, f->next_id, ids[mk_forest[j]], n[mk_forest[j]], (int32_t *)lists + off,
+              (int64_t *)counts + j};
+    off += g.n;
+    mk.push_back(g);
+  }
+  cudaMemsetAsync(counts, 0, mk.size() * 8, s);
+  st = launch_erase_mark_many(mk, table, s);
+  std::vector<int64_t> ne(mk.size());
+  if (!st) st = cuda_check(cudaMemcpyAsync(ne.data(), counts, ne.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (st) return st;
+  std::vector<int> act;             // indices into mk of forests that erased something
+  for (size_t j = 0; j < mk.size(); ++j) {
+    if (out_n) out_n[mk_forest[j]] = ne[j];
+    F[mk_forest[j]]->live -= ne[j];
+    if (ne[j] > 0) act.push_back((int)j);
+  }
+  if (act.empty()) return BDL_OK;
+  // 2. lazily build the bloom filter of every nonempty tree (Sec. V-A)
+  std::vector<TreeSeg> blooms;
+  for (int j : act) {
+    bdl_forest *f = F[mk_forest[j]];
+    for (int i = 0; i < kMaxLevel && !st; ++i) {
+      Tree *t = f->trees[i];
+      if (!t || t->live == 0 || t->bloom) continue;
+      int64_t need = (t->size * f->cfg.bloom_bits_per_key + 255) / 256, blocks = 1;
+      while (blocks < need) blocks *= 2;
+      void *b = nullptr;
+      st = dev_alloc(f, &b, (size_t)blocks * 32, s);
+      if (st) break;
+      t->bloom = (uint32_t *)b;
+      t->bloom_blocks = blocks;
+      t->bloom_bytes = (size_t)blocks * 32;
+      cudaMemsetAsync(t->bloom, 0, t->bloom_bytes, s);
+      TreeSeg g;
+      memset(&g, 0, sizeof(g));
+      g.pts = t->pts;
+      g.size = t->size;
+      g.dim = f->dim;
+      g.bloom = t->bloom;
+      g.blocks = blocks;
+      g.seed = f->cfg.hash_seed;
+      blooms.push_back(g);
+    }
+  }
+  if (st) return st;
+  if (!blooms.empty()) {
+    void *bt = nullptr;
+    st = tmp.get(table_bytes(blooms.size(), sizeof(TreeSeg)), &bt);
+    if (!st) st = launch_bloom_build_many(blooms, bt, s);
+    if (st) return st;
+  }
+  // 3. probe, descend, tombstone (Alg. 2 on every tree of every forest, one
+  //    launch); a large batch descends in spatial order
+  std::vector<ForestView> views(act.size());
+  std::vector<EraseCall> calls;
+  for (size_t a = 0; a < act.size(); ++a) {
+    const int j = act[a];
+    bdl_forest *f = F[mk_forest[j]];
+    views[a] = forest_view(f);
+    const int32_t *order = mk[j].list;
+    if (ne[j] >= kSortMinQueries) {
+      void *sorted = nullptr;
+      if (tmp.get(a256((size_t)ne[j] * 4) + query_sort_bytes(ne[j], f->dim), &sorted) == BDL_OK) {
+        launch_point_sort(f->idtab, mk[j].list, ne[j], f->dim,
+                          (char *)sorted + a256((size_t)ne[j] * 4), (int32_t *)sorted, s);
+        order = (const int32_t *)sorted;
+      }
+    }
+    calls.push_back(EraseCall{&views[a], order, ne[j], f->cfg.hash_seed});
+  }
+  {
+    void *et = nullptr;
+    st = tmp.get(erase_table_bytes(calls), &et);
+    if (!st) st = launch_erase_jobs(calls, et, s);
+    if (st) return st;
+  }
+  // 4. refresh the k-NN records' live counts; compact the buffers; counts back
+  std::vector<TreeSeg> lives;
+  std::vector<BufSeg> bufs;
+  void *outs = nullptr;
+  st = tmp.get(act.size() * (kMaxLevel + 1) * 8, &outs);
+  if (st) return st;
+  for (size_t a = 0; a < act.size(); ++a) {
+    bdl_forest *f = F[mk_forest[act[a]]];
+    BufSeg b;
+    memset(&b, 0, sizeof(b));
+    b.buf = f->buf;
+    b.nbuf = f->nbuf;
+    b.alive = f->alive;
+    b.out = (int64_t *)outs + a * (kMaxLevel + 1);
+    for (int i = kMaxLevel - 1; i >= 0; --i) {
+      Tree *t = f->trees[i];
+      if (!t) continue;
+      b.roots[b.ntrees++] = t->live_nodes;
+      TreeSeg g;
+      memset(&g, 0, sizeof(g));
+      g.dim = f->dim;
+      g.h = t->h;
+      g.node = t->node;
+      g.live = t->live_nodes;
+      g.pk = t->pk;
+      lives.push_back(g);
+    }
+    bufs.push_back(b);
+  }
+  void *lt = nullptr, *bt2 = nullptr;
+  if (!lives.empty()) {
+    st = tmp.get(table_bytes(lives.size(), sizeof(TreeSeg)), &lt);
+    if (!st) st = launch_pack_lives_many(lives, lt, s);
+    if (st) return st;
+  }
+  st = tmp.get(table_bytes(bufs.size(), sizeof(BufSeg)), &bt2);
+  if (!st) st = launch_buffer_compact_many(bufs, bt2, s);
+  std::vector<int64_t> ho(act.size() * (kMaxLevel + 1));
+  if (!st) st = cuda_check(cudaMemcpyAsync(ho.data(), outs, ho.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (st) return st;
+  // 5. new counts; trees below half capacity are emptied and their points
+  //    reinserted (Alg. 4), all forests' reinsertions built together
+  std::vector<bdl_forest *> touched;
+  for (size_t a = 0; a < act.size(); ++a) {
+    bdl_forest *f = F[mk_forest[act[a]]];
+    const int64_t *o = &ho[a * (kMaxLevel + 1)];
+    if (o[0] != f->nbuf) f->buf_dirty = true;
+    f->nbuf = o[0];
+    int r = 0;
+    for (int i = kMaxLevel - 1; i >= 0; --i)
+      if (f->trees[i]) f->trees[i]->live = o[1 + r++];
+    touched.push_back(f);
+  }
+  st = reinsert_low(touched, s);
+  if (st) return st;
+  return cuda_check(cudaGetLastError(), "erase");
+}
+
+// Alg. 4's rebuild step for the given forests: every tree with fewer live
+// points than half its capacity X*2^i is emptied, and its live points are
+// reinserted through Insert_L in ascending id order, keeping their ids.  The
+// forests' new trees are built in shared launches.  If that cannot get
+// memory, the emptied trees stay where they were (queries remain exact).
+static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s) {
+  struct Low {
+    bdl_forest *f;
+    std::vector<Tree *> trees;
+    int64_t nr;
+    void *R;
+    uint64_t Fsave;
+    Tree *saved[kMaxLevel];
+  };
+  std::vector<Low> lows;
+  for (bdl_forest *f : fs) {
+    Low L;
+    L.f = f;
+    L.nr = 0;
+    L.R = nullptr;
+    for (int i = 0; i < kMaxLevel; ++i) {
+      Tree *t = f->trees[i];
+      if (t && 2 * t->live < ((int64_t)f->cfg.buffer_size << i)) {
+        L.trees.push_back(t);
+        L.nr += t->live;
+      }
+    }
+    if (!L.trees.empty()) lows.push_back(std::move(L));
+  }
+  if (lows.empty()) return BDL_OK;
+  int st = BDL_OK;
+  for (auto &L : lows) {
+    if (st) break;
+    st = dev_alloc(L.f, &L.R, (size_t)std::max<int64_t>(L.nr, 1) * 4, s);
+    if (!st) st = collect_sorted_live(L.f, L.trees, L.nr, (int32_t *)L.R, s);
+  }
+  std::vector<InsertPlan> plans(lows.size());
+  std::vector<BuildTree> bt;
+  std::vector<ClearedSrc> cl;
+  std::vector<int> bt_plan;
+  if (!st) {
+    for (size_t j = 0; j < lows.size(); ++j) {
+      Low &L = lows[j];
+      L.Fsave = L.f->F;
+      memcpy(L.saved, L.f->trees, sizeof(L.saved));
+      for (Tree *t : L.trees) {
+        L.f->trees[t->level] = nullptr;
+        L.f->F &= ~((uint64_t)1 << t->level);
+      }
+    }
+    for (size_t j = 0; j < lows.size() && !st; ++j) {
+      Low &L = lows[j];
+      if (L.nr == 0) continue;
+      st = plan_insert(L.f, PoolSrc{L.f->buf, L.f->nbuf, (const int32_t *)L.R, 0}, L.nr, plans[j], bt,
+                       cl, s);
+      bt_plan.resize(bt.size(), (int)j);
+    }
+    if (st) {
+      for (auto &ip : plans)
+        if (ip.f) drop_plan(ip, s);
+    } else {
+      Temp tmp(lows[0].f, s);
+      st = build_and_commit(plans, bt, cl, bt_plan, {}, tmp, s);
+    }
+    for (auto &L : lows) {
+      if (st) {                    // put the emptied trees back
+        L.f->F = L.Fsave;
+        memcpy(L.f->trees, L.saved, sizeof(L.saved));
+      } else {
+        for (Tree *t : L.trees) free_tree(L.f, t, s);
+      }
+    }
+  }
+  for (auto &L : lows)
+    if (L.R) dev_free(L.f, L.R, (size_t)std::max<int64_t>(L.nr, 1) * 4, s);
+  return st;
+}
+
+// kNN_L on nf forests: stale buffer trees rebuilt in shared builds, then one
+// k-NN launch per dimension over every forest's queries.
+static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const int64_t *m, int k,
+                    int32_t *const *oi, int64_t *const *od, cudaStream_t s) {
+  if (k < 1 || k > kMaxK) return set_error(BDL_EINVAL, "k must be in 1..32");
+  for (int i = 0; i < nf; ++i) {
+    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
+    if (m[i] < 0) return set_error(BDL_EINVAL, "m < 0");
+    if (m[i] > 0 && (!q[i] || !oi[i] || !od[i])) return set_error(BDL_EINVAL, "NULL pointer");
+  }
+  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
+  refresh_btrees(F, nf, s);
+  Temp tmp(F[0], s);
+  std::vector<ForestView> views(nf);
+  std::vector<KnnCall> calls;
+  for (int i = 0; i < nf; ++i) {
+    if (m[i] == 0) continue;
+    views[i] = knn_view(F[i], false, s);
+    // large batches run in spatial order so that neighbouring threads walk
+    // neighbouring paths; results are written back in input order
+    int32_t *perm = nullptr;
+    if (m[i] >= kSortMinQueries) {
+      void *scratch = nullptr;
+      if (tmp.get(query_sort_bytes(m[i], F[i]->dim), &scratch) == BDL_OK) {
+        perm = (int32_t *)scratch;
+        launch_query_sort(q[i], m[i], F[i]->dim, (char *)scratch + a256((size_t)m[i] * 4), perm, s);
+      }
+    }
+    calls.push_back(KnnCall{&views[i], q[i], perm, m[i], oi[i], od[i]});
+  }
+  int st = BDL_OK;
+  std::vector<int> dims;
+  for (auto &c : calls)
+    if (std::find(dims.begin(), dims.end(), c.fv->dim) == dims.end()) dims.push_back(c.fv->dim);
+  for (int d : dims) {
+    std::vector<KnnCall> g;
+    unsigned long long *stats = nullptr;
+    for (auto &c : calls)
+      if (c.fv->dim == d) g.push_back(c);
+    for (int i = 0; i < nf; ++i)
+      if (F[i]->dim == d && F[i]->knn_stats) stats = F[i]->knn_stats;
+    void *table = nullptr;
+    const size_t tb = knn_table_bytes(g);
+    if (tb) st = tmp.get(tb, &table);
+    if (!st) st = launch_knn_jobs(g, d, k, table, stats, s);
+    if (st) return st;
+  }
+  return BDL_OK;
+}
+
 // With BDL_DEBUG_CHECK=1 every call waits for its kernels and fails with
 // BDL_EINTERNAL if one of them recorded an out-of-range index.
 static int finish(bdl_forest *f, cudaStream_t s, int st) {
@@ -395,6 +1028,12 @@ static int finish(bdl_forest *f, cudaStream_t s, int st) {
 }
 
 int finish_call(bdl_forest *f, cudaStream_t s, int st) { return finish(f, s, st); }
+
+static int finish_many(bdl_forest *const *F, int nf, cudaStream_t s, int st) {
+  for (int i = 0; i < nf && !st; ++i)
+    if (F[i]) st = finish(F[i], s, st);
+  return st;
+}
 
 static int check_config(const bdl_config &c) {
   if (c.leaf_size < 2 || c.leaf_size > 64) return set_error(BDL_EINVAL, "leaf_size must be in 2..64");
@@ -472,28 +1111,17 @@ int bdl_kernel_count(void) { return kKernelCount; }
 const char *bdl_kernel_name(int id) { return id >= 0 && id < kKernelCount ? kKernelNames[id] : ""; }
 
 int bdl_insert(bdl_forest *f, const int32_t *pts, int64_t n, int32_t *out_ids, bdl_stream_t stream) {
-  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
-  if (n < 0) return set_error(BDL_EINVAL, "n < 0");
-  if (n == 0) return BDL_OK;
-  if (!pts) return set_error(BDL_EINVAL, "pts is NULL");
-  if (f->next_id + n > (int64_t)INT32_MAX) return set_error(BDL_EINVAL, "id space (2^31 - 1) exhausted");
+  return bdl_insert_batch(&f, 1, &pts, &n, &out_ids, stream);
+}
+
+int bdl_insert_batch(bdl_forest *const *forests, int nf, const int32_t *const *pts, const int64_t *n,
+                     int32_t *const *out_ids, bdl_stream_t stream) {
+  if (nf < 0 || (nf > 0 && (!forests || !pts || !n || !out_ids))) return set_error(BDL_EINVAL, "NULL array");
+  if (nf == 0) return BDL_OK;
+  if (!forests[0]) return set_error(BDL_EINVAL, "forest is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  DeviceGuard g(f->device);
-  int st = ensure_id_capacity(f, f->next_id + n, s);
-  if (st) return st;
-  cudaMemsetAsync(f->dev_small, 0, 8, s);
-  launch_append_validate(pts, n, f->dim, f->idtab + f->next_id * f->dim, f->dev_small, s);
-  st = sync_read(f, f->dev_small, 1, s);
-  if (st) return st;
-  if (f->pinned[0]) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
-  const int64_t first = f->next_id;
-  st = insert_pool(f, nullptr, first, n, s);
-  if (st) return st;
-  launch_set_alive(f->alive, first, n, s);
-  launch_iota(out_ids, first, n, s);
-  f->next_id += n;
-  f->live += n;
-  return finish(f, s, cuda_check(cudaGetLastError(), "insert"));
+  DeviceGuard g(forests[0]->device);
+  return finish_many(forests, nf, s, insert_many(forests, nf, pts, n, out_ids, s));
 }
 
 int bdl_create(int dim, const bdl_config *cfg, const int32_t *pts, int64_t n, int32_t *out_ids,
@@ -538,138 +1166,37 @@ int bdl_create(int dim, const bdl_config *cfg, const int32_t *pts, int64_t n, in
 }
 
 int bdl_erase(bdl_forest *f, const int32_t *ids, int64_t n, int64_t *out_n, bdl_stream_t stream) {
-  if (out_n) *out_n = 0;
-  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
-  if (n < 0) return set_error(BDL_EINVAL, "n < 0");
-  if (n == 0 || f->next_id == 0) return BDL_OK;
-  if (!ids) return set_error(BDL_EINVAL, "ids is NULL");
+  return bdl_erase_batch(&f, 1, &ids, &n, out_n, stream);
+}
+
+int bdl_erase_batch(bdl_forest *const *forests, int nf, const int32_t *const *ids, const int64_t *n,
+                    int64_t *out_n, bdl_stream_t stream) {
+  if (nf < 0 || (nf > 0 && (!forests || !ids || !n))) return set_error(BDL_EINVAL, "NULL array");
+  if (nf == 0) return BDL_OK;
+  if (!forests[0]) {
+    if (out_n)
+      for (int i = 0; i < nf; ++i) out_n[i] = 0;
+    return set_error(BDL_EINVAL, "forest is NULL");
+  }
   cudaStream_t s = (cudaStream_t)stream;
-  DeviceGuard g(f->device);
-  void *list = nullptr;
-  int st = dev_alloc(f, &list, (size_t)n * 4, s);
-  if (st) return st;
-  // 1. dedup against the live set
-  cudaMemsetAsync(f->dev_small, 0, 8, s);
-  launch_erase_mark(f->alive, f->next_id, ids, n, (int32_t *)list, f->dev_small, s);
-  st = sync_read(f, f->dev_small, 1, s);
-  if (st) { dev_free(f, list, (size_t)n * 4, s); return st; }
-  const int64_t ne = f->pinned[0];
-  if (out_n) *out_n = ne;
-  if (ne == 0) {
-    dev_free(f, list, (size_t)n * 4, s);
-    return BDL_OK;
-  }
-  f->live -= ne;
-  // 2. lazily build the bloom filter of every nonempty tree (Sec. V-A)
-  for (int i = 0; i < kMaxLevel && !st; ++i) {
-    Tree *t = f->trees[i];
-    if (!t || t->live == 0 || t->bloom) continue;
-    int64_t need = (t->size * f->cfg.bloom_bits_per_key + 255) / 256, blocks = 1;
-    while (blocks < need) blocks *= 2;
-    void *b = nullptr;
-    st = dev_alloc(f, &b, (size_t)blocks * 32, s);
-    if (st) break;
-    t->bloom = (uint32_t *)b;
-    t->bloom_blocks = blocks;
-    t->bloom_bytes = (size_t)blocks * 32;
-    cudaMemsetAsync(t->bloom, 0, t->bloom_bytes, s);
-    launch_bloom_build(t, f->dim, f->cfg.hash_seed, s);
-  }
-  if (st) { dev_free(f, list, (size_t)n * 4, s); return st; }
-  // 3. probe, descend, tombstone (Alg. 2 per tree, all trees in one launch);
-  //    large batches descend in spatial order so neighbouring threads share paths
-  ForestView fv = forest_view(f);
-  const int32_t *order = (const int32_t *)list;
-  void *sorted = nullptr;
-  size_t sorted_bytes = 0;
-  if (ne >= kSortMinQueries) {
-    sorted_bytes = a256((size_t)ne * 4) + query_sort_bytes(ne, f->dim);
-    if (dev_alloc(f, &sorted, sorted_bytes, s) == BDL_OK) {
-      launch_point_sort(f->idtab, (const int32_t *)list, ne, f->dim,
-                        (char *)sorted + a256((size_t)ne * 4), (int32_t *)sorted, s);
-      order = (const int32_t *)sorted;
-    } else {
-      sorted = nullptr;   // same result in input order
-    }
-  }
-  launch_erase_locate(fv, f->cfg.hash_seed, order, ne, s);
-  if (sorted) dev_free(f, sorted, sorted_bytes, s);
-  for (int i = 0; i < kMaxLevel; ++i)   // live counts changed: refresh the k-NN records
-    if (f->trees[i]) launch_pack_lives(f->trees[i], f->dim, s);
-  // 4. the buffer
-  launch_buffer_compact(f->buf, f->nbuf, f->alive, f->dev_small, s);
-  launch_gather_roots(fv, f->dev_small + 1, s);
-  st = sync_read(f, f->dev_small, 1 + fv.ntrees, s);
-  dev_free(f, list, (size_t)n * 4, s);
-  if (st) return st;
-  if (f->pinned[0] != f->nbuf) f->buf_dirty = true;
-  f->nbuf = f->pinned[0];
-  for (int j = 0; j < fv.ntrees; ++j) f->trees[fv.tree[j].level]->live = f->pinned[1 + j];
-  // 5. trees below half capacity (Alg. 4 lines 3-4)
-  std::vector<Tree *> low;
-  int64_t nr = 0;
-  for (int i = 0; i < kMaxLevel; ++i) {
-    Tree *t = f->trees[i];
-    if (t && 2 * t->live < ((int64_t)f->cfg.buffer_size << i)) {
-      low.push_back(t);
-      nr += t->live;
-    }
-  }
-  if (low.empty()) return finish(f, s, cuda_check(cudaGetLastError(), "erase"));
-  void *R = nullptr;
-  st = dev_alloc(f, &R, (size_t)std::max<int64_t>(nr, 1) * 4, s);
-  if (!st) st = collect_sorted_live(f, low, nr, (int32_t *)R, s);
-  if (st) {
-    dev_free(f, R, (size_t)std::max<int64_t>(nr, 1) * 4, s);
-    return st;
-  }
-  uint64_t Fsave = f->F;
-  Tree *saved[kMaxLevel];
-  memcpy(saved, f->trees, sizeof(saved));
-  for (Tree *t : low) {
-    f->trees[t->level] = nullptr;
-    f->F &= ~((uint64_t)1 << t->level);
-  }
-  st = insert_pool(f, (const int32_t *)R, 0, nr, s);
-  if (st) {
-    // reinsertion failed: keep the emptied trees where they were (still exact)
-    f->F = Fsave;
-    memcpy(f->trees, saved, sizeof(saved));
-  } else {
-    for (Tree *t : low) free_tree(f, t, s);
-  }
-  dev_free(f, R, (size_t)std::max<int64_t>(nr, 1) * 4, s);
-  if (st) return st;
-  return finish(f, s, cuda_check(cudaGetLastError(), "erase"));
+  DeviceGuard g(forests[0]->device);
+  return finish_many(forests, nf, s, erase_many(forests, nf, ids, n, out_n, s));
 }
 
 int bdl_knn(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids, int64_t *out_d2,
             bdl_stream_t stream) {
-  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
-  if (k < 1 || k > kMaxK) return set_error(BDL_EINVAL, "k must be in 1..32");
-  if (m < 0) return set_error(BDL_EINVAL, "m < 0");
-  if (m == 0) return BDL_OK;
-  if (!q || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL pointer");
-  DeviceGuard g(f->device);
+  return bdl_knn_batch(&f, 1, &q, &m, k, &out_ids, &out_d2, stream);
+}
+
+int bdl_knn_batch(bdl_forest *const *forests, int nf, const int32_t *const *q, const int64_t *m, int k,
+                  int32_t *const *out_ids, int64_t *const *out_d2, bdl_stream_t stream) {
+  if (nf < 0 || (nf > 0 && (!forests || !q || !m || !out_ids || !out_d2)))
+    return set_error(BDL_EINVAL, "NULL array");
+  if (nf == 0) return BDL_OK;
+  if (!forests[0]) return set_error(BDL_EINVAL, "forest is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  ForestView fv = knn_view(f, true, s);
-  // large batches run in spatial order so that neighbouring threads walk
-  // neighbouring paths; results are written back in input order
-  void *scratch = nullptr;
-  size_t sbytes = 0;
-  int32_t *perm = nullptr;
-  if (m >= kSortMinQueries) {
-    sbytes = query_sort_bytes(m, f->dim);
-    if (dev_alloc(f, &scratch, sbytes, s) == BDL_OK) {
-      perm = (int32_t *)scratch;
-      launch_query_sort(q, m, f->dim, (char *)scratch + ((size_t)m * 4 + 255) / 256 * 256, perm, s);
-    } else {
-      scratch = nullptr;   // fall back to input order (same results)
-    }
-  }
-  int st = launch_knn(fv, q, perm, m, k, out_ids, out_d2, f->knn_stats, s);
-  if (scratch) dev_free(f, scratch, sbytes, s);
-  return finish(f, s, st);
+  DeviceGuard g(forests[0]->device);
+  return finish_many(forests, nf, s, knn_many(forests, nf, q, m, k, out_ids, out_d2, s));
 }
 
 int bdl_size(const bdl_forest *f, int64_t *out) {

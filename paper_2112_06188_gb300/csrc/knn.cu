@@ -94,21 +94,34 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
   return s * (1.0f - 3.814697265625e-06f);   // 1 - 2^-18
 }
 
+// Largest j in [0, n) with pre[j] <= x (pre[0] = 0 <= x < pre[n]).
+__device__ __forceinline__ int knn_find(const int64_t *pre, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Query t of job J (one forest's batch) against the trees trees[0 ..
+// J.ntrees).  Called by whole warps of one job, which stay resident and
+// converged until each of their lanes is done.
 template <int D, bool STATS>
-__global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, const int32_t *qs,
-                                                         const int32_t *perm, int64_t m, int k,
-                                                         int32_t *out_ids, int64_t *out_d2,
-                                                         unsigned long long *stats) {
+__device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees, int64_t t, int k,
+                                          unsigned long long *stats) {
   // k (d2, id) slots per thread: [slot][thread]
   extern __shared__ __align__(8) unsigned char knn_sm[];
   uint64_t *s_d = reinterpret_cast<uint64_t *>(knn_sm);
   int32_t *s_id = reinterpret_cast<int32_t *>(s_d + (size_t)k * kKnnThreads);
-  // whole warps stay resident (and converged) until every lane is done
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((t & ~(int64_t)31) >= m) return;
+  const int64_t m = J.m;
+  const int32_t *qs = J.q, *perm = J.perm;
+  int32_t *out_ids = J.oi;
+  int64_t *out_d2 = J.od;
   const bool active = t < m;
   const int64_t qi = active ? (perm ? perm[t] : t) : 0;
-  const int dim = D ? D : F.dim;
+  const int dim = D ? D : J.dim;
   const int rec = packed_node_ints(dim);
   const int rs = rec_ints(dim);
   int32_t q[D ? D : kMaxDim];
@@ -122,8 +135,9 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
   float smd[kStack];
   const float kInf = __int_as_float(0x7f800000);
 
-  for (int ti = 0; ti < F.ntrees; ++ti) {
-    const TreeView &T = F.tree[ti];
+  const int ntrees = J.ntrees;
+  for (int ti = 0; ti < ntrees; ++ti) {
+    const TreeView &T = trees[ti];
     if (T.live[0] <= 0) continue;
     // code >= 0: internal node record; code < 0: leaf -1-code
     int sp = 0;
@@ -187,7 +201,7 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
       if (code < 0) {
         leaf = -1 - code;
       } else if (code >= ninternal || sp + 2 > kStack) {
-        atomicOr(F.err, code >= ninternal ? kErrChild : kErrStack);
+        atomicOr(J.err, code >= ninternal ? kErrChild : kErrStack);
       } else {
         const int32_t *r = T.pk + (int64_t)code * rec;
         int4 hdr;
@@ -228,11 +242,11 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
       }
       if (leaf >= 0) {
         if (leaf > ninternal) {
-          atomicOr(F.err, kErrChild);
+          atomicOr(J.err, kErrChild);
         } else {
           pa = T.leaf_off[leaf];
           pz = T.leaf_off[leaf + 1];
-          if (pa < 0 || pz > T.size || pa > pz) atomicOr(F.err, kErrLeaf);
+          if (pa < 0 || pz > T.size || pa > pz) atomicOr(J.err, kErrLeaf);
           else pending = true;
         }
       }
@@ -240,9 +254,9 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
   }
   if (!active) return;
   // the buffer tree: exact scan of its points
-  for (int64_t j = 0; j < F.nbuf; ++j) {
-    const int32_t id = F.buf[j];
-    const int32_t *p = F.idtab + (int64_t)id * dim;
+  for (int64_t j = 0; j < J.nbuf; ++j) {
+    const int32_t id = J.buf[j];
+    const int32_t *p = J.idtab + (int64_t)id * dim;
     uint64_t s = 0;
 #pragma unroll
     for (int c = 0; c < (D ? D : kMaxDim); ++c) {
@@ -267,16 +281,53 @@ __global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const ForestView F, con
   }
 }
 
+// Many forests: every warp finds its job in the table (jobs are warp-aligned).
+template <int D, bool STATS>
+__global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const KnnJob *jobs, const int64_t *job_warp,
+                                                         int njobs, int k,
+                                                         unsigned long long *stats) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= job_warp[njobs]) return;
+  const int jb = knn_find(job_warp, njobs, w);
+  knn_query<D, STATS>(jobs[jb], jobs[jb].trees, (w - job_warp[jb]) * 32 + (threadIdx.x & 31), k, stats);
+}
+
+// One forest: its job and tree views travel as kernel parameters, read
+// through the constant cache (the per-tree fields are warp-uniform).
+struct KnnOne {
+  KnnJob job;
+  TreeView trees[kMaxLevel];
+};
+
+template <int D, bool STATS>
+__global__ void __launch_bounds__(kKnnThreads, 12) k_knn_one(const __grid_constant__ KnnOne P, int k,
+                                                             unsigned long long *stats) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~(int64_t)31) >= P.job.m) return;     // whole warp past the end
+  knn_query<D, STATS>(P.job, P.trees, t, k, stats);
+}
+
 template <int D>
-void launch_d(const ForestView &fv, const int32_t *q, const int32_t *perm, int64_t m, int k,
-              int32_t *oi, int64_t *od, unsigned long long *stats, cudaStream_t s) {
+void launch_d(const KnnJob *jobs, const int64_t *job_warp, int njobs, int64_t warps, int k,
+              unsigned long long *stats, cudaStream_t s) {
   const size_t smem = (size_t)k * kKnnThreads * 12;   // <= 48 KB for k <= 32
   KScope ks_(kK_knn, s);
-  const unsigned grid = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
+  const unsigned grid = (unsigned)((warps * 32 + kKnnThreads - 1) / kKnnThreads);
   if (stats)
-    k_knn<D, true><<<grid, kKnnThreads, smem, s>>>(fv, q, perm, m, k, oi, od, stats);
+    k_knn<D, true><<<grid, kKnnThreads, smem, s>>>(jobs, job_warp, njobs, k, stats);
   else
-    k_knn<D, false><<<grid, kKnnThreads, smem, s>>>(fv, q, perm, m, k, oi, od, stats);
+    k_knn<D, false><<<grid, kKnnThreads, smem, s>>>(jobs, job_warp, njobs, k, stats);
+}
+
+template <int D>
+void launch_one(const KnnOne &P, int k, unsigned long long *stats, cudaStream_t s) {
+  const size_t smem = (size_t)k * kKnnThreads * 12;
+  KScope ks_(kK_knn, s);
+  const unsigned grid = (unsigned)((P.job.m + kKnnThreads - 1) / kKnnThreads);
+  if (stats)
+    k_knn_one<D, true><<<grid, kKnnThreads, smem, s>>>(P, k, stats);
+  else
+    k_knn_one<D, false><<<grid, kKnnThreads, smem, s>>>(P, k, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -284,11 +335,18 @@ void launch_d(const ForestView &fv, const int32_t *q, const int32_t *perm, int64
 // h internal levels (a complete tree of its own)
 // ---------------------------------------------------------------------------
 
-__global__ void k_pack_nodes(const Node *node, const int32_t *box, const int32_t *live, int h,
-                             int dim, int32_t *pk) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nint = ((int64_t)1 << h) - 1;
-  if (g >= nint) return;
+// One thread per internal node of many trees (table entry j owns the work
+// items pre[j] .. pre[j+1]-1, one per internal node of tree j).
+__global__ void k_pack_nodes(const TreeSeg *segs, const int64_t *pre, int nseg) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[nseg]) return;
+  const int j = knn_find(pre, nseg, x);
+  const TreeSeg &T = segs[j];
+  const Node *node = T.node;
+  const int32_t *box = T.box, *live = T.live;
+  const int h = T.h, dim = T.dim;
+  int32_t *pk = T.pk;
+  const int64_t g = x - pre[j];
   const int t = 63 - __clzll(g + 1);          // depth of the g-th internal node (BFS order)
   const int64_t i = g + 1 - ((int64_t)1 << t);
   const int64_t v = veb_slot(h + 1, t, i);    // slot among all nodes
@@ -420,44 +478,105 @@ __global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m,
 
 }  // namespace
 
-int launch_knn(const ForestView &fv, const int32_t *q, const int32_t *perm, int64_t m, int k,
-               int32_t *out_ids, int64_t *out_d2, unsigned long long *stats, cudaStream_t s) {
-  if (m <= 0) return BDL_OK;
-  switch (fv.dim) {
-    case 2: launch_d<2>(fv, q, perm, m, k, out_ids, out_d2, stats, s); break;
-    case 3: launch_d<3>(fv, q, perm, m, k, out_ids, out_d2, stats, s); break;
-    case 5: launch_d<5>(fv, q, perm, m, k, out_ids, out_d2, stats, s); break;
-    case 7: launch_d<7>(fv, q, perm, m, k, out_ids, out_d2, stats, s); break;
-    default: launch_d<0>(fv, q, perm, m, k, out_ids, out_d2, stats, s); break;
+size_t knn_table_bytes(const std::vector<KnnCall> &calls) {
+  if (calls.size() == 1) return 0;   // one forest: no table (kernel parameters)
+  size_t n = calls.size(), views = 0;
+  for (const auto &c : calls) views += (size_t)c.fv->ntrees;
+  return n * sizeof(KnnJob) + (n + 1) * 8 + views * sizeof(TreeView) + 64;
+}
+
+int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,
+                    unsigned long long *stats, cudaStream_t s) {
+  const size_t n = calls.size();
+  if (n == 1) {
+    const KnnCall &c = calls[0];
+    if (c.m == 0) return BDL_OK;
+    KnnOne P;
+    memset(&P, 0, sizeof(P));
+    P.job.ntrees = c.fv->ntrees;
+    P.job.dim = c.fv->dim;
+    P.job.idtab = c.fv->idtab;
+    P.job.buf = c.fv->buf;
+    P.job.nbuf = c.fv->nbuf;
+    P.job.err = c.fv->err;
+    P.job.q = c.q;
+    P.job.perm = c.perm;
+    P.job.m = c.m;
+    P.job.oi = c.oi;
+    P.job.od = c.od;
+    for (int t = 0; t < c.fv->ntrees; ++t) P.trees[t] = c.fv->tree[t];
+    switch (dim) {
+      case 2: launch_one<2>(P, k, stats, s); break;
+      case 3: launch_one<3>(P, k, stats, s); break;
+      case 5: launch_one<5>(P, k, stats, s); break;
+      case 7: launch_one<7>(P, k, stats, s); break;
+      default: launch_one<0>(P, k, stats, s); break;
+    }
+    return cuda_check(cudaGetLastError(), "knn kernel");
+  }
+  // host image: jobs, warp prefix, tree views; its pointers point into `table`
+  std::vector<unsigned char> img(knn_table_bytes(calls));
+  KnnJob *jobs = (KnnJob *)img.data();
+  int64_t *warp = (int64_t *)(img.data() + n * sizeof(KnnJob));
+  const size_t views_off = n * sizeof(KnnJob) + (n + 1) * 8;
+  TreeView *views = (TreeView *)(img.data() + views_off);
+  size_t v = 0;
+  warp[0] = 0;
+  for (size_t j = 0; j < n; ++j) {
+    const KnnCall &c = calls[j];
+    KnnJob &J = jobs[j];
+    memset(&J, 0, sizeof(J));
+    J.trees = (const TreeView *)((char *)table + views_off) + v;
+    J.ntrees = c.fv->ntrees;
+    J.dim = c.fv->dim;
+    J.idtab = c.fv->idtab;
+    J.buf = c.fv->buf;
+    J.nbuf = c.fv->nbuf;
+    J.err = c.fv->err;
+    J.q = c.q;
+    J.perm = c.perm;
+    J.m = c.m;
+    J.oi = c.oi;
+    J.od = c.od;
+    for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
+    warp[j + 1] = warp[j] + (c.m + 31) / 32;
+  }
+  if (warp[n] == 0) return BDL_OK;
+  int st = h2d(table, img.data(), img.size(), s);
+  if (st) return st;
+  const KnnJob *dj = (const KnnJob *)table;
+  const int64_t *dw = (const int64_t *)((char *)table + n * sizeof(KnnJob));
+  switch (dim) {
+    case 2: launch_d<2>(dj, dw, (int)n, warp[n], k, stats, s); break;
+    case 3: launch_d<3>(dj, dw, (int)n, warp[n], k, stats, s); break;
+    case 5: launch_d<5>(dj, dw, (int)n, warp[n], k, stats, s); break;
+    case 7: launch_d<7>(dj, dw, (int)n, warp[n], k, stats, s); break;
+    default: launch_d<0>(dj, dw, (int)n, warp[n], k, stats, s); break;
   }
   return cuda_check(cudaGetLastError(), "knn kernel");
 }
 
-void launch_pack_nodes(const Tree *t, int dim, cudaStream_t s) {
-  int64_t nint = ((int64_t)1 << t->h) - 1;
-  if (nint <= 0) return;
-  KScope ks_(kK_pack_nodes, s);
-  k_pack_nodes<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(t->node, t->box, t->live_nodes, t->h,
-                                                               dim, t->pk);
+void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<TreeSeg> &segs,
+                        std::vector<int64_t> &pre) {
+  pre.assign(1, 0);
+  for (const Tree *t : trees) {
+    TreeSeg g;
+    memset(&g, 0, sizeof(g));
+    g.dim = dim;
+    g.h = t->h;
+    g.node = t->node;
+    g.box = t->box;
+    g.live = t->live_nodes;
+    g.pk = t->pk;
+    segs.push_back(g);
+    pre.push_back(pre.back() + (((int64_t)1 << t->h) - 1));
+  }
 }
 
-// After an erase only the live counts of the packed records change.
-__global__ void k_pack_lives(const Node *node, const int32_t *live, int h, int dim, int32_t *pk) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nint = ((int64_t)1 << h) - 1;
-  if (g >= nint) return;
-  const int t = 63 - __clzll(g + 1);
-  const int64_t i = g + 1 - ((int64_t)1 << t);
-  const Node nd = node[veb_slot(h + 1, t, i)];
-  int2 lv = make_int2(live[nd.l], live[nd.r]);
-  *reinterpret_cast<int2 *>(pk + veb_slot(h, t, i) * packed_node_ints(dim) + 2) = lv;
-}
-
-void launch_pack_lives(const Tree *t, int dim, cudaStream_t s) {
-  int64_t nint = ((int64_t)1 << t->h) - 1;
-  if (nint <= 0) return;
+void launch_pack_nodes(const TreeSeg *segs, const int64_t *pre, int nseg, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
   KScope ks_(kK_pack_nodes, s);
-  k_pack_lives<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(t->node, t->live_nodes, t->h, dim, t->pk);
+  k_pack_nodes<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(segs, pre, nseg);
 }
 
 size_t query_sort_bytes(int64_t m, int dim) {
@@ -554,7 +673,9 @@ extern "C" int bdl_knn_noalloc(bdl_forest *f, const int32_t *q, int64_t m, int k
       perm = (int32_t *)scratch;
       launch_query_sort(q, m, f->dim, (char *)scratch + kNoAllocPermBytes, perm, s);
     }
-    st = finish_call(f, s, launch_knn(fv, q, perm, m, k, out_ids, out_d2, f->knn_stats, s));
+    // a single forest's job goes by kernel parameters: no table to place
+    std::vector<KnnCall> calls{KnnCall{&fv, q, perm, m, out_ids, out_d2}};
+    st = finish_call(f, s, launch_knn_jobs(calls, f->dim, k, nullptr, f->knn_stats, s));
   }
   if (prev >= 0 && prev != f->device) cudaSetDevice(prev);
   return st;

@@ -17,6 +17,10 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
 
 
+def _addr(t):
+    return t.data_ptr() if t is not None and t.numel() else None
+
+
 def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -166,3 +170,45 @@ class Forest:
             return tuple(int(x) for x in out)
         capi.check(capi.bdl_knn_stats(self._h, 1 if enable else 0, None), "bdl_knn_stats")
         return None
+
+
+# --- batched forests: one call for many independent forests -----------------
+
+def _batch_stream(forests, stream):
+    if stream is None and forests:
+        stream = forests[0]._stream()
+    return _stream_handle(stream)
+
+
+def insert_batch(forests, points, stream=None):
+    """Insert_L on every forest; points[i] is a device tensor [n_i, dim_i].
+    Returns the list of id tensors."""
+    ps = [p.to(torch.int32).contiguous().reshape(-1, f.dim) for f, p in zip(forests, points)]
+    ids = [torch.empty(p.shape[0], dtype=torch.int32, device=p.device) for p in ps]
+    capi.check(capi.bdl_insert_batch([f._h for f in forests], [_addr(p) for p in ps],
+                                     [p.shape[0] for p in ps], [_addr(i) for i in ids],
+                                     _batch_stream(forests, stream)), "bdl_insert_batch")
+    return ids
+
+
+def erase_batch(forests, ids, stream=None):
+    """Erase_L on every forest; returns the list of counts erased."""
+    ts = [i.to(torch.int32).contiguous().reshape(-1) for i in ids]
+    st, n = capi.bdl_erase_batch([f._h for f in forests], [_addr(t) for t in ts],
+                                 [t.shape[0] for t in ts], _batch_stream(forests, stream))
+    capi.check(st, "bdl_erase_batch")
+    return n
+
+
+def knn_batch(forests, queries, k, out=None, stream=None):
+    """kNN_L on every forest; queries[i] is a device tensor [m_i, dim_i].
+    Returns a list of (ids [m_i, k], d2 [m_i, k])."""
+    qs = [q.to(torch.int32).contiguous().reshape(-1, f.dim) for f, q in zip(forests, queries)]
+    if out is None:
+        out = [(torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device),
+                torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)) for q in qs]
+    capi.check(capi.bdl_knn_batch([f._h for f in forests], [_addr(q) for q in qs],
+                                  [q.shape[0] for q in qs], k, [_addr(o[0]) for o in out],
+                                  [_addr(o[1]) for o in out], _batch_stream(forests, stream)),
+               "bdl_knn_batch")
+    return out

@@ -1,0 +1,221 @@
+"""Batched forests through bdl_insert_batch / bdl_erase_batch / bdl_knn_batch.
+
+One call on many independent forests must give every forest exactly what the
+single-forest calls give (same trees, node for node, same buffers, same bloom
+words, same k-NN rows), and what the oracle gives.  The workload is many small
+forests of log-uniform sizes in 2-D and 3-D with insert batches of 5-20%,
+delete batches of 2-10% (some far larger, so that trees fall below half and
+are rebuilt) and k = 8 queries per forest.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.oracle import OracleForest
+from paper_2112_06188_gb300 import inputs
+from tests.treecheck import assert_same_tree
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_06188_gb300 import build_lib
+    build_lib.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def log_uniform(n, lo, hi, seed):
+    r = np.random.default_rng(seed)
+    return np.exp(r.uniform(np.log(lo), np.log(hi), size=n)).astype(np.int64)
+
+
+def same_state(a, b, what):
+    """Two forests (GPU/GPU or GPU/oracle) hold the same structure."""
+    assert a.tree_mask() == b.tree_mask(), what
+    assert np.array_equal(np.sort(a.buffer_ids()), np.sort(b.buffer_ids())), what
+    assert a.size() == b.size(), what
+    for lvl in b.tree_levels():
+        ta, tb = a.tree(lvl), b.tree(lvl)
+        assert_same_tree(ta, tb, "%s tree %d" % (what, lvl))
+        assert (ta["bloom"] is None) == (tb["bloom"] is None), what
+        if ta["bloom"] is not None:
+            assert np.array_equal(ta["bloom"], tb["bloom"]), "%s bloom %d" % (what, lvl)
+
+
+class Workload:
+    """nf forests, a live set per forest, seeded batches."""
+
+    def __init__(self, nf, lo, hi, dims, seed, configs=None):
+        from paper_2112_06188_gb300.forest import Forest
+        self.rng = np.random.default_rng(seed)
+        self.sizes = log_uniform(nf, lo, hi, seed)
+        self.dims = [dims[i % len(dims)] for i in range(nf)]
+        self.configs = configs or [dict(leaf_size=16, buffer_size=1024)] * nf
+        self.A = [Forest(d, **c) for d, c in zip(self.dims, self.configs)]   # batched calls
+        self.B = [Forest(d, **c) for d, c in zip(self.dims, self.configs)]   # single calls
+        self.live = [inputs.LiveSet(d) for d in self.dims]
+
+    def points(self, i, n):
+        return self.rng.integers(0, 1 << 20, size=(n, self.dims[i]), dtype=np.int32)
+
+    def close(self):
+        for f in self.A + self.B:
+            f.close()
+
+
+def run_insert(w, pts):
+    from paper_2112_06188_gb300.forest import insert_batch
+    ids_a = insert_batch(w.A, [dev(p) for p in pts])
+    for i, p in enumerate(pts):
+        ids_b = w.B[i].insert(dev(p))
+        want = w.live[i].insert(p)
+        assert np.array_equal(ids_a[i].cpu().numpy(), want)
+        assert np.array_equal(ids_b.cpu().numpy(), want)
+
+
+def run_erase(w, ids):
+    from paper_2112_06188_gb300.forest import erase_batch
+    na = erase_batch(w.A, [dev(e) for e in ids])
+    for i, e in enumerate(ids):
+        nb = w.B[i].erase(dev(e))
+        assert na[i] == nb == w.live[i].erase(e)
+
+
+def run_knn(w, k, m_lo, m_hi):
+    from paper_2112_06188_gb300.forest import knn_batch
+    qs = []
+    for i in range(len(w.A)):
+        m = int(w.rng.integers(m_lo, m_hi + 1))
+        lp = w.live[i].coords[w.live[i].alive]
+        q = inputs.queries_from(lp, m, seed=int(w.rng.integers(1 << 30))) if len(lp) else w.points(i, m)
+        qs.append(q)
+    out = knn_batch(w.A, [dev(q) for q in qs], k)
+    rows = []
+    for i, q in enumerate(qs):
+        bi, bd = w.B[i].knn(dev(q), k)
+        ai, ad = out[i]
+        assert torch.equal(ai, bi) and torch.equal(ad, bd), "forest %d" % i
+        rows.append((q, ai.cpu().numpy(), ad.cpu().numpy()))
+    return rows
+
+
+def test_batch_equals_single_calls_and_oracle():
+    nf = 24
+    w = Workload(nf, 500, 60000, dims=(2, 3), seed=11)
+    ora = {i: OracleForest(w.dims[i], leaf_size=16, buffer_size=1024) for i in range(0, nf, 6)}
+
+    def check(tag):
+        for i in range(nf):
+            same_state(w.A[i], w.B[i], "%s forest %d" % (tag, i))
+        for i, o in ora.items():
+            same_state(w.A[i], o, "%s forest %d vs oracle" % (tag, i))
+
+    pts = [w.points(i, int(w.sizes[i])) for i in range(nf)]
+    run_insert(w, pts)
+    for i, o in ora.items():
+        o.insert(pts[i])
+    check("build")
+    for step in range(3):
+        frac = w.rng.uniform(0.05, 0.20, size=nf)
+        pts = [w.points(i, max(1, int(frac[i] * w.sizes[i]))) for i in range(nf)]
+        run_insert(w, pts)
+        for i, o in ora.items():
+            o.insert(pts[i])
+        dfrac = w.rng.uniform(0.02, 0.10, size=nf)
+        if step == 1:
+            dfrac[::4] = 0.6          # these fall below half: rebuilds in several forests at once
+        ids = []
+        for i in range(nf):
+            lid = w.live[i].live_ids()
+            ids.append(inputs.sample_ids(lid, max(1, int(dfrac[i] * len(lid))), seed=100 * step + i))
+        for i, o in ora.items():
+            assert o.erase(ids[i]) == int(np.isin(ids[i], w.live[i].live_ids()).sum())
+        run_erase(w, ids)
+        check("step %d" % step)
+        rows = run_knn(w, 8, 1000, 5000)
+        for i, o in ora.items():
+            q, gi, gd = rows[i]
+            oi, od = o.knn(q, 8)
+            assert np.array_equal(gi, oi) and np.array_equal(gd, od), "forest %d vs oracle" % i
+    w.close()
+
+
+def test_batch_mixed_dims_and_configs():
+    """Forests of dimensions 2, 3, 5 and 7, different leaf sizes, buffer sizes and
+    bloom seeds in the same calls."""
+    configs = [dict(leaf_size=16, buffer_size=1024), dict(leaf_size=8, buffer_size=512, hash_seed=7),
+               dict(leaf_size=32, buffer_size=2048, bloom_bits_per_key=8),
+               dict(leaf_size=4, buffer_size=256, hash_seed=123456789)]
+    nf = 12
+    w = Workload(nf, 300, 30000, dims=(2, 3, 5, 7), seed=5,
+                 configs=[configs[i % 4] for i in range(nf)])
+    run_insert(w, [w.points(i, int(w.sizes[i])) for i in range(nf)])
+    for step in range(2):
+        ids = [inputs.sample_ids(w.live[i].live_ids(), max(1, len(w.live[i].live_ids()) // 3),
+                                 seed=step * 50 + i) for i in range(nf)]
+        run_erase(w, ids)
+        run_insert(w, [w.points(i, int(w.sizes[i]) // 7 + 1) for i in range(nf)])
+        for i in range(nf):
+            same_state(w.A[i], w.B[i], "forest %d" % i)
+        run_knn(w, 5, 1, 700)
+    w.close()
+
+
+def test_batch_large_queries_sorted_path():
+    """Query batches above the spatial-sort threshold in some forests, below it in others."""
+    w = Workload(4, 40000, 120000, dims=(3,), seed=9)
+    run_insert(w, [w.points(i, int(w.sizes[i])) for i in range(4)])
+    run_knn(w, 10, 20000, 50000)
+    w.close()
+
+
+def test_batch_all_or_nothing_on_bad_coordinate():
+    from paper_2112_06188_gb300 import capi
+    from paper_2112_06188_gb300.forest import insert_batch
+    w = Workload(3, 2000, 5000, dims=(2,), seed=3)
+    run_insert(w, [w.points(i, int(w.sizes[i])) for i in range(3)])
+    before = [(f.tree_mask(), f.size(), list(f.buffer_ids())) for f in w.A]
+    pts = [w.points(i, 3000) for i in range(3)]
+    pts[2][1234, 1] = 1 << 20
+    with pytest.raises(capi.BdlError) as e:
+        insert_batch(w.A, [dev(p) for p in pts])
+    assert e.value.status == capi.BDL_EINVAL
+    assert [(f.tree_mask(), f.size(), list(f.buffer_ids())) for f in w.A] == before
+    pts[2][1234, 1] = 5
+    run_insert(w, pts)                 # ids continue where they were
+    for i in range(3):
+        same_state(w.A[i], w.B[i], "forest %d" % i)
+    w.close()
+
+
+def test_batch_argument_rules():
+    from paper_2112_06188_gb300 import capi
+    from paper_2112_06188_gb300.forest import Forest, erase_batch, insert_batch, knn_batch
+    f, g = Forest(2), Forest(2)
+    p = dev(inputs.uniform_points(3000, 2, seed=1))
+    with pytest.raises(capi.BdlError):
+        insert_batch([f, f], [p, p])
+    assert f.size() == 0
+    insert_batch([f, g], [p, p[:100]])
+    with pytest.raises(capi.BdlError):
+        erase_batch([g, g], [dev(np.arange(5, dtype=np.int32))] * 2)
+    assert g.size() == 100
+    # the same forest twice in a k-NN batch is allowed
+    q = dev(inputs.uniform_points(50, 2, seed=2))
+    (a_i, a_d), (b_i, b_d) = knn_batch([f, f], [q, q[:7]], 4)
+    s_i, s_d = f.knn(q, 4)
+    assert torch.equal(a_i, s_i) and torch.equal(b_i, s_i[:7]) and torch.equal(b_d, s_d[:7])
+    # empty batches and empty entries
+    assert insert_batch([], []) == []
+    assert erase_batch([f, g], [dev(np.zeros(0, np.int32)), dev(np.array([3, 3, -1], np.int32))]) == [0, 1]
+    out = knn_batch([f, g], [dev(np.zeros((0, 2), np.int32)), q], 3)
+    assert out[0][0].shape == (0, 3)
+    assert torch.equal(out[1][0], g.knn(q, 3)[0])
+    f.close()
+    g.close()
