@@ -16,6 +16,8 @@
  *   Alg. 5       kNN_L: one tree at a time, largest first (Sec. V-B)
  *   Sec. V-A     per-tree bloom filter, built lazily before the first erase
  *   Sec. V-D     leaves hold up to L points
+ *   Sec. V-C     the spatial-median splitting rule, as an alternative to the
+ *                object median (orc_forest_set_split)
  * plus brute-force exact k-NN (the closed-form definition of the result).
  *
  * Readings where the paper is silent, ambiguous or garbled are stated at the
@@ -69,6 +71,7 @@ typedef struct {
 
 typedef struct {
     int dim, L, X, bpk;
+    int split;              /* 0: object median (default), 1: spatial median */
     uint64_t seed;
     int32_t *coord;         /* id table: [id][dim] */
     unsigned char *alive;   /* [id] */
@@ -144,7 +147,36 @@ static void build_rec(obuild *b, int64_t lo, int64_t hi, int64_t idx, int c, int
         nd->lo = lo;
         nd->hi = hi;
         t->bfs2veb[((int64_t)1 << depth) - 1 + bfs] = idx;
-        if (top) {
+        if (top && f->split == 1) {
+            /* Spatial median (Sec. V-C): the splitting value is the average of
+             * the smallest and largest coordinate c among the node's points,
+             * and the points are partitioned around it.
+             * Reading G12: on the integer grid the average is rounded down,
+             * v = floor((min + max) / 2); points with coordinate <= v go left.
+             * The stored key is (v << 31) | (2^31 - 1), so that a point's
+             * composite key is <= it exactly when its coordinate is <= v and
+             * descents by key stay as for the object median.  The tree keeps
+             * the shape of reading G2 (h split levels), so children may hold
+             * any number of points, none included; an empty node's v is 0. */
+            int64_t m = hi - lo;
+            int32_t mn = INT32_MAX, mx = INT32_MIN;
+            for (int64_t i = lo; i < hi; i++) {
+                int32_t x = f->coord[(int64_t)b->ids[i] * f->dim + c];
+                if (x < mn) mn = x;
+                if (x > mx) mx = x;
+            }
+            int64_t v = m > 0 ? ((int64_t)mn + (int64_t)mx) / 2 : 0;
+            int64_t nl = 0;
+            for (int64_t i = lo; i < hi; i++)      /* left part first, stable */
+                if (f->coord[(int64_t)b->ids[i] * f->dim + c] <= v) b->tmp[nl++].id = b->ids[i];
+            int64_t nr = nl;
+            for (int64_t i = lo; i < hi; i++)
+                if (f->coord[(int64_t)b->ids[i] * f->dim + c] > v) b->tmp[nr++].id = b->ids[i];
+            for (int64_t i = 0; i < m; i++) b->ids[lo + i] = b->tmp[i].id;
+            nd->is_leaf = 0;
+            nd->key = (v << 31) | (int64_t)0x7FFFFFFF;
+            nd->mid = lo + nl;
+        } else if (top) {
             /* median partition in dimension c (Sec. V-C: by sorting).
              * Reading G3: the left child takes the ceil(m/2) smallest composite
              * keys; the node stores the largest key of the left child. */
@@ -614,6 +646,15 @@ void *orc_forest_new(int dim, int leaf_size, int buffer_size, int bloom_bits_per
     f->alive = (unsigned char *)xcalloc((size_t)f->cap_ids, 1);
     f->buf = (int32_t *)xmalloc((size_t)buffer_size * sizeof(int32_t));
     return f;
+}
+
+/* Splitting rule of the trees built from now on: 0 object median, 1 spatial
+ * median (Sec. V-C).  Returns 0, or -1 for an unknown rule. */
+int orc_forest_set_split(void *h, int split)
+{
+    if (split != 0 && split != 1) return -1;
+    ((oforest *)h)->split = split;
+    return 0;
 }
 
 void orc_forest_free(void *h)

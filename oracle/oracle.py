@@ -40,6 +40,8 @@ def lib():
         L.orc_forest_new.restype = P
         L.orc_forest_new.argtypes = [i32, i32, i32, i32, u64]
         L.orc_forest_free.argtypes = [P]
+        L.orc_forest_set_split.restype = i32
+        L.orc_forest_set_split.argtypes = [P, i32]
         L.orc_insert.restype = i64
         L.orc_insert.argtypes = [P, P, i64]
         L.orc_erase.restype = i64
@@ -95,14 +97,20 @@ class OracleForest:
     """Serial BDL-tree: Insert_L / Erase_L / kNN_L of the paper, on the CPU."""
 
     def __init__(self, dim, leaf_size=16, buffer_size=1024, bloom_bits_per_key=16,
-                 hash_seed=0x5EED):
+                 hash_seed=0x5EED, split="object"):
+        """split: "object" (median of the points, the default) or "spatial"
+        (midpoint of their extent), the two rules of Sec. V-C."""
         self.dim = dim
         self.leaf_size = leaf_size
         self.buffer_size = buffer_size
+        self.split = split
         self._h = lib().orc_forest_new(dim, leaf_size, buffer_size,
                                        bloom_bits_per_key, hash_seed)
         if not self._h:
             raise ValueError("invalid oracle forest parameters")
+        if split not in ("object", "spatial"):
+            raise ValueError("split must be 'object' or 'spatial'")
+        lib().orc_forest_set_split(self._h, 1 if split == "spatial" else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)

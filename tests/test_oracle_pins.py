@@ -272,3 +272,66 @@ def test_below_half_is_strict():
     # the X-1 survivors went to the buffer; one more point makes tree 0
     f.insert(inputs.uniform_points(1, 2, seed=10))
     assert f.tree_mask() == 1 and len(f.buffer_ids()) == 0
+
+
+# --- the spatial-median rule (Sec. V-C) ------------------------------------
+
+def test_spatial_worked_example():
+    from tests.treecheck import check_tree_spatial
+    rows = read_golden("spatial_fig1.txt")
+    pts = np.array([[int(r[1]), int(r[2])] for r in rows if r[0] == "point"], np.int32)
+    (_, dim0, split, left, right), = [r for r in rows if r[0] == "root"]
+    f = OracleForest(2, leaf_size=1, buffer_size=2, split="spatial")
+    f.insert(pts)
+    t = f.tree(0)
+    assert t["h"] == 1
+    assert int(t["key"][0]) >> 31 == int(split) and int(dim0) == 0 % 2
+    off = t["leaf_off"]
+    assert list(t["ids"][off[0]:off[1]]) == [int(left)]
+    assert list(t["ids"][off[1]:off[2]]) == [int(right)]
+    check_tree_spatial(t, pts, 2)
+
+
+@pytest.mark.parametrize("gen", ["uniform", "clusters", "duplicates", "line"])
+def test_spatial_tree_shape(gen):
+    from tests.treecheck import check_tree_spatial
+    dim = 3
+    if gen == "uniform":
+        pts = inputs.uniform_points(9000, dim, seed=1)
+    elif gen == "clusters":
+        pts = inputs.gaussian_clusters(9000, dim, seed=2, n_clusters=5)
+    elif gen == "duplicates":
+        pts = inputs.duplicate_heavy_points(9000, dim, seed=3, distinct=4)
+    else:                      # all points on one axis: every other level splits nothing
+        pts = np.zeros((9000, dim), np.int32)
+        pts[:, 0] = np.random.default_rng(4).integers(0, 1 << 20, 9000)
+    f = OracleForest(dim, leaf_size=8, buffer_size=1024, split="spatial")
+    f.insert(pts)
+    for lvl in f.tree_levels():
+        check_tree_spatial(f.tree(lvl), pts, dim)
+    ids = inputs.sample_ids(np.arange(len(pts)), 4000, seed=5)
+    f.erase(ids)
+    for lvl in f.tree_levels():
+        check_tree_spatial(f.tree(lvl), pts, dim)
+
+
+@pytest.mark.parametrize("dim,k", [(2, 5), (3, 10), (5, 1)])
+def test_spatial_knn_matches_bruteforce(dim, k):
+    live = inputs.LiveSet(dim)
+    f = OracleForest(dim, leaf_size=8, buffer_size=256, split="spatial")
+    g = OracleForest(dim, leaf_size=8, buffer_size=256)
+    rng = np.random.default_rng(dim)
+    for step in range(4):
+        p = inputs.gaussian_clusters(3000, dim, seed=10 + step, n_clusters=6)
+        live.insert(p)
+        f.insert(p)
+        g.insert(p)
+        e = inputs.sample_ids(live.live_ids(), 1200, seed=20 + step)
+        assert f.erase(e) == live.erase(e) == g.erase(e)
+        q = np.concatenate([rng.integers(0, 1 << 20, (150, dim), dtype=np.int32), p[:50]])
+        lp, lid = live.live_points()
+        bi, bd = bruteforce_knn(lp, lid, q, k)
+        fi, fd = f.knn(q, k)
+        gi, gd = g.knn(q, k)
+        assert np.array_equal(fi, bi) and np.array_equal(fd, bd)
+        assert np.array_equal(gi, fi) and np.array_equal(gd, fd)

@@ -89,3 +89,52 @@ def assert_same_tree(a, b, what=""):
                           np.asarray(b["leaf_off"]).astype(np.int64)), what + " leaf ranges"
     for i, (x, y) in enumerate(zip(leaf_sets(a), leaf_sets(b))):
         assert np.array_equal(x, y), "%s leaf %d ids" % (what, i)
+
+
+def check_tree_spatial(t, coords_by_id, dim):
+    """The spatial-median rule (Sec. V-C): every internal node of depth t splits
+    its points in dimension t mod d at v = floor((min + max) / 2) of their
+    coordinates (v = 0 for an empty node), key (v << 31) | (2^31 - 1), points
+    with coordinate <= v on the left; leaves hold any number of points; boxes
+    and live counts are those of the points below (an empty box is
+    [INT32_MAX, INT32_MIN])."""
+    h = t["h"]
+    nn = t["nnodes"]
+    assert nn == (2 << h) - 1
+    child = np.asarray(t["child"]).reshape(nn, 2)
+    leaf_off = np.asarray(t["leaf_off"], dtype=np.int64)
+    ids = np.asarray(t["ids"])
+    real_ids = np.where(ids < 0, ids & 0x7FFFFFFF, ids) if ids.dtype == np.int32 else ids
+    dead = np.asarray(t["dead"], dtype=bool)
+    assert leaf_off[0] == 0 and leaf_off[-1] == len(ids)
+    assert np.all(np.diff(leaf_off) >= 0)
+    box = np.asarray(t["box"]).reshape(nn, 2 * dim)
+    live = np.asarray(t["node_live"])
+    key = np.asarray(t["key"])
+    seen = np.zeros(nn, dtype=bool)
+    imax, imin = np.iinfo(np.int32).max, np.iinfo(np.int32).min
+    stack = [(0, 0, 0, 1 << h)]
+    while stack:
+        v, dep, a, nlf = stack.pop()
+        assert 0 <= v < nn and not seen[v], "vEB slots must be a permutation"
+        seen[v] = True
+        lo, hi = leaf_off[a], leaf_off[a + nlf]
+        pts = coords_by_id[real_ids[lo:hi]]
+        if hi > lo:
+            assert np.array_equal(box[v, :dim], pts.min(axis=0)), "box lo"
+            assert np.array_equal(box[v, dim:], pts.max(axis=0)), "box hi"
+        else:
+            assert np.all(box[v, :dim] == imax) and np.all(box[v, dim:] == imin), "empty box"
+        assert live[v] == int((~dead[lo:hi]).sum()), "live count"
+        if dep == h:
+            assert child[v, 0] == -1 - a, "leaf index"
+            continue
+        c = dep % dim
+        sv = (int(pts[:, c].min()) + int(pts[:, c].max())) // 2 if hi > lo else 0
+        assert key[v] == (sv << 31) | 0x7FFFFFFF, "spatial split key"
+        mid = leaf_off[a + nlf // 2]
+        assert np.all(coords_by_id[real_ids[lo:mid], c] <= sv), "left of the split"
+        assert np.all(coords_by_id[real_ids[mid:hi], c] > sv), "right of the split"
+        stack.append((int(child[v, 0]), dep + 1, a, nlf // 2))
+        stack.append((int(child[v, 1]), dep + 1, a + nlf // 2, nlf // 2))
+    assert seen.all()
