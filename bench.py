@@ -56,11 +56,12 @@ def parse():
     ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--k", type=int, default=None, help="default 10 (forest10m), 8 (forests)")
     ap.add_argument("--dim", type=int, default=3)
-    ap.add_argument("--leaf", type=int, default=16)
+    ap.add_argument("--leaf", default="auto",
+                    help="leaf size, or 'auto': autotuned in {8, 16, 32} on this workload before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="forest10m", choices=["forest10m", "forests", "serve"])
-    ap.add_argument("--rate", type=float, default=1000.0, help="serve: requests per second")
+    ap.add_argument("--rate", type=float, default=600.0, help="serve: requests per second")
     ap.add_argument("--n-final", type=int, default=50_000_000, help="serve: stop at this many points")
     ap.add_argument("--forests", type=int, default=512)
     a = ap.parse_args()
@@ -201,6 +202,18 @@ def run_ours(a, rank, world, dist):
     def H2D(x):
         return torch.from_numpy(x).to(dev)
 
+    autotune = None
+    if a.leaf == "auto":
+        from paper_2112_06188_gb300.autotune import tune_leaf_size
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:3]]
+            best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream)
+        del tsteps
+        a.leaf = best
+        autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
+                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
+    a.leaf = int(a.leaf)
     with torch.cuda.stream(stream):
         f = Forest(a.dim, leaf_size=a.leaf, buffer_size=1024, stream=stream, device=dev)
         f.insert(H2D(W.initial))
@@ -298,7 +311,7 @@ def run_ours(a, rank, world, dist):
     res = {
         "ms": ms, "launches": launches, "prof": prof, "clocks": clk, "wall": wall,
         "knn_stats": (nodes, points, nq), "e2e_ms": statistics.median(e2e_ms) if e2e_ms else None,
-        "h2d": h2d, "d2h": d2h, "ops_per_step": ops_per_step,
+        "h2d": h2d, "d2h": d2h, "ops_per_step": ops_per_step, "autotune": autotune,
     }
     return res
 
@@ -567,24 +580,37 @@ def serve_once(a, reqs, initial, serial, paced, dev):
     f = Forest(5, leaf_size=16, buffer_size=1024, hbm_budget_bytes=SERVE_HBM_BUDGET, device=dev)
     f.insert(torch.from_numpy(initial).to(dev))
     torch.cuda.synchronize(dev)
+    # outputs allocated (pinned) up front, so that submitting costs nothing
+    outs = []
+    for _, kind, payload, k in reqs:
+        if kind == "insert":
+            outs.append(torch.empty(payload.shape[0], dtype=torch.int32).pin_memory())
+        elif kind == "knn":
+            outs.append((torch.empty((payload.shape[0], k), dtype=torch.int32).pin_memory(),
+                         torch.empty((payload.shape[0], k), dtype=torch.int64).pin_memory()))
+        else:
+            outs.append(None)
     srv = Server(f, serial=serial, staging_budget_bytes=SERVE_STAGING, max_inflight=256)
     tickets = [None] * len(reqs)
     lateness = []
+    start = [0.0]
 
     def submitter():
-        t0 = time.perf_counter()
+        # request i arrives at start + t_i on the server's clock; latency is
+        # counted from that arrival, so a late submit cannot hide queueing
+        t0 = start[0] = srv.now_ms()
         for i, (t, kind, payload, k) in enumerate(reqs):
             if paced:
-                dt = t - (time.perf_counter() - t0)
+                dt = t * 1e3 - (srv.now_ms() - t0)
                 if dt > 0:
-                    time.sleep(dt)
-                lateness.append(time.perf_counter() - t0 - t)
+                    time.sleep(dt * 1e-3)
+                lateness.append(srv.now_ms() - t0 - t * 1e3)
             if kind == "insert":
-                tickets[i] = srv.insert(payload)
+                tickets[i] = srv.insert(payload, out=outs[i])
             elif kind == "erase":
                 tickets[i] = srv.erase(payload)
             else:
-                tickets[i] = srv.knn(payload, k)
+                tickets[i] = srv.knn(payload, k, out=outs[i])
 
     t0 = time.perf_counter()
     th = threading.Thread(target=submitter)
@@ -592,6 +618,8 @@ def serve_once(a, reqs, initial, serial, paced, dev):
     th.join()
     res = [srv.wait(t) for t in tickets]
     makespan = time.perf_counter() - t0
+    for (t, _, _, _), r in zip(reqs, res):
+        r["t_arrival_ms"] = start[0] + (t * 1e3 if paced else 0.0)
     groups = srv.groups()
     srv.close()
     live = f.size()
@@ -602,7 +630,7 @@ def serve_once(a, reqs, initial, serial, paced, dev):
 def latency_summary(reqs, res):
     out = {}
     for kind in ("insert", "erase", "knn"):
-        lat = [r["t_done_ms"] - r["t_submit_ms"] for (_, kd, _, _), r in zip(reqs, res) if kd == kind]
+        lat = [r["t_done_ms"] - r["t_arrival_ms"] for (_, kd, _, _), r in zip(reqs, res) if kd == kind]
         if lat:
             out[kind] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
                          "p99_ms": round(float(np.percentile(lat, 99)), 3), "count": len(lat)}
@@ -669,7 +697,8 @@ def run_serve(a):
                     "offered_span_s": round(reqs[-1][0], 4), "served_span_s": round(span, 4),
                     "served_span_one_at_a_time_s": round(span_s, 4),
                     "device_groups": groups, "device_groups_one_at_a_time": groups_s,
-                    "submit_lateness_p99_ms": round(float(np.percentile(late, 99)) * 1e3, 3) if late else None},
+                    "latency_from": "arrival time (Poisson schedule on the server's clock)",
+                    "submit_lateness_p99_ms": round(float(np.percentile(late, 99)), 3) if late else None},
         "identical_results": bool(identical), "all_ok": bool(ok),
         "gpu_launches": launches,
         "clocks": clk,
@@ -764,7 +793,7 @@ def oracle_sample(a, nsteps, seed=2):
     from oracle.oracle import OracleForest
     n0, b, m = a.n0 // 10, a.batch // 10, a.queries // 10
     W = StepInputs(n0, b, m, a.dim, nsteps, seed=seed)
-    o = OracleForest(a.dim, leaf_size=a.leaf, buffer_size=1024)
+    o = OracleForest(a.dim, leaf_size=16 if a.leaf == "auto" else int(a.leaf), buffer_size=1024)
     o.insert(W.initial)
     times = []
     for ins, era, q in W.steps:
@@ -878,6 +907,8 @@ def main():
         "roofline": roofline(a, res, peaks),
         "clocks": res["clocks"],
     }
+    if res["autotune"]:
+        out["config"]["leaf_autotune"] = res["autotune"]
     if res["e2e_ms"]:
         out["e2e"] = {"value": round(ops / (res["e2e_ms"] * 1e-3), 1), "unit": "ops/s",
                       "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"],

@@ -231,6 +231,10 @@ int bdl_server_wait(bdl_server *s, uint64_t ticket, bdl_result *out_host);
 /* Wait until every submitted request has completed. */
 int bdl_server_drain(bdl_server *s);
 
+/* The server's clock: ms since it was created (the clock of bdl_result's
+ * timestamps). */
+double bdl_server_now_ms(const bdl_server *s);
+
 /* Device groups run so far. */
 int bdl_server_stats(const bdl_server *s, int64_t *out_groups_host);
 

@@ -1,0 +1,77 @@
+"""Leaf-size autotuner.
+
+The leaf size L (points per leaf, Sec. V-D) trades tree height -- node
+visits per query and levels per build -- against points scanned per leaf.
+The k-NN answers do not depend on it (they are the exact k nearest by
+(squared distance, id)), only the speed does, so L can be chosen per
+workload by measurement: for every candidate, build a forest on the
+workload's own initial points and time a few steps of it (one insert batch,
+one erase batch, one k-NN batch) with CUDA events; the fastest mean step
+wins.  Every step runs in the CUDA library; this module only times calls.
+"""
+import numpy as np
+import torch
+
+from . import inputs
+from .forest import Forest
+
+CANDIDATES = (8, 16, 32)
+
+
+def time_steps(dim, leaf, initial, steps, k, device=None, stream=None):
+    """Mean milliseconds of one (insert, erase, k-NN) step over `steps`, on a
+    forest of `initial` (device tensor) with leaf size `leaf`; the first step
+    is a warm-up and is not counted."""
+    stream = stream or torch.cuda.current_stream(device)
+    f = Forest(dim, leaf_size=leaf, stream=stream, device=device)
+    try:
+        f.insert(initial)
+        times = []
+        for i, (ins, era, q) in enumerate(steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.insert(ins)
+            f.erase(era)
+            f.knn(q, k)
+            b.record(stream)
+            b.synchronize()
+            if i:
+                times.append(a.elapsed_time(b))
+        return float(np.mean(times))
+    finally:
+        f.close()
+
+
+def tune_leaf_size(dim, initial, steps, k, candidates=CANDIDATES, device=None, stream=None):
+    """The fastest leaf size among `candidates` for this workload, and the
+    measured mean step time (ms) of each.  `initial` is a device tensor of
+    points; `steps` a list of at least two (insert points, erase ids, queries)
+    device-tensor triples."""
+    if len(steps) < 2:
+        raise ValueError("need a warm-up step and at least one timed step")
+    ms = {L: time_steps(dim, L, initial, steps, k, device, stream) for L in candidates}
+    best = min(ms, key=ms.get)
+    return best, ms
+
+
+def synthetic_steps(dim, n0, batch, queries, nsteps, seed, device=None):
+    """A uniform forest of n0 points and `nsteps` steps of the shape the
+    autotuner times (insert `batch`, erase `batch` live ids, `queries`
+    live-set queries), all on the device."""
+    dev = device or torch.device("cuda")
+    pts = inputs.uniform_points(n0, dim, seed)
+    live = inputs.LiveSet(dim)
+    live.insert(pts)
+    rng = np.random.default_rng(seed + 1)
+    steps = []
+    for _ in range(nsteps):
+        ins = rng.integers(0, inputs.GRID, size=(batch, dim), dtype=np.int32)
+        live.insert(ins)
+        era = rng.choice(live.live_ids(), size=min(batch, int(live.alive.sum())), replace=False)
+        live.erase(era)
+        lid = live.live_ids()
+        q = live.coords[lid[rng.integers(0, len(lid), size=queries)]]
+        T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        steps.append((T(ins), T(era.astype(np.int32)), T(q)))
+    return torch.from_numpy(pts).to(dev), steps

@@ -20,7 +20,7 @@ SYMBOLS = [
     "bdl_profile", "bdl_profile_read", "bdl_kernel_count", "bdl_kernel_name", "bdl_knn_noalloc",
     "bdl_insert_batch", "bdl_erase_batch", "bdl_knn_batch",
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
-    "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy",
+    "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -102,6 +102,7 @@ def load(path=None):
         "bdl_server_drain": (i32, [P]),
         "bdl_server_stats": (i32, [P, P]),
         "bdl_server_destroy": (i32, [P]),
+        "bdl_server_now_ms": (ctypes.c_double, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -227,6 +228,10 @@ def bdl_server_stats(s):
     g = ctypes.c_int64(0)
     st = load().bdl_server_stats(s, _ref(g))
     return st, g.value
+
+
+def bdl_server_now_ms(s):
+    return float(load().bdl_server_now_ms(s))
 
 
 def bdl_server_destroy(s):

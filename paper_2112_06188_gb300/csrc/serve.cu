@@ -185,10 +185,16 @@ int run_insert(bdl_server *S, Group *g) {
   int64_t n = 0;
   for (Req *q : g->reqs) n += q->r.n;
   const int32_t *pts = (const int32_t *)g->reqs[0]->d_in;
+  bool one_by_one = false;
   if (g->reqs.size() > 1 && n > 0) {       // concatenate the inputs
     g->merged_bytes = (size_t)n * f->dim * 4;
-    int st = cuda_check(cudaMallocFromPoolAsync(&g->merged, g->merged_bytes, S->pool, S->s_exec), "staging");
-    if (st) return st;
+    if (cudaMallocFromPoolAsync(&g->merged, g->merged_bytes, S->pool, S->s_exec) != cudaSuccess) {
+      cudaGetLastError();
+      g->merged = nullptr;
+      one_by_one = true;                   // no room to merge: same results, one call each
+    }
+  }
+  if (g->merged) {
     size_t off = 0;
     for (Req *q : g->reqs) {
       if (q->in_bytes)
@@ -198,7 +204,7 @@ int run_insert(bdl_server *S, Group *g) {
     pts = (const int32_t *)g->merged;
   }
   const int64_t first_id = f->next_id;
-  int st = bdl_insert(f, pts, n, nullptr, S->s_exec);
+  int st = one_by_one ? BDL_EINVAL : bdl_insert(f, pts, n, nullptr, S->s_exec);
   if (st == BDL_EINVAL && g->reqs.size() > 1) {
     // one of them is bad: run them one by one so each gets its own status
     for (Req *q : g->reqs) {
@@ -444,6 +450,8 @@ int bdl_server_drain(bdl_server *S) {
   S->cv_wait.wait(lk, [&] { return S->submitted.empty() && S->inflight == 0; });
   return BDL_OK;
 }
+
+double bdl_server_now_ms(const bdl_server *S) { return S ? ms_since(S) : 0.0; }
 
 int bdl_server_stats(const bdl_server *S, int64_t *out_groups) {
   if (!S) return set_error(BDL_EINVAL, "server is NULL");

@@ -48,19 +48,24 @@ class Server:
         self._keep[t] = (kind, data, out_ids, out_d2)
         return t
 
-    def insert(self, points):
+    def insert(self, points, out=None):
+        """Queue Insert_L of `points`; `out` (pinned int32 [n]) receives the ids."""
         p = _pinned(points, torch.int32).reshape(-1, self.forest.dim)
-        ids = torch.empty(p.shape[0], dtype=torch.int32).pin_memory()
+        ids = out if out is not None else torch.empty(p.shape[0], dtype=torch.int32).pin_memory()
         return self._submit(capi.BDL_REQ_INSERT, p, out_ids=ids, n=p.shape[0])
 
     def erase(self, ids):
         i = _pinned(ids, torch.int32).reshape(-1)
         return self._submit(capi.BDL_REQ_ERASE, i, n=i.shape[0])
 
-    def knn(self, queries, k):
+    def knn(self, queries, k, out=None):
+        """Queue kNN_L; `out` = (pinned int32 [m, k], pinned int64 [m, k]) receives the rows."""
         q = _pinned(queries, torch.int32).reshape(-1, self.forest.dim)
-        oi = torch.empty((q.shape[0], k), dtype=torch.int32).pin_memory()
-        od = torch.empty((q.shape[0], k), dtype=torch.int64).pin_memory()
+        if out is None:
+            oi = torch.empty((q.shape[0], k), dtype=torch.int32).pin_memory()
+            od = torch.empty((q.shape[0], k), dtype=torch.int64).pin_memory()
+        else:
+            oi, od = out
         return self._submit(capi.BDL_REQ_KNN, q, k=k, out_ids=oi, out_d2=od, n=q.shape[0])
 
     def wait(self, ticket):
@@ -79,6 +84,10 @@ class Server:
 
     def drain(self):
         capi.check(capi.bdl_server_drain(self._h), "bdl_server_drain")
+
+    def now_ms(self):
+        """The server's clock (ms since creation), the clock of the results' timestamps."""
+        return capi.bdl_server_now_ms(self._h)
 
     def groups(self):
         st, g = capi.bdl_server_stats(self._h)
