@@ -28,6 +28,14 @@ from 1M to 50M points under a Poisson stream of insert (1k-1M points), erase
 4:1:5 mix, served by the library's continuous-batching server under a fixed
 device-memory budget, and again by its one-request-at-a-time mode; p50/p99
 latency per request type and sustained updates/s and queries/s are reported.
+
+--workload sweep runs the paper's sweeps (Sec. VI) on two 10M-point sets, a 2-D
+Gaussian-cluster mixture (standing in for the 2-D VisualVar set) and 7-D
+uniform points: insert throughput against the batch size when the whole set is
+inserted batch by batch into an empty forest, erase throughput against the
+batch size when the whole set is erased batch by batch, and k-NN throughput
+(every point queried: the k-NN graph) against k = 2..11 after the set was
+inserted in 5% batches.
 """
 import argparse
 import json
@@ -60,7 +68,9 @@ def parse():
                     help="leaf size, or 'auto': autotuned in {8, 16, 32} on this workload before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="forest10m", choices=["forest10m", "forests", "serve"])
+    ap.add_argument("--workload", default="forest10m", choices=["forest10m", "forests", "serve", "sweep"])
+    ap.add_argument("--split", default="object", choices=["object", "spatial"],
+                    help="splitting rule of the trees (Sec. V-C)")
     ap.add_argument("--rate", type=float, default=600.0, help="serve: requests per second")
     ap.add_argument("--n-final", type=int, default=50_000_000, help="serve: stop at this many points")
     ap.add_argument("--forests", type=int, default=512)
@@ -74,7 +84,7 @@ def workload_config(a, n_gpus):
     return {"workload": "3-D uniform int32 forest of %d points; per step insert %d, erase %d "
                         "live ids, k=%d NN for %d live-set queries" % (a.n0, a.batch, a.batch, a.k, a.queries),
             "dim": a.dim, "n0": a.n0, "insert_batch": a.batch, "erase_batch": a.batch,
-            "queries": a.queries, "k": a.k, "leaf_size": a.leaf, "buffer_size": 1024,
+            "queries": a.queries, "k": a.k, "leaf_size": a.leaf, "buffer_size": 1024, "split": a.split,
             "l2": "flushed between steps (256 MB write), inputs resident in HBM",
             "parallelism": "one independent forest per GPU" if n_gpus > 1 else "single GPU"}
 
@@ -208,14 +218,15 @@ def run_ours(a, rank, world, dist):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:3]]
-            best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream)
+            best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream,
+                                              split=a.split)
         del tsteps
         a.leaf = best
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
                     "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
     a.leaf = int(a.leaf)
     with torch.cuda.stream(stream):
-        f = Forest(a.dim, leaf_size=a.leaf, buffer_size=1024, stream=stream, device=dev)
+        f = Forest(a.dim, leaf_size=a.leaf, buffer_size=1024, stream=stream, device=dev, split=a.split)
         f.insert(H2D(W.initial))
         dev_steps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps]
         out_ids = torch.empty((a.queries, a.k), dtype=torch.int32, device=dev)
@@ -733,6 +744,81 @@ def serve_cpu_sample(a, n_req=40):
                       "one host core" % n_req}
 
 
+# ---------------------------------------------------------------------------
+# sweeps: batch size (inserts, erases) and k
+# ---------------------------------------------------------------------------
+
+SWEEP_BATCHES = (10_000, 100_000, 1_000_000, 2_000_000, 3_000_000, 4_000_000, 5_000_000)
+SWEEP_KS = tuple(range(2, 12))
+
+
+def run_sweep(a):
+    import torch
+    from paper_2112_06188_gb300 import capi, inputs
+    from paper_2112_06188_gb300.forest import Forest
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    capi.load()
+    stream = torch.cuda.Stream(dev)
+    n = 10_000_000
+    sets = {"2-D clusters": (2, inputs.gaussian_clusters(n, 2, seed=21)),
+            "7-D uniform": (7, inputs.uniform_points(n, 7, seed=22))}
+
+    def timed(fn):
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        a_.record(stream)
+        fn()
+        b_.record(stream)
+        b_.synchronize()
+        return a_.elapsed_time(b_)
+
+    out = {"insert_updates_per_s": {}, "erase_updates_per_s": {}, "knn_queries_per_s": {}}
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for name, (dim, pts) in sets.items():
+        P = torch.from_numpy(pts).to(dev)
+        ins, era, kq = {}, {}, {}
+        for b in SWEEP_BATCHES:
+            with torch.cuda.stream(stream):
+                f = Forest(dim, stream=stream, device=dev, split=a.split)
+                ms = timed(lambda: [f.insert(P[i:i + b]) for i in range(0, n, b)])
+                ins[b] = round(n / (ms * 1e-3), 1)
+                ids = torch.from_numpy(np.random.default_rng(b).permutation(n).astype(np.int32)).to(dev)
+                ms = timed(lambda: [f.erase(ids[i:i + b]) for i in range(0, n, b)])
+                era[b] = round(n / (ms * 1e-3), 1)
+                assert f.size() == 0
+                f.close()
+        with torch.cuda.stream(stream):
+            f = Forest(dim, stream=stream, device=dev, split=a.split)
+            step = n // 20
+            for i in range(0, n, step):
+                f.insert(P[i:i + step])
+            oi = torch.empty((n, max(SWEEP_KS)), dtype=torch.int32, device=dev)
+            od = torch.empty((n, max(SWEEP_KS)), dtype=torch.int64, device=dev)
+            f.knn(P[:100_000], 2)          # warm-up (buffer tree)
+            for k in SWEEP_KS:
+                ok, dk = oi[:, :k].contiguous(), od[:, :k].contiguous()
+                ms = timed(lambda: f.knn(P, k, out=(ok, dk)))
+                kq[k] = round(n / (ms * 1e-3), 1)
+            f.close()
+        out["insert_updates_per_s"][name] = ins
+        out["erase_updates_per_s"][name] = era
+        out["knn_queries_per_s"][name] = kq
+        del P
+    clk = clocks.stop()
+    best = max(v for d in out["knn_queries_per_s"].values() for v in d.values())
+    return {"metric": METRIC, "value": best, "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "sweeps on 10M points (2-D clusters, 7-D uniform): insert and erase "
+                                   "throughput vs batch size, k-NN graph throughput vs k after 5% insert "
+                                   "batches", "split": a.split, "leaf_size": 16, "buffer_size": 1024,
+                       "batches": list(SWEEP_BATCHES), "ks": list(SWEEP_KS)},
+            "sweep": out, "clocks": clk}
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when the summary is missing or the kernel source changed since the capture."""
@@ -793,7 +879,7 @@ def oracle_sample(a, nsteps, seed=2):
     from oracle.oracle import OracleForest
     n0, b, m = a.n0 // 10, a.batch // 10, a.queries // 10
     W = StepInputs(n0, b, m, a.dim, nsteps, seed=seed)
-    o = OracleForest(a.dim, leaf_size=16 if a.leaf == "auto" else int(a.leaf), buffer_size=1024)
+    o = OracleForest(a.dim, leaf_size=16 if a.leaf == "auto" else int(a.leaf), buffer_size=1024, split=a.split)
     o.insert(W.initial)
     times = []
     for ins, era, q in W.steps:
@@ -866,6 +952,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
+    if a.workload == "sweep":
+        if rank == 0:
+            print(json.dumps(run_sweep(a)), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     if a.workload == "serve":
         if rank == 0:
             print(json.dumps(run_serve(a)), flush=True)

@@ -59,7 +59,14 @@ typedef struct {
     int32_t bloom_hashes;       /* bits set per key; must be 8 (split-block filter) */
     uint64_t hash_seed;         /* bloom hash seed; default 0x5EED */
     int64_t hbm_budget_bytes;   /* cap on the forest's device memory; 0 = none */
+    int32_t split_rule;         /* BDL_SPLIT_OBJECT (default): split at the median point
+                                   (Alg. 1); BDL_SPLIT_SPATIAL: split at the midpoint of the
+                                   points' extent, v = floor((min + max) / 2), coordinates <= v
+                                   to the left (Sec. V-C).  k-NN results are the same. */
+    int32_t reserved_;          /* 0 */
 } bdl_config;
+
+enum { BDL_SPLIT_OBJECT = 0, BDL_SPLIT_SPATIAL = 1 };
 
 /* Fill *cfg with the defaults above. */
 void bdl_default_config(bdl_config *cfg);

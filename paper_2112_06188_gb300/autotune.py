@@ -18,12 +18,12 @@ from .forest import Forest
 CANDIDATES = (8, 16, 32)
 
 
-def time_steps(dim, leaf, initial, steps, k, device=None, stream=None):
+def time_steps(dim, leaf, initial, steps, k, device=None, stream=None, split="object"):
     """Mean milliseconds of one (insert, erase, k-NN) step over `steps`, on a
     forest of `initial` (device tensor) with leaf size `leaf`; the first step
     is a warm-up and is not counted."""
     stream = stream or torch.cuda.current_stream(device)
-    f = Forest(dim, leaf_size=leaf, stream=stream, device=device)
+    f = Forest(dim, leaf_size=leaf, stream=stream, device=device, split=split)
     try:
         f.insert(initial)
         times = []
@@ -43,14 +43,14 @@ def time_steps(dim, leaf, initial, steps, k, device=None, stream=None):
         f.close()
 
 
-def tune_leaf_size(dim, initial, steps, k, candidates=CANDIDATES, device=None, stream=None):
+def tune_leaf_size(dim, initial, steps, k, candidates=CANDIDATES, device=None, stream=None, split="object"):
     """The fastest leaf size among `candidates` for this workload, and the
     measured mean step time (ms) of each.  `initial` is a device tensor of
     points; `steps` a list of at least two (insert points, erase ids, queries)
     device-tensor triples."""
     if len(steps) < 2:
         raise ValueError("need a warm-up step and at least one timed step")
-    ms = {L: time_steps(dim, L, initial, steps, k, device, stream) for L in candidates}
+    ms = {L: time_steps(dim, L, initial, steps, k, device, stream, split) for L in candidates}
     best = min(ms, key=ms.get)
     return best, ms
 

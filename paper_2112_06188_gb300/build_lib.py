@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libbdl_gb300.so")
-SOURCES = ["forest.cu", "build.cu", "erase.cu", "knn.cu", "serve.cu"]
+SOURCES = ["forest.cu", "build.cu", "erase.cu", "knn.cu", "serve.cu", "spatial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

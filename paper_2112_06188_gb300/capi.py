@@ -29,7 +29,11 @@ BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
 class BdlConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("buffer_size", ctypes.c_int32),
                 ("bloom_bits_per_key", ctypes.c_int32), ("bloom_hashes", ctypes.c_int32),
-                ("hash_seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_int64)]
+                ("hash_seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_int64),
+                ("split_rule", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+BDL_SPLIT_OBJECT, BDL_SPLIT_SPATIAL = 0, 1
 
 
 class BdlRequest(ctypes.Structure):

@@ -52,6 +52,11 @@ enum KernelId : int {
   kK_fill,
   kK_pack_lives,
   kK_put_blob,
+  kK_sp_gather,
+  kK_sp_minmax,
+  kK_sp_scatter,
+  kK_sp_split,
+  kK_sp_box,
   kKernelCount
 };
 extern const char *const kKernelNames[kKernelCount];
@@ -325,6 +330,13 @@ struct ClearedSrc {        // a cleared tree whose live points join a new tree
 // Gather the points of the new trees (of any number of forests with the same
 // dim) into staging and build all of them in shared launches.  Scratch is
 // charged to forest `af`.
+// The object-median (Alg. 1, build.cu) and spatial-median (Sec. V-C,
+// spatial.cu) builds; build_trees picks by af's splitting rule, and every
+// tree in one call must come from forests with that rule.
+int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
+                       const std::vector<ClearedSrc> &cl, cudaStream_t s);
+int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
+                        const std::vector<ClearedSrc> &cl, cudaStream_t s);
 int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
                 const std::vector<ClearedSrc> &cl, cudaStream_t s);
 void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s);

@@ -914,7 +914,13 @@ int smem_subtree_capacity(int dim) {
   return 2048;
 }
 
-int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
+int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt, const std::vector<ClearedSrc> &cl,
+                cudaStream_t s) {
+  if (af->cfg.split_rule == BDL_SPLIT_SPATIAL) return build_trees_spatial(af, dim, bt, cl, s);
+  return build_trees_object(af, dim, bt, cl, s);
+}
+
+int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
                 const std::vector<ClearedSrc> &cl, cudaStream_t s) {
   if (bt.empty()) return BDL_OK;
   const int ntree = (int)bt.size();

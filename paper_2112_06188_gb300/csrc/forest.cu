@@ -48,6 +48,11 @@ const char *const kKernelNames[kKernelCount] = {
     "k_fill",
     "k_pack_lives",
     "k_put_blob",
+    "k_sp_gather",
+    "k_sp_minmax",
+    "k_sp_scatter",
+    "k_sp_split",
+    "k_sp_box",
 };
 
 // ---- live per-kernel timing (CUDA events on the launching stream) ----
@@ -495,6 +500,10 @@ static void commit_insert(InsertPlan &ip, cudaStream_t s) {
   ip.newbuf = nullptr;
 }
 
+// Trees of forests in one class are built together: same dimension, same
+// splitting rule (Sec. V-C).
+static int build_class(const bdl_forest *f) { return 2 * f->dim + (f->cfg.split_rule == BDL_SPLIT_SPATIAL); }
+
 // Per-call device scratch for small tables, charged to one forest.
 struct Temp {
   bdl_forest *f;
@@ -517,20 +526,20 @@ static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTre
                             std::vector<ClearedSrc> &cl, std::vector<int> &bt_plan,
                             std::vector<FillSeg> extra_fills, Temp &tmp, cudaStream_t s) {
   int st = BDL_OK;
-  // one build per dimension present
-  std::vector<int> dims;
+  // one build per (dimension, splitting rule) present
+  std::vector<int> classes;
   for (auto &b : bt) {
-    int d = plans[bt_plan[&b - bt.data()]].f->dim;
-    if (std::find(dims.begin(), dims.end(), d) == dims.end()) dims.push_back(d);
+    int d = build_class(plans[bt_plan[&b - bt.data()]].f);
+    if (std::find(classes.begin(), classes.end(), d) == classes.end()) classes.push_back(d);
   }
-  for (int d : dims) {
+  for (int d : classes) {
     if (st) break;
     std::vector<BuildTree> g;
     std::vector<int> remap(bt.size(), -1);
     bdl_forest *charge = nullptr;
     for (size_t j = 0; j < bt.size(); ++j) {
       bdl_forest *f = plans[bt_plan[j]].f;
-      if (f->dim != d) continue;
+      if (build_class(f) != d) continue;
       if (!charge) charge = f;
       remap[j] = (int)g.size();
       g.push_back(bt[j]);
@@ -538,7 +547,7 @@ static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTre
     std::vector<ClearedSrc> gc;
     for (auto &c : cl)
       if (remap[c.dst] >= 0) gc.push_back(ClearedSrc{c.pts, c.size, remap[c.dst]});
-    st = build_trees(charge, d, g, gc, s);
+    st = build_trees(charge, charge->dim, g, gc, s);
   }
   std::vector<FillSeg> fills = std::move(extra_fills);
   for (auto &ip : plans)
@@ -582,15 +591,17 @@ static void refresh_btrees(bdl_forest *const *F, int nf, cudaStream_t s) {
     bt.push_back(b);
     owner.push_back(i);
   }
-  std::vector<int> dims;
-  for (size_t j = 0; j < bt.size(); ++j)
-    if (std::find(dims.begin(), dims.end(), F[owner[j]]->dim) == dims.end()) dims.push_back(F[owner[j]]->dim);
-  for (int d : dims) {
+  std::vector<int> classes;
+  for (size_t j = 0; j < bt.size(); ++j) {
+    const int c = build_class(F[owner[j]]);
+    if (std::find(classes.begin(), classes.end(), c) == classes.end()) classes.push_back(c);
+  }
+  for (int d : classes) {
     std::vector<BuildTree> g;
     std::vector<int> who;
     for (size_t j = 0; j < bt.size(); ++j)
-      if (F[owner[j]]->dim == d) { g.push_back(bt[j]); who.push_back(owner[j]); }
-    const bool ok = build_trees(F[who[0]], d, g, {}, s) == BDL_OK;
+      if (build_class(F[owner[j]]) == d) { g.push_back(bt[j]); who.push_back(owner[j]); }
+    const bool ok = build_trees(F[who[0]], F[who[0]]->dim, g, {}, s) == BDL_OK;
     for (size_t j = 0; j < g.size(); ++j) {
       if (ok) F[who[j]]->btree = g[j].tree;
       else free_tree(F[who[j]], g[j].tree, s);
@@ -1043,6 +1054,8 @@ static int check_config(const bdl_config &c) {
     return set_error(BDL_EINVAL, "bloom_bits_per_key must be in 1..64");
   if (c.bloom_hashes != 8) return set_error(BDL_EINVAL, "bloom_hashes must be 8");
   if (c.hbm_budget_bytes < 0) return set_error(BDL_EINVAL, "hbm_budget_bytes must be >= 0");
+  if (c.split_rule != BDL_SPLIT_OBJECT && c.split_rule != BDL_SPLIT_SPATIAL)
+    return set_error(BDL_EINVAL, "split_rule must be BDL_SPLIT_OBJECT or BDL_SPLIT_SPATIAL");
   return BDL_OK;
 }
 
@@ -1060,6 +1073,8 @@ void bdl_default_config(bdl_config *cfg) {
   cfg->bloom_hashes = 8;
   cfg->hash_seed = 0x5EED;
   cfg->hbm_budget_bytes = 0;
+  cfg->split_rule = BDL_SPLIT_OBJECT;
+  cfg->reserved_ = 0;
 }
 
 const char *bdl_status_string(int st) {

@@ -31,7 +31,9 @@ class Forest:
     """A batch-dynamic kd-tree forest resident on one GPU."""
 
     def __init__(self, dim, points=None, leaf_size=16, buffer_size=1024, bloom_bits_per_key=16,
-                 hash_seed=0x5EED, hbm_budget_bytes=0, device=None, stream=None):
+                 hash_seed=0x5EED, hbm_budget_bytes=0, device=None, stream=None, split="object"):
+        """split: "object" (median point, Alg. 1) or "spatial" (midpoint of the
+        extent, Sec. V-C); k-NN answers are the same either way."""
         capi.load()
         self.dim = dim
         self.device = torch.device(device or "cuda")
@@ -40,6 +42,10 @@ class Forest:
         cfg.leaf_size, cfg.buffer_size = leaf_size, buffer_size
         cfg.bloom_bits_per_key, cfg.hash_seed = bloom_bits_per_key, hash_seed
         cfg.hbm_budget_bytes = hbm_budget_bytes
+        if split not in ("object", "spatial"):
+            raise ValueError("split must be 'object' or 'spatial'")
+        cfg.split_rule = capi.BDL_SPLIT_SPATIAL if split == "spatial" else capi.BDL_SPLIT_OBJECT
+        self.split = split
         self.cfg = cfg
         with torch.cuda.device(self.device):
             st, h = capi.bdl_create(dim, cfg, None, 0, None, _stream_handle(stream))
