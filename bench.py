@@ -497,11 +497,50 @@ def run_forests(a, rank, world, dist):
         msA, msB = max_over_ranks(msA, dist, dev), max_over_ranks(msB, dist, dev)
     identical = all(torch.equal(flat[i].oi, outB[i][0]) and torch.equal(flat[i].od, outB[i][1])
                     for i in range(a.warmup, nsteps))
+    # read-only repeats of the last step's k-NN on the final forests: the
+    # batched call, a prepared plan (kernels only), and that plan replayed
+    # from a CUDA graph; all must give the same rows
+    x = flat[-1]
+    R = 20
+    ref_i, ref_d = x.oi.clone(), x.od.clone()
+
+    def rep_ms(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(R):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / R
+
+    eager_ms = rep_ms(lambda: capi.check(L.bdl_knn_batch(hA, nf, x.c_q, x.c_m, a.k, x.c_oi, x.c_od, sh),
+                                         "bdl_knn_batch"))
+    same_eager = torch.equal(x.oi, ref_i) and torch.equal(x.od, ref_d)
+    st, plan = capi.bdl_knn_plan_create(list(hA), x.p_q, x.m, a.k, x.p_oi, x.p_od, sh)
+    capi.check(st, "bdl_knn_plan_create")
+    plan_ms = rep_ms(lambda: capi.check(L.bdl_knn_plan_launch(plan, sh), "bdl_knn_plan_launch"))
+    same_plan = torch.equal(x.oi, ref_i) and torch.equal(x.od, ref_d)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        capi.check(L.bdl_knn_plan_launch(plan, ctypes.c_void_p(stream.cuda_stream)), "bdl_knn_plan_launch")
+    x.oi.fill_(-1)
+    def replay():
+        with torch.cuda.stream(stream):    # replays run on the current stream
+            g.replay()
+
+    graph_ms = rep_ms(replay)
+    same_graph = torch.equal(x.oi, ref_i) and torch.equal(x.od, ref_d)
+    del g
+    capi.bdl_knn_plan_destroy(plan)
+    knn_repeat = {"queries": sum(x.m), "batched_call_ms": round(eager_ms, 3), "prepared_plan_ms": round(plan_ms, 3),
+                  "cuda_graph_replay_ms": round(graph_ms, 3),
+                  "identical_results": bool(same_eager and same_plan and same_graph)}
     identical = identical and all(f.size() == g.size() and f.tree_mask() == g.tree_mask()
                                   for f, g in zip(A, B))
     x = flat[-1]
     res = {"msA": msA, "msB": msB, "launchesA": launchesA // a.steps, "launchesB": launchesB // a.steps,
-           "prof": prof, "clocks": clk, "identical": bool(identical),
+           "prof": prof, "clocks": clk, "identical": bool(identical), "knn_repeat": knn_repeat,
            "ops": sum(flat[i].ops for i in range(a.warmup, nsteps)) / a.steps,
            "inserted": sum(x.n_ins), "erased": sum(x.n_era), "queries": sum(x.m),
            "points": int(sum(f.size() for f in A))}
@@ -548,6 +587,7 @@ def report_forests(a, res, world):
                              "gpu_launches": res["launchesB"]},
         "speedup_vs_per_forest": round(msB["step"] / msA["step"], 2),
         "identical_results": res["identical"],
+        "knn_repeat_final_forests": res["knn_repeat"],
         "per_step": {"inserted": res["inserted"], "erased": res["erased"], "queries": res["queries"],
                      "live_points_after": res["points"]},
         "gpu_launches": res["launchesA"],

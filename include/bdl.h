@@ -166,6 +166,25 @@ int bdl_knn_batch(bdl_forest *const *forests, int nf, const int32_t *const *q_de
                   int k, int32_t *const *out_ids_dev, int64_t *const *out_d2_dev,
                   bdl_stream_t stream);
 
+/* A prepared kNN_L over forests[nf] (a forest may appear more than once):
+ * the job tables and the query-ordering scratch are made once, in device
+ * memory the plan owns (charged to forests[0]), so that
+ * bdl_knn_plan_launch issues kernels and memsets only -- on any stream,
+ * inside a CUDA graph capture too.  Every launch answers the queries that
+ * q_dev[i] holds when it runs (contents may change between launches, the
+ * pointers and sizes may not) against the forests as they were when the
+ * plan was made; a launch after an insert or erase on any of them returns
+ * BDL_EINVAL and launches nothing.  (A captured graph replays without that
+ * check: do not replay it after changing the forests.)  Results equal
+ * bdl_knn_batch's.  Destroy the plan before its forests. */
+typedef struct bdl_knn_plan bdl_knn_plan;
+int bdl_knn_plan_create(bdl_forest *const *forests, int nf, const int32_t *const *q_dev,
+                        const int64_t *m, int k, int32_t *const *out_ids_dev,
+                        int64_t *const *out_d2_dev, bdl_stream_t stream, bdl_knn_plan **out);
+int bdl_knn_plan_launch(bdl_knn_plan *plan, bdl_stream_t stream);
+/* Waits for the device, then frees the plan's memory.  NULL is a no-op. */
+int bdl_knn_plan_destroy(bdl_knn_plan *plan);
+
 /* ---------------------------------------------------------------------
  * Serving: a request server that keeps one forest resident and takes
  * insert / erase / k-NN requests from host memory as they arrive.

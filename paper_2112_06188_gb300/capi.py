@@ -21,6 +21,7 @@ SYMBOLS = [
     "bdl_insert_batch", "bdl_erase_batch", "bdl_knn_batch",
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
     "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
+    "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -107,6 +108,9 @@ def load(path=None):
         "bdl_server_stats": (i32, [P, P]),
         "bdl_server_destroy": (i32, [P]),
         "bdl_server_now_ms": (ctypes.c_double, [P]),
+        "bdl_knn_plan_create": (i32, [P, i32, P, P, i32, P, P, P, P]),
+        "bdl_knn_plan_launch": (i32, [P, P]),
+        "bdl_knn_plan_destroy": (i32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -195,6 +199,22 @@ def bdl_erase_batch(forests, ids_dev, n, stream):
 def bdl_knn_batch(forests, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
     return load().bdl_knn_batch(_ptr_array(forests), len(forests), _ptr_array(q_dev), _i64_array(m),
                                 k, _ptr_array(out_ids_dev), _ptr_array(out_d2_dev), stream)
+
+
+def bdl_knn_plan_create(forests, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
+    """Returns (status, plan handle)."""
+    h = ctypes.c_void_p()
+    st = load().bdl_knn_plan_create(_ptr_array(forests), len(forests), _ptr_array(q_dev), _i64_array(m), k,
+                                    _ptr_array(out_ids_dev), _ptr_array(out_d2_dev), stream, _ref(h))
+    return st, h.value
+
+
+def bdl_knn_plan_launch(plan, stream):
+    return load().bdl_knn_plan_launch(plan, stream)
+
+
+def bdl_knn_plan_destroy(plan):
+    return load().bdl_knn_plan_destroy(plan)
 
 
 def bdl_server_default_config():

@@ -298,6 +298,7 @@ struct bdl_forest {
   unsigned long long *err = nullptr;  // device error word (inside dev_small)
   bool debug_check = false;      // BDL_DEBUG_CHECK=1: sync and check err after each call
   unsigned long long *knn_stats = nullptr;  // [3] device counters, or nullptr
+  uint64_t version = 0;          // bumped by every change of the trees or the buffer
 };
 
 namespace bdl {
@@ -444,6 +445,13 @@ struct KnnJob {
 // Device bytes the job table of `calls` needs (0 for a single call, whose job
 // travels as kernel parameters; `table` may then be null).
 size_t knn_table_bytes(const std::vector<KnnCall> &calls);
+// The table path in two halves (prepared k-NN plans): upload the job table of
+// `calls` (knn_table_bytes_always bytes at `table`; *warps = warps to launch),
+// then launch it as often as wanted.
+size_t knn_table_bytes_always(const std::vector<KnnCall> &calls);
+int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, cudaStream_t s);
+int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, unsigned long long *stats,
+                     cudaStream_t s);
 // k-NN for every call (all of dimension `dim`) in one launch; the job table
 // is uploaded to `table` (knn_table_bytes of device memory) on stream s.
 int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,

@@ -496,6 +496,7 @@ static void commit_insert(InsertPlan &ip, cudaStream_t s) {
     f->F = ip.Fnew;
   }
   f->buf_dirty = true;
+  f->version++;
   ip.built.clear();
   ip.newbuf = nullptr;
 }
@@ -576,6 +577,7 @@ static void refresh_btrees(bdl_forest *const *F, int nf, cudaStream_t s) {
     free_tree(f, f->btree, s);
     f->btree = nullptr;
     f->buf_dirty = false;
+    f->version++;
     if (f->nbuf == 0) continue;
     Tree *t = nullptr;
     if (alloc_tree(f, kMaxLevel, f->nbuf, s, &t) != BDL_OK) continue;
@@ -777,6 +779,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   for (size_t j = 0; j < mk.size(); ++j) {
     if (out_n) out_n[mk_forest[j]] = ne[j];
     F[mk_forest[j]]->live -= ne[j];
+    if (ne[j] > 0) F[mk_forest[j]]->version++;
     if (ne[j] > 0) act.push_back((int)j);
   }
   if (act.empty()) return BDL_OK;
@@ -1026,6 +1029,114 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
   return BDL_OK;
 }
 
+}  // namespace bdl
+
+// A prepared kNN_L over many forests: job tables and sort scratch live in
+// device memory owned by the plan, so a launch is kernels only.
+struct bdl_knn_plan {
+  std::vector<bdl_forest *> F;
+  std::vector<uint64_t> version;   // of each forest when the plan was made
+  int device = 0, k = 0;
+  struct Part {
+    int dim, njobs;
+    int64_t warps;
+    void *table;
+    unsigned long long *stats;
+  };
+  struct Sort {
+    const int32_t *q;
+    int64_t m;
+    int dim;
+    int32_t *perm;
+    void *scratch;
+  };
+  std::vector<Part> parts;
+  std::vector<Sort> sorts;
+  bdl_forest *charge = nullptr;
+  void *block = nullptr;
+  size_t bytes = 0;
+};
+
+namespace bdl {
+
+static int knn_plan_make(bdl_forest *const *F, int nf, const int32_t *const *q, const int64_t *m, int k,
+                         int32_t *const *oi, int64_t *const *od, cudaStream_t s, bdl_knn_plan *P) {
+  if (k < 1 || k > kMaxK) return set_error(BDL_EINVAL, "k must be in 1..32");
+  if (nf < 1) return set_error(BDL_EINVAL, "a plan needs at least one forest");
+  for (int i = 0; i < nf; ++i) {
+    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
+    if (m[i] < 0) return set_error(BDL_EINVAL, "m < 0");
+    if (m[i] > 0 && (!q[i] || !oi[i] || !od[i])) return set_error(BDL_EINVAL, "NULL pointer");
+  }
+  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
+  refresh_btrees(F, nf, s);
+  std::vector<ForestView> views(nf);
+  std::vector<KnnCall> calls;
+  size_t sort_bytes = 0;
+  for (int i = 0; i < nf; ++i) {
+    if (m[i] == 0) continue;
+    views[i] = knn_view(F[i], false, s);
+    if (m[i] >= kSortMinQueries) sort_bytes += a256(query_sort_bytes(m[i], F[i]->dim));
+    calls.push_back(KnnCall{&views[i], q[i], nullptr, m[i], oi[i], od[i]});
+  }
+  std::vector<int> dims;
+  for (auto &c : calls)
+    if (std::find(dims.begin(), dims.end(), c.fv->dim) == dims.end()) dims.push_back(c.fv->dim);
+  std::vector<std::vector<KnnCall>> groups;
+  size_t table_bytes = 0;
+  for (int d : dims) {
+    std::vector<KnnCall> g;
+    for (auto &c : calls)
+      if (c.fv->dim == d) g.push_back(c);
+    table_bytes += a256(knn_table_bytes_always(g));
+    groups.push_back(std::move(g));
+  }
+  P->bytes = std::max<size_t>(table_bytes + sort_bytes, 256);
+  P->charge = F[0];
+  int st = dev_alloc(F[0], &P->block, P->bytes, s);
+  if (st) return st;
+  char *p = (char *)P->block;
+  // sort scratch first: its permutation is part of the jobs
+  for (auto &c : calls) {
+    if (c.m < kSortMinQueries) continue;
+    bdl_knn_plan::Sort so{c.q, c.m, c.fv->dim, (int32_t *)p, p + a256((size_t)c.m * 4)};
+    P->sorts.push_back(so);
+    p += a256(query_sort_bytes(c.m, c.fv->dim));
+  }
+  for (auto &g : groups)
+    for (auto &c : g)
+      for (auto &so : P->sorts)
+        if (so.q == c.q && so.m == c.m) c.perm = so.perm;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const int d = dims[gi];
+    unsigned long long *stats = nullptr;
+    for (int i = 0; i < nf; ++i)
+      if (F[i]->dim == d && F[i]->knn_stats) stats = F[i]->knn_stats;
+    bdl_knn_plan::Part part{d, (int)groups[gi].size(), 0, p, stats};
+    st = upload_knn_table(groups[gi], p, &part.warps, s);
+    if (st) return st;
+    p += a256(knn_table_bytes_always(groups[gi]));
+    P->parts.push_back(part);
+  }
+  P->F.assign(F, F + nf);
+  for (int i = 0; i < nf; ++i) P->version.push_back(F[i]->version);
+  P->device = F[0]->device;
+  P->k = k;
+  return cuda_check(cudaGetLastError(), "k-NN plan");
+}
+
+static int knn_plan_launch(bdl_knn_plan *P, cudaStream_t s) {
+  for (size_t i = 0; i < P->F.size(); ++i)
+    if (P->F[i]->version != P->version[i])
+      return set_error(BDL_EINVAL, "a forest changed since the k-NN plan was made");
+  for (auto &so : P->sorts) launch_query_sort(so.q, so.m, so.dim, so.scratch, so.perm, s);
+  for (auto &part : P->parts) {
+    const int st = launch_knn_table(part.table, part.njobs, part.warps, part.dim, P->k, part.stats, s);
+    if (st) return st;
+  }
+  return BDL_OK;
+}
+
 // With BDL_DEBUG_CHECK=1 every call waits for its kernels and fails with
 // BDL_EINTERNAL if one of them recorded an out-of-range index.
 static int finish(bdl_forest *f, cudaStream_t s, int st) {
@@ -1212,6 +1323,43 @@ int bdl_knn_batch(bdl_forest *const *forests, int nf, const int32_t *const *q, c
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(forests[0]->device);
   return finish_many(forests, nf, s, knn_many(forests, nf, q, m, k, out_ids, out_d2, s));
+}
+
+int bdl_knn_plan_create(bdl_forest *const *forests, int nf, const int32_t *const *q, const int64_t *m, int k,
+                        int32_t *const *out_ids, int64_t *const *out_d2, bdl_stream_t stream,
+                        bdl_knn_plan **out) {
+  if (!out) return set_error(BDL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nf < 1 || !forests || !q || !m || !out_ids || !out_d2) return set_error(BDL_EINVAL, "NULL array");
+  if (!forests[0]) return set_error(BDL_EINVAL, "forest is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(forests[0]->device);
+  bdl_knn_plan *P = new bdl_knn_plan();
+  int st = knn_plan_make(forests, nf, q, m, k, out_ids, out_d2, s, P);
+  if (!st) st = finish_many(forests, nf, s, st);
+  if (st) {
+    if (P->block) dev_free(P->charge, P->block, P->bytes, s);
+    delete P;
+    return st;
+  }
+  *out = P;
+  return BDL_OK;
+}
+
+int bdl_knn_plan_launch(bdl_knn_plan *plan, bdl_stream_t stream) {
+  if (!plan) return set_error(BDL_EINVAL, "plan is NULL");
+  DeviceGuard g(plan->device);
+  return knn_plan_launch(plan, (cudaStream_t)stream);
+}
+
+int bdl_knn_plan_destroy(bdl_knn_plan *plan) {
+  if (!plan) return BDL_OK;
+  DeviceGuard g(plan->device);
+  cudaDeviceSynchronize();   // no launch of the plan may still be running
+  if (plan->block) dev_free(plan->charge, plan->block, plan->bytes, 0);
+  const int st = cuda_check(cudaStreamSynchronize(0), "sync");
+  delete plan;
+  return st;
 }
 
 int bdl_size(const bdl_forest *f, int64_t *out) {

@@ -480,9 +480,61 @@ __global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m,
 
 size_t knn_table_bytes(const std::vector<KnnCall> &calls) {
   if (calls.size() == 1) return 0;   // one forest: no table (kernel parameters)
+  return knn_table_bytes_always(calls);
+}
+
+size_t knn_table_bytes_always(const std::vector<KnnCall> &calls) {
   size_t n = calls.size(), views = 0;
   for (const auto &c : calls) views += (size_t)c.fv->ntrees;
   return n * sizeof(KnnJob) + (n + 1) * 8 + views * sizeof(TreeView) + 64;
+}
+
+int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, cudaStream_t s) {
+  const size_t n = calls.size();
+  std::vector<unsigned char> img(knn_table_bytes_always(calls));
+  KnnJob *jobs = (KnnJob *)img.data();
+  int64_t *warp = (int64_t *)(img.data() + n * sizeof(KnnJob));
+  const size_t views_off = n * sizeof(KnnJob) + (n + 1) * 8;
+  TreeView *views = (TreeView *)(img.data() + views_off);
+  size_t v = 0;
+  warp[0] = 0;
+  for (size_t j = 0; j < n; ++j) {
+    const KnnCall &c = calls[j];
+    KnnJob &J = jobs[j];
+    memset(&J, 0, sizeof(J));
+    J.trees = (const TreeView *)((char *)table + views_off) + v;
+    J.ntrees = c.fv->ntrees;
+    J.dim = c.fv->dim;
+    J.idtab = c.fv->idtab;
+    J.buf = c.fv->buf;
+    J.nbuf = c.fv->nbuf;
+    J.err = c.fv->err;
+    J.q = c.q;
+    J.perm = c.perm;
+    J.m = c.m;
+    J.oi = c.oi;
+    J.od = c.od;
+    for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
+    warp[j + 1] = warp[j] + (c.m + 31) / 32;
+  }
+  *warps = warp[n];
+  if (warp[n] == 0) return BDL_OK;
+  return h2d(table, img.data(), img.size(), s);
+}
+
+int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, unsigned long long *stats,
+                     cudaStream_t s) {
+  if (warps == 0) return BDL_OK;
+  const KnnJob *dj = (const KnnJob *)table;
+  const int64_t *dw = (const int64_t *)((const char *)table + njobs * sizeof(KnnJob));
+  switch (dim) {
+    case 2: launch_d<2>(dj, dw, njobs, warps, k, stats, s); break;
+    case 3: launch_d<3>(dj, dw, njobs, warps, k, stats, s); break;
+    case 5: launch_d<5>(dj, dw, njobs, warps, k, stats, s); break;
+    case 7: launch_d<7>(dj, dw, njobs, warps, k, stats, s); break;
+    default: launch_d<0>(dj, dw, njobs, warps, k, stats, s); break;
+  }
+  return cuda_check(cudaGetLastError(), "knn kernel");
 }
 
 int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,
@@ -514,46 +566,10 @@ int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *tab
     }
     return cuda_check(cudaGetLastError(), "knn kernel");
   }
-  // host image: jobs, warp prefix, tree views; its pointers point into `table`
-  std::vector<unsigned char> img(knn_table_bytes(calls));
-  KnnJob *jobs = (KnnJob *)img.data();
-  int64_t *warp = (int64_t *)(img.data() + n * sizeof(KnnJob));
-  const size_t views_off = n * sizeof(KnnJob) + (n + 1) * 8;
-  TreeView *views = (TreeView *)(img.data() + views_off);
-  size_t v = 0;
-  warp[0] = 0;
-  for (size_t j = 0; j < n; ++j) {
-    const KnnCall &c = calls[j];
-    KnnJob &J = jobs[j];
-    memset(&J, 0, sizeof(J));
-    J.trees = (const TreeView *)((char *)table + views_off) + v;
-    J.ntrees = c.fv->ntrees;
-    J.dim = c.fv->dim;
-    J.idtab = c.fv->idtab;
-    J.buf = c.fv->buf;
-    J.nbuf = c.fv->nbuf;
-    J.err = c.fv->err;
-    J.q = c.q;
-    J.perm = c.perm;
-    J.m = c.m;
-    J.oi = c.oi;
-    J.od = c.od;
-    for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
-    warp[j + 1] = warp[j] + (c.m + 31) / 32;
-  }
-  if (warp[n] == 0) return BDL_OK;
-  int st = h2d(table, img.data(), img.size(), s);
+  int64_t warps = 0;
+  int st = upload_knn_table(calls, table, &warps, s);
   if (st) return st;
-  const KnnJob *dj = (const KnnJob *)table;
-  const int64_t *dw = (const int64_t *)((char *)table + n * sizeof(KnnJob));
-  switch (dim) {
-    case 2: launch_d<2>(dj, dw, (int)n, warp[n], k, stats, s); break;
-    case 3: launch_d<3>(dj, dw, (int)n, warp[n], k, stats, s); break;
-    case 5: launch_d<5>(dj, dw, (int)n, warp[n], k, stats, s); break;
-    case 7: launch_d<7>(dj, dw, (int)n, warp[n], k, stats, s); break;
-    default: launch_d<0>(dj, dw, (int)n, warp[n], k, stats, s); break;
-  }
-  return cuda_check(cudaGetLastError(), "knn kernel");
+  return launch_knn_table(table, (int)n, warps, dim, k, stats, s);
 }
 
 void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<TreeSeg> &segs,

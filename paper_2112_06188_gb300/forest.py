@@ -218,3 +218,41 @@ def knn_batch(forests, queries, k, out=None, stream=None):
                                   [_addr(o[1]) for o in out], _batch_stream(forests, stream)),
                "bdl_knn_batch")
     return out
+
+
+class KnnPlan:
+    """A prepared kNN_L over forests[i] with the device query tensors queries[i]:
+    launch() answers whatever the query tensors hold at that time (same
+    shapes), against the forests as they were when the plan was made.  A launch
+    issues kernels only, so it can be captured in a CUDA graph."""
+
+    def __init__(self, forests, queries, k, out=None, stream=None):
+        self.queries = [q.reshape(-1, f.dim) for f, q in zip(forests, queries)]
+        for q in self.queries:
+            if q.dtype != torch.int32 or not q.is_contiguous() or not q.is_cuda:
+                raise ValueError("plan queries must be contiguous int32 device tensors")
+        if out is None:
+            out = [(torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device),
+                    torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)) for q in self.queries]
+        self.out = out
+        self.forests = list(forests)
+        st, h = capi.bdl_knn_plan_create([f._h for f in forests], [_addr(q) for q in self.queries],
+                                         [q.shape[0] for q in self.queries], k, [_addr(o[0]) for o in out],
+                                         [_addr(o[1]) for o in out], _batch_stream(forests, stream))
+        capi.check(st, "bdl_knn_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        capi.check(capi.bdl_knn_plan_launch(self._h, _batch_stream(self.forests, stream)), "bdl_knn_plan_launch")
+        return self.out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.bdl_knn_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

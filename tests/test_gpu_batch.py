@@ -219,3 +219,50 @@ def test_batch_argument_rules():
     assert torch.equal(out[1][0], g.knn(q, 3)[0])
     f.close()
     g.close()
+
+
+def test_knn_plan_launch_and_graph():
+    """A prepared k-NN: equal to bdl_knn_batch, follows new query contents,
+    replays from a CUDA graph, refuses to run after an update."""
+    from paper_2112_06188_gb300 import capi
+    from paper_2112_06188_gb300.forest import Forest, KnnPlan, knn_batch
+    dims = [2, 3, 3, 5, 2]
+    F = [Forest(d) for d in dims]
+    for i, (f, d) in enumerate(zip(F, dims)):
+        f.insert(dev(inputs.uniform_points(4000 + 9000 * i, d, seed=i)))
+    ms = [100, 1, 40000, 2500, 0]            # one batch above the spatial-sort threshold
+    qs = [dev(inputs.uniform_points(m, d, seed=10 + i)) for i, (m, d) in enumerate(zip(ms, dims))]
+    plan = KnnPlan(F, qs, 6)
+    got = plan.launch()
+    want = knn_batch(F, qs, 6)
+    for (a, b), (c, d) in zip(got, want):
+        assert torch.equal(a, c) and torch.equal(b, d)
+    # new contents, same tensors
+    for i, (q, d) in enumerate(zip(qs, dims)):
+        q.copy_(dev(inputs.uniform_points(q.shape[0], d, seed=50 + i)))
+    got = [(a.clone(), b.clone()) for a, b in plan.launch()]
+    want = knn_batch(F, qs, 6)
+    for (a, b), (c, d) in zip(got, want):
+        assert torch.equal(a, c) and torch.equal(b, d)
+    # captured once, replayed with fresh queries
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.launch(stream=s)
+    for i, (q, d) in enumerate(zip(qs, dims)):
+        q.copy_(dev(inputs.uniform_points(q.shape[0], d, seed=90 + i)))
+    for o in plan.out:
+        o[0].fill_(-7)
+    g.replay()
+    torch.cuda.synchronize()
+    want = knn_batch(F, qs, 6)
+    for (a, b), (c, d) in zip(plan.out, want):
+        assert torch.equal(a, c) and torch.equal(b, d)
+    # an update invalidates the plan
+    F[1].insert(dev(inputs.uniform_points(10, 3, seed=1)))
+    with pytest.raises(capi.BdlError):
+        plan.launch()
+    plan.close()
+    for f in F:
+        f.close()
