@@ -350,7 +350,11 @@ __global__ void k_bloom_build_many(const TreeSeg *segs, const int64_t *pre, int 
   int64_t blk;
   uint64_t bits;
   bloom_hash(g.seed, g.blocks, id, blk, bits);
-  for (int w = 0; w < 8; ++w) atomicOr(&g.bloom[blk * 8 + w], bloom_word_bit(bits, w));
+  // the block's eight words as four 64-bit halves: four atomics per key
+  unsigned long long *b64 = reinterpret_cast<unsigned long long *>(g.bloom + blk * 8);
+  for (int w = 0; w < 4; ++w)
+    atomicOr(&b64[w], (unsigned long long)bloom_word_bit(bits, 2 * w) |
+                          ((unsigned long long)bloom_word_bit(bits, 2 * w + 1) << 32));
 }
 
 __global__ void k_pack_lives_many(const TreeSeg *segs, const int64_t *pre, int nseg) {

@@ -4,8 +4,11 @@
 // GPU design:
 //  * One thread per query walks the trees one after another with its own
 //    depth-first stack (nearer child first) and keeps its k best candidates
-//    sorted by (squared distance, id) in registers -- the role of the paper's
-//    2k-entry kNN buffer (Sec. IV-A3).
+//    sorted by (squared distance, id) in shared memory, the current k-th in
+//    registers -- the role of the paper's 2k-entry kNN buffer (Sec. IV-A3).
+//  * Leaf points are first tested with a float distance that can only
+//    overstate what the exact int64 test accepts; the exact distance is
+//    computed for the few that pass.
 //  * A subtree is skipped when its bounding box is farther than the current
 //    k-th distance (strictly) or when it holds no live point (the NULL
 //    subtree of Alg. 2).
@@ -153,8 +156,8 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
       const unsigned wm = __ballot_sync(0xffffffffu, pending || sp > 0);
       if (!wm) break;
       const unsigned pm = __ballot_sync(0xffffffffu, pending);
-      if (2 * __popc(pm) >= __popc(wm)) {
-        // at least half of the working lanes have a leaf due: scan them together
+      if (3 * __popc(pm) >= 2 * __popc(wm)) {
+        // two thirds of the working lanes have a leaf due: scan them together
         if (pending) {
           for (int j = pa; j < pz; ++j) {
             const int32_t *src = T.pts + (int64_t)j * rs;
@@ -171,6 +174,19 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
                 p[c4 + 3] = v.w;
               }
               id = p[D ? D : 0];
+              if (STATS) npts += id >= 0;
+              // float filter first: the rounded sum of squares is within
+              // (D + 1) * 2^-24 of the exact one, so after the 1 - 2^-18
+              // scaling it exceeds the rounded-up k-th distance only for a
+              // point whose exact distance exceeds the k-th; the exact int64
+              // distance is computed for the rest
+              float sf = 0.f;
+#pragma unroll
+              for (int c = 0; c < (D ? D : 1); ++c) {
+                const float g = (float)(q[c] - p[c]);
+                sf = fmaf(g, g, sf);
+              }
+              if (sf * (1.0f - 3.814697265625e-06f) > best.kdf) continue;
 #pragma unroll
               for (int c = 0; c < (D ? D : 1); ++c) {
                 int32_t g = q[c] - p[c];
@@ -178,13 +194,13 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
               }
             } else {
               id = src[dim];
+              if (STATS) npts += id >= 0;
               for (int c = 0; c < dim; ++c) {
                 int32_t g = q[c] - src[c];
                 s += (uint64_t)((int64_t)g * g);
               }
             }
-            if (id < 0) continue;
-            if (STATS) npts++;
+            if (id < 0) continue;   // erased
             if (best.better(s, id)) best.insert(s, id, k);
           }
           pending = false;
