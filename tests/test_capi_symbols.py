@@ -54,3 +54,38 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert out.value is None
     lib.bdl_destroy.restype = ctypes.c_int
     assert lib.bdl_destroy(None) == 0
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu(lib):
+    """The batched, plan and server entry points validate their arguments on the
+    host before any device work (so this runs without a GPU)."""
+    from paper_2112_06188_gb300 import capi
+    capi.load()
+    P = ctypes.c_void_p
+    # empty batches are no-ops
+    assert capi.bdl_insert_batch([], [], [], [], None) == capi.BDL_OK
+    assert capi.bdl_erase_batch([], [], [], None)[0] == capi.BDL_OK
+    assert capi.bdl_knn_batch([], [], [], 5, [], [], None) == capi.BDL_OK
+    # a NULL forest in a batch
+    assert capi.bdl_insert_batch([None], [None], [0], [None], None) == capi.BDL_EINVAL
+    assert capi.bdl_knn_batch([None], [None], [0], 5, [None], [None], None) == capi.BDL_EINVAL
+    # plans need at least one forest
+    st, h = capi.bdl_knn_plan_create([], [], [], 5, [], [], None)
+    assert st == capi.BDL_EINVAL and h is None
+    assert capi.bdl_knn_plan_launch(None, None) == capi.BDL_EINVAL
+    assert capi.bdl_knn_plan_destroy(None) == capi.BDL_OK
+    # servers
+    st, h = capi.bdl_server_create(None, None)
+    assert st == capi.BDL_EINVAL and h is None
+    req = capi.BdlRequest()
+    assert capi.bdl_server_submit(None, req)[0] == capi.BDL_EINVAL
+    assert capi.bdl_server_destroy(None) == capi.BDL_OK
+    cfg = capi.bdl_server_default_config()
+    assert cfg.max_inflight == 64 and cfg.serial == 0 and cfg.staging_budget_bytes == 1 << 30
+    # the splitting rule is part of the configuration and is checked
+    c = capi.bdl_default_config()
+    assert c.split_rule == capi.BDL_SPLIT_OBJECT
+    c.split_rule = 7
+    out = P()
+    assert lib.bdl_create(3, ctypes.byref(c), None, ctypes.c_int64(0), None, None, ctypes.byref(out)) == 1
+    assert "split_rule" in capi.last_error()
