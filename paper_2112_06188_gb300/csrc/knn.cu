@@ -97,6 +97,12 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
   return s * (1.0f - 3.814697265625e-06f);   // 1 - 2^-18
 }
 
+// A traversal stack entry: the node code and the lower bound of its box
+// distance, in one 64-bit word (one local-memory access per push and pop).
+__device__ __forceinline__ uint64_t stack_entry(float lb, int code) {
+  return ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)code;
+}
+
 // Largest j in [0, n) with pre[j] <= x (pre[0] = 0 <= x < pre[n]).
 __device__ __forceinline__ int knn_find(const int64_t *pre, int n, int64_t x) {
   int lo = 0, hi = n - 1;
@@ -134,8 +140,7 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
   TopK best;
   best.init(s_d, s_id);
   unsigned long long nvisit = 0, npts = 0;
-  int32_t sv[kStack];
-  float smd[kStack];
+  uint64_t stk[kStack];   // (distance bits << 32) | code
   const float kInf = __int_as_float(0x7f800000);
 
   const int ntrees = J.ntrees;
@@ -145,8 +150,7 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
     // code >= 0: internal node record; code < 0: leaf -1-code
     int sp = 0;
     if (active) {
-      sv[0] = T.h > 0 ? 0 : -1;
-      smd[0] = box_mindist_lb<D>(q, T.box, dim);
+      stk[0] = stack_entry(box_mindist_lb<D>(q, T.box, dim), T.h > 0 ? 0 : -1);
       sp = 1;
     }
     const int32_t ninternal = (int32_t)(((int64_t)1 << T.h) - 1);
@@ -210,8 +214,9 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
       // otherwise every lane without a due leaf takes one traversal step
       if (pending || sp == 0) continue;
       --sp;
-      const int code = sv[sp];
-      if (best.prune(smd[sp])) continue;
+      const uint64_t e = stk[sp];
+      const int code = (int)(uint32_t)e;
+      if (best.prune(__uint_as_float((uint32_t)(e >> 32)))) continue;
       if (STATS) nvisit++;
       int leaf = -1;
       if (code < 0) {
@@ -244,14 +249,13 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
         const bool lfirst = ml <= mr;
         const int vn = lfirst ? hdr.x : hdr.y, vf = lfirst ? hdr.y : hdr.x;
         const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
-        if (mf != kInf && !best.prune(mf)) { sv[sp] = vf; smd[sp] = mf; sp++; }
+        if (mf != kInf && !best.prune(mf)) { stk[sp] = stack_entry(mf, vf); sp++; }
         if (mn != kInf && !best.prune(mn)) {
           if (vn < 0) {          // nearer child is a leaf: due now
             if (STATS) nvisit++;
             leaf = -1 - vn;
           } else {
-            sv[sp] = vn;
-            smd[sp] = mn;
+            stk[sp] = stack_entry(mn, vn);
             sp++;
           }
         }
