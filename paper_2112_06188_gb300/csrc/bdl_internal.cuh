@@ -293,12 +293,14 @@ struct bdl_forest {
   uint64_t F = 0;
   int64_t live = 0;              // host mirror of the live count
   int64_t bytes_in_use = 0;
-  int64_t *pinned = nullptr;     // small pinned host scratch for counts
+  int64_t *pinned = nullptr;     // small pinned host scratch: [0, kPinnedFlags) insert flags,
+                                 // [500] the error word
   int64_t *dev_small = nullptr;  // small device scratch for counts / flags
   unsigned long long *err = nullptr;  // device error word (inside dev_small)
   bool debug_check = false;      // BDL_DEBUG_CHECK=1: sync and check err after each call
   unsigned long long *knn_stats = nullptr;  // [3] device counters, or nullptr
   uint64_t version = 0;          // bumped by every change of the trees or the buffer
+  cudaEvent_t ev_flags = nullptr;  // recorded behind the insert flags' copy
 };
 
 namespace bdl {
@@ -320,6 +322,7 @@ ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s);
 // BDL_DEBUG_CHECK: wait for the call's kernels and report a bounds-check hit.
 int finish_call(bdl_forest *f, cudaStream_t s, int status);
 constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input order
+constexpr size_t kPinnedFlags = 256;           // insert-validation flags that fit the pinned scratch
 int smem_subtree_capacity(int dim);
 
 // ---- build.cu ----

@@ -300,7 +300,9 @@ __global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
   switch (g.kind) {
     case kFillAppend: {            // copy coordinates into the id table, check the grid
       const int32_t v = g.src[i];
-      g.dst[i] = v;
+      // an off-grid value is flagged and stored clamped, so that work started
+      // before the flag is read back only ever sees grid coordinates
+      g.dst[i] = min(max(v, 0), (1 << kCoordBits) - 1);
       if (v < 0 || v >= (1 << kCoordBits)) atomicOr(g.flag, 1ull);
       break;
     }

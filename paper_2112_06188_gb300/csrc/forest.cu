@@ -523,9 +523,11 @@ struct Temp {
 
 // Build the planned trees of many forests, grouped by dimension, then fill
 // the new buffers and commit.  Plans with q == 0 only fill.
-static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTree> &bt,
-                            std::vector<ClearedSrc> &cl, std::vector<int> &bt_plan,
-                            std::vector<FillSeg> extra_fills, Temp &tmp, cudaStream_t s) {
+// Device work of the plans: build every new tree (one build per class) and
+// write the new buffers.  On failure every plan is dropped.
+static int build_planned(std::vector<InsertPlan> &plans, std::vector<BuildTree> &bt,
+                         std::vector<ClearedSrc> &cl, std::vector<int> &bt_plan, Temp &tmp,
+                         cudaStream_t s) {
   int st = BDL_OK;
   // one build per (dimension, splitting rule) present
   std::vector<int> classes;
@@ -550,11 +552,24 @@ static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTre
       if (remap[c.dst] >= 0) gc.push_back(ClearedSrc{c.pts, c.size, remap[c.dst]});
     st = build_trees(charge, charge->dim, g, gc, s);
   }
-  std::vector<FillSeg> fills = std::move(extra_fills);
+  std::vector<FillSeg> fills;
   for (auto &ip : plans)
     if (ip.f && (ip.q > 0 ? ip.rem > 0 : ip.n > 0)) fills.push_back(tail_fill(ip));
   void *table = nullptr;
   if (!st && !fills.empty()) st = tmp.get(table_bytes(fills.size(), sizeof(FillSeg)), &table);
+  if (!st && !fills.empty()) st = launch_fill_many(fills, table, s);
+  if (st)
+    for (auto &ip : plans) drop_plan(ip, s);
+  return st;
+}
+
+// Install built plans: the given fills (alive bits, ids out) on the device,
+// then the trees and buffers on the host.
+static int commit_planned(std::vector<InsertPlan> &plans, std::vector<FillSeg> fills, Temp &tmp,
+                          cudaStream_t s) {
+  int st = BDL_OK;
+  void *table = nullptr;
+  if (!fills.empty()) st = tmp.get(table_bytes(fills.size(), sizeof(FillSeg)), &table);
   if (!st && !fills.empty()) st = launch_fill_many(fills, table, s);
   if (st) {
     for (auto &ip : plans) drop_plan(ip, s);
@@ -563,6 +578,14 @@ static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTre
   for (auto &ip : plans)
     if (ip.f) commit_insert(ip, s);
   return BDL_OK;
+}
+
+static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTree> &bt,
+                            std::vector<ClearedSrc> &cl, std::vector<int> &bt_plan,
+                            std::vector<FillSeg> extra_fills, Temp &tmp, cudaStream_t s) {
+  const int st = build_planned(plans, bt, cl, bt_plan, tmp, s);
+  if (st) return st;
+  return commit_planned(plans, std::move(extra_fills), tmp, s);
 }
 
 // The buffer's points get a small kd-tree of their own for k-NN (the paper's
@@ -684,12 +707,32 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   for (size_t j = 0; j < app.size(); ++j) app[j].flag = (unsigned long long *)flags + j;
   cudaMemsetAsync(flags, 0, app.size() * 8, s);
   st = launch_fill_many(app, table, s);
-  std::vector<unsigned long long> hf(app.size());
-  if (!st) st = cuda_check(cudaMemcpyAsync(hf.data(), flags, hf.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
-  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  // The append stores off-grid coordinates clamped onto the grid and flags
+  // them.  With room for the flags in the forest's pinned scratch, the build
+  // goes ahead without waiting: it only ever sees grid coordinates, and its
+  // result is installed after the flags have come back clean (else dropped:
+  // nothing it wrote is reachable from the forest).  Without room, wait first.
+  int64_t *hf = F[0]->pinned;
+  const bool ahead = app.size() <= kPinnedFlags;
+  std::vector<int64_t> hf_big;
+  if (!ahead) {
+    hf_big.resize(app.size());
+    hf = hf_big.data();
+  }
+  if (!st) st = cuda_check(cudaMemcpyAsync(hf, flags, app.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st && ahead) {
+    if (!F[0]->ev_flags) st = cuda_check(cudaEventCreateWithFlags(&F[0]->ev_flags, cudaEventDisableTiming),
+                                         "cudaEventCreate");
+    if (!st) st = cuda_check(cudaEventRecord(F[0]->ev_flags, s), "cudaEventRecord");
+  }
+  if (!st && !ahead) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
-  for (auto v : hf)
-    if (v) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
+  auto off_grid = [&]() {
+    for (size_t j = 0; j < app.size(); ++j)
+      if (hf[j]) return true;
+    return false;
+  };
+  if (!ahead && off_grid()) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
   // 2. plan every forest (Alg. 3), allocating the new trees
   std::vector<InsertPlan> plans(nf);
   std::vector<BuildTree> bt;
@@ -703,9 +746,11 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   if (st) {
     for (auto &ip : plans)
       if (ip.f) drop_plan(ip, s);
+    if (ahead) cudaEventSynchronize(F[0]->ev_flags);   // the flags' copy targets pinned scratch
     return st;
   }
-  // 3. build, new buffers, alive bits and ids out, commit
+  // 3. build and new buffers; then, once the coordinates are known to be on
+  //    the grid, alive bits, ids out and the commit
   std::vector<FillSeg> post;
   for (int i = 0; i < nf; ++i) {
     if (n[i] == 0) continue;
@@ -723,7 +768,18 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
       post.push_back(g);
     }
   }
-  st = build_and_commit(plans, bt, cl, bt_plan, post, tmp, s);
+  st = build_planned(plans, bt, cl, bt_plan, tmp, s);
+  if (ahead) {
+    const int es = cuda_check(cudaEventSynchronize(F[0]->ev_flags), "cudaEventSynchronize");
+    if (!st) st = es;
+    if (!st && off_grid()) {
+      for (auto &ip : plans)
+        if (ip.f) drop_plan(ip, s);
+      return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
+    }
+  }
+  if (st) return st;   // (a failed build has dropped its plans)
+  st = commit_planned(plans, post, tmp, s);
   if (st) return st;
   for (int i = 0; i < nf; ++i) {
     F[i]->next_id += n[i];
@@ -1383,6 +1439,7 @@ int bdl_destroy(bdl_forest *f) {
   dev_free(f, f->dev_small, 4096, s);
   if (f->knn_stats) dev_free(f, f->knn_stats, 64, s);
   cudaStreamSynchronize(s);
+  if (f->ev_flags) cudaEventDestroy(f->ev_flags);
   if (f->pinned) cudaFreeHost(f->pinned);
   delete f;
   return cuda_check(cudaGetLastError(), "destroy");
