@@ -84,7 +84,9 @@ int bdl_create(int dim, const bdl_config *cfg, const int32_t *pts_dev, int64_t n
  * the overflow (Sec. IV-B1), trees are merged by binary-counter carry
  * F_new = F + (b + n) / X and the new trees are rebuilt with median splits in
  * vEB layout (Alg. 1).  A coordinate outside [0, 2^20) gives BDL_EINVAL and
- * leaves the forest unchanged.  Synchronises `stream` once (validation). */
+ * leaves the forest unchanged.  Waits once, before returning, for the
+ * validation of the coordinates (the new trees are built meanwhile on grid-
+ * clamped values and installed only if every coordinate was on the grid). */
 int bdl_insert(bdl_forest *f, const int32_t *pts_dev, int64_t n, int32_t *out_ids_dev,
                bdl_stream_t stream);
 
