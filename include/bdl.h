@@ -273,6 +273,11 @@ int bdl_server_destroy(bdl_server *s);
 /* Number of live points (host-side count, no device access). */
 int bdl_size(const bdl_forest *f, int64_t *out_live_host);
 
+/* The id the next inserted point will get, i.e. the number of ids assigned
+ * so far (host-side value, no device access).  After a successful insert of
+ * n points the ids were next_id - n .. next_id - 1. */
+int bdl_next_id(const bdl_forest *f, int64_t *out_next_id_host);
+
 /* Free the forest and all its device memory (waits for its pending work).
  * NULL is a no-op. */
 int bdl_destroy(bdl_forest *f);

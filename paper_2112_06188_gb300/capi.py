@@ -21,7 +21,7 @@ SYMBOLS = [
     "bdl_insert_batch", "bdl_erase_batch", "bdl_knn_batch",
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
     "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
-    "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy",
+    "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy", "bdl_next_id",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -111,6 +111,7 @@ def load(path=None):
         "bdl_knn_plan_create": (i32, [P, i32, P, P, i32, P, P, P, P]),
         "bdl_knn_plan_launch": (i32, [P, P]),
         "bdl_knn_plan_destroy": (i32, [P]),
+        "bdl_next_id": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -265,6 +266,12 @@ def bdl_server_destroy(s):
 def bdl_size(f):
     out = ctypes.c_int64(0)
     st = load().bdl_size(f, _ref(out))
+    return st, out.value
+
+
+def bdl_next_id(f):
+    out = ctypes.c_int64(0)
+    st = load().bdl_next_id(f, _ref(out))
     return st, out.value
 
 

@@ -1424,6 +1424,12 @@ int bdl_size(const bdl_forest *f, int64_t *out) {
   return BDL_OK;
 }
 
+int bdl_next_id(const bdl_forest *f, int64_t *out) {
+  if (!f || !out) return set_error(BDL_EINVAL, "NULL pointer");
+  *out = f->next_id;
+  return BDL_OK;
+}
+
 int bdl_destroy(bdl_forest *f) {
   if (!f) return BDL_OK;
   DeviceGuard g(f->device);

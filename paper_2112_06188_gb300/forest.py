@@ -86,13 +86,21 @@ class Forest:
         return t.cpu()
 
     def insert(self, points):
-        """Insert_L: returns the new ids (device tensor if points were on the device)."""
+        """Insert_L: returns the new ids (device tensor if points were on the
+        device; for host points a host tensor, known without a device read:
+        the ids are consecutive)."""
         on_host = not (isinstance(points, torch.Tensor) and points.is_cuda)
         p = self._dev(points, torch.int32).reshape(-1, self.dim)
+        if on_host:
+            capi.check(capi.bdl_insert(self._h, _ptr(p), p.shape[0], None, _stream_handle(self.stream)),
+                       "bdl_insert")
+            st, nxt = capi.bdl_next_id(self._h)
+            capi.check(st, "bdl_next_id")
+            return torch.arange(nxt - p.shape[0], nxt, dtype=torch.int32)
         ids = torch.empty(p.shape[0], dtype=torch.int32, device=self.device)
         capi.check(capi.bdl_insert(self._h, _ptr(p), p.shape[0], _ptr(ids),
                                    _stream_handle(self.stream)), "bdl_insert")
-        return self._host(ids) if on_host else ids
+        return ids
 
     def erase(self, ids):
         """Erase_L: returns the number of points erased."""
