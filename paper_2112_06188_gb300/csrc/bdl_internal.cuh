@@ -371,7 +371,7 @@ int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t 
                         int32_t *out, cudaStream_t s);
 
 // Table-driven helpers (one launch for many forests or trees).
-enum FillKind : int32_t { kFillAppend = 0, kFillPoolTail = 1, kFillIota = 2, kFillAlive = 3 };
+enum FillKind : int32_t { kFillAppend = 0, kFillPoolTail = 1, kFillIota = 2, kFillAlive = 3, kFillZero = 4 };
 struct FillSeg {           // `count` work items of one kind
   int32_t kind, pad_;
   int64_t count;

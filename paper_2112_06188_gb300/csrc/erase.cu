@@ -308,6 +308,7 @@ __global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
     }
     case kFillPoolTail: g.dst[i] = pool_entry(g, g.from + i); break;
     case kFillIota: g.dst[i] = (int32_t)(g.first + i); break;
+    case kFillZero: g.dst[i] = 0; break;
     case kFillAlive: {
       const int64_t id = g.first + i;
       atomicOr(&g.alive[id >> 5], 1u << (id & 31));

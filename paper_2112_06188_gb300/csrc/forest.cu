@@ -302,8 +302,11 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   t->live_nodes = (int32_t *)p; p += b_live;
   t->leaf_off = (int32_t *)p; p += b_leaf;
   t->pk = (int32_t *)p;
-  // unwritten nodes read as leaf 0 (children -1, -1): never outside the arrays
-  cudaMemsetAsync(t->node, 0xff, (size_t)t->nnodes * 16, s);
+  // Every build writes every node.  Under BDL_DEBUG_CHECK the node array starts
+  // filled with -1 anyway, so that a node a build failed to write reads the
+  // same each time; without it such a node could only trip the kernels' own
+  // index checks, which never step outside the arrays.
+  if (f->debug_check) cudaMemsetAsync(t->node, 0xff, (size_t)t->nnodes * 16, s);
   *out = t;
   return BDL_OK;
 }
@@ -841,6 +844,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   if (act.empty()) return BDL_OK;
   // 2. lazily build the bloom filter of every nonempty tree (Sec. V-A)
   std::vector<TreeSeg> blooms;
+  std::vector<FillSeg> zeros;
   for (int j : act) {
     bdl_forest *f = F[mk_forest[j]];
     for (int i = 0; i < kMaxLevel && !st; ++i) {
@@ -854,7 +858,12 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       t->bloom = (uint32_t *)b;
       t->bloom_blocks = blocks;
       t->bloom_bytes = (size_t)blocks * 32;
-      cudaMemsetAsync(t->bloom, 0, t->bloom_bytes, s);
+      FillSeg z;                     // zeroed in one launch with the others
+      memset(&z, 0, sizeof(z));
+      z.kind = kFillZero;
+      z.count = blocks * 8;
+      z.dst = (int32_t *)t->bloom;
+      zeros.push_back(z);
       TreeSeg g;
       memset(&g, 0, sizeof(g));
       g.pts = t->pts;
@@ -867,6 +876,12 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     }
   }
   if (st) return st;
+  if (!zeros.empty()) {
+    void *zt = nullptr;
+    st = tmp.get(table_bytes(zeros.size(), sizeof(FillSeg)), &zt);
+    if (!st) st = launch_fill_many(zeros, zt, s);
+    if (st) return st;
+  }
   if (!blooms.empty()) {
     void *bt = nullptr;
     st = tmp.get(table_bytes(blooms.size(), sizeof(TreeSeg)), &bt);
