@@ -236,6 +236,7 @@ struct Tree {
   int64_t size = 0, live = 0;
   int h = 0;
   int64_t nnodes = 0, nleaves = 0;
+  int64_t room = 0;        // points the arrays have room for (>= size)
   void *block = nullptr;   // one pool allocation holding the arrays below
   size_t bytes = 0;
   int32_t *pts = nullptr;      // [size][rec_ints(dim)] in leaf order
@@ -286,6 +287,7 @@ struct bdl_forest {
   uint32_t *alive = nullptr;     // [id_cap / 32]
   int64_t id_cap = 0, next_id = 0;
   int32_t *buf = nullptr;        // [X] ascending ids
+  int32_t *buf_spare = nullptr;  // [X] the previous buffer, reused as the next one
   int64_t nbuf = 0;
   bdl::Tree *trees[bdl::kMaxLevel] = {};
   bdl::Tree *btree = nullptr;    // kd-tree over the buffer's points (k-NN only), built lazily

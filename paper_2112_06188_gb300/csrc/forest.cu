@@ -276,19 +276,29 @@ static void free_tree(bdl_forest *f, Tree *t, cudaStream_t s) {
   delete t;
 }
 
-static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tree **out) {
-  Tree *t = new Tree();
-  t->level = level;
+// Set a tree's shape for `size` points (its arrays must have room for it).
+static void shape_tree(const bdl_forest *f, Tree *t, int64_t size) {
   t->size = size;
   t->live = size;
   t->h = tree_height(size, f->cfg.leaf_size);
   t->nnodes = ((int64_t)2 << t->h) - 1;
   t->nleaves = (int64_t)1 << t->h;
-  size_t b_pts = a256((size_t)rec_ints(f->dim) * size * 4),
+}
+
+// A tree of `size` points whose arrays have room for up to `room` points
+// (room >= size; the buffer's tree is laid out for a full buffer and reused).
+static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tree **out, int64_t room = 0) {
+  Tree *t = new Tree();
+  t->level = level;
+  room = std::max(room, size);
+  shape_tree(f, t, room);               // the layout is that of the largest shape
+  t->room = room;
+  size_t b_pts = a256((size_t)rec_ints(f->dim) * room * 4),
          b_node = a256((size_t)t->nnodes * 16),
          b_box = a256((size_t)t->nnodes * 2 * f->dim * 4), b_live = a256((size_t)t->nnodes * 4),
          b_leaf = a256((size_t)(t->nleaves + 1) * 4),
          b_pk = a256((size_t)(t->nleaves - 1) * packed_node_ints(f->dim) * 4);
+  shape_tree(f, t, size);
   t->bytes = b_pts + b_node + b_box + b_live + b_leaf + b_pk;
   int st = dev_alloc(f, &t->block, t->bytes, s);
   if (st) {
@@ -443,6 +453,13 @@ static int plan_insert(bdl_forest *f, const PoolSrc &pool, int64_t n, InsertPlan
     prev = j;
   }
   if (pos != ip.q * X) return set_error(BDL_EINTERNAL, "planner: pool split mismatch");
+  // the new buffer: the forest's spare one (the buffer before last, kept
+  // instead of freed), else a new allocation
+  if (f->buf_spare) {
+    ip.newbuf = f->buf_spare;
+    f->buf_spare = nullptr;
+    return BDL_OK;
+  }
   return dev_alloc(f, &ip.newbuf, (size_t)X * 4, s);
 }
 
@@ -450,7 +467,10 @@ static int plan_insert(bdl_forest *f, const PoolSrc &pool, int64_t n, InsertPlan
 static void drop_plan(InsertPlan &ip, cudaStream_t s) {
   for (Tree *t : ip.built) free_tree(ip.f, t, s);
   ip.built.clear();
-  if (ip.newbuf) dev_free(ip.f, ip.newbuf, (size_t)ip.f->cfg.buffer_size * 4, s);
+  if (ip.newbuf) {
+    if (!ip.f->buf_spare) ip.f->buf_spare = (int32_t *)ip.newbuf;
+    else dev_free(ip.f, ip.newbuf, (size_t)ip.f->cfg.buffer_size * 4, s);
+  }
   ip.newbuf = nullptr;
 }
 
@@ -493,7 +513,10 @@ static void commit_insert(InsertPlan &ip, cudaStream_t s) {
         f->trees[i] = nullptr;
       }
     for (Tree *t : ip.built) f->trees[t->level] = t;
-    dev_free(f, f->buf, (size_t)X * 4, s);
+    // the old buffer becomes the spare (its last readers are earlier on the
+    // stream than any writer of the next insert)
+    if (!f->buf_spare) f->buf_spare = f->buf;
+    else dev_free(f, f->buf, (size_t)X * 4, s);
     f->buf = (int32_t *)ip.newbuf;
     f->nbuf = ip.rem;
     f->F = ip.Fnew;
@@ -600,13 +623,21 @@ static void refresh_btrees(bdl_forest *const *F, int nf, cudaStream_t s) {
   for (int i = 0; i < nf; ++i) {
     bdl_forest *f = F[i];
     if (!f->buf_dirty) continue;
-    free_tree(f, f->btree, s);
-    f->btree = nullptr;
     f->buf_dirty = false;
     f->version++;
-    if (f->nbuf == 0) continue;
-    Tree *t = nullptr;
-    if (alloc_tree(f, kMaxLevel, f->nbuf, s, &t) != BDL_OK) continue;
+    // the tree's arrays have room for a full buffer and are rebuilt in place
+    // (earlier readers are earlier on the stream)
+    Tree *t = f->btree;
+    f->btree = nullptr;
+    if (f->nbuf == 0) {
+      free_tree(f, t, s);
+      continue;
+    }
+    if (t) {
+      shape_tree(f, t, f->nbuf);
+    } else if (alloc_tree(f, kMaxLevel, f->nbuf, s, &t, f->cfg.buffer_size) != BDL_OK) {
+      continue;
+    }
     BuildTree b;
     b.tree = t;
     b.s = f->nbuf;
@@ -1457,6 +1488,7 @@ int bdl_destroy(bdl_forest *f) {
     dev_free(f, f->alive, (size_t)f->id_cap / 8, s);
   }
   dev_free(f, f->buf, (size_t)f->cfg.buffer_size * 4, s);
+  dev_free(f, f->buf_spare, (size_t)f->cfg.buffer_size * 4, s);
   dev_free(f, f->dev_small, 4096, s);
   if (f->knn_stats) dev_free(f, f->knn_stats, 64, s);
   cudaStreamSynchronize(s);
