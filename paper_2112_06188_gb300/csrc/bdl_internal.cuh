@@ -243,7 +243,9 @@ struct Tree {
   int32_t *box = nullptr, *live_nodes = nullptr, *leaf_off = nullptr;
   Node *node = nullptr;        // [nnodes], vEB order
   int32_t *pk = nullptr;       // packed internal nodes (k-NN), (2^h - 1) records
-  uint32_t *bloom = nullptr;   // separate allocation, built lazily
+  uint32_t *bloom = nullptr;   // the bloom filter once built (lazily), else nullptr
+  uint32_t *bloom_room = nullptr;  // its place in the block (static trees)
+  int64_t bloom_room_blocks = 0;
   int64_t bloom_blocks = 0;
   size_t bloom_bytes = 0;
 };

@@ -271,9 +271,17 @@ int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
 
 static void free_tree(bdl_forest *f, Tree *t, cudaStream_t s) {
   if (!t) return;
-  dev_free(f, t->block, t->bytes, s);
-  dev_free(f, t->bloom, t->bloom_bytes, s);
+  dev_free(f, t->block, t->bytes, s);   // the bloom filter, if any, lives in the block
   delete t;
+}
+
+// Blocks of the split-block bloom filter of a tree of `size` points: the
+// smallest power of two with at least bits_per_key bits per point (Sec. V-A).
+static int64_t bloom_blocks_for(const bdl_forest *f, int64_t size) {
+  const int64_t need = (size * f->cfg.bloom_bits_per_key + 255) / 256;
+  int64_t blocks = 1;
+  while (blocks < need) blocks *= 2;
+  return blocks;
 }
 
 // Set a tree's shape for `size` points (its arrays must have room for it).
@@ -299,7 +307,11 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
          b_leaf = a256((size_t)(t->nleaves + 1) * 4),
          b_pk = a256((size_t)(t->nleaves - 1) * packed_node_ints(f->dim) * 4);
   shape_tree(f, t, size);
-  t->bytes = b_pts + b_node + b_box + b_live + b_leaf + b_pk;
+  // a static tree's bloom filter (Sec. V-A) is built lazily but its room is
+  // part of the block, so building it needs no allocation
+  const int64_t blocks = level < kMaxLevel ? bloom_blocks_for(f, size) : 0;
+  const size_t b_bloom = a256((size_t)blocks * 32);
+  t->bytes = b_pts + b_node + b_box + b_live + b_leaf + b_pk + b_bloom;
   int st = dev_alloc(f, &t->block, t->bytes, s);
   if (st) {
     delete t;
@@ -311,7 +323,9 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
   t->box = (int32_t *)p; p += b_box;
   t->live_nodes = (int32_t *)p; p += b_live;
   t->leaf_off = (int32_t *)p; p += b_leaf;
-  t->pk = (int32_t *)p;
+  t->pk = (int32_t *)p; p += b_pk;
+  t->bloom_room = blocks ? (uint32_t *)p : nullptr;
+  t->bloom_room_blocks = blocks;
   // Every build writes every node.  Under BDL_DEBUG_CHECK the node array starts
   // filled with -1 anyway, so that a node a build failed to write reads the
   // same each time; without it such a node could only trip the kernels' own
@@ -881,12 +895,12 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     for (int i = 0; i < kMaxLevel && !st; ++i) {
       Tree *t = f->trees[i];
       if (!t || t->live == 0 || t->bloom) continue;
-      int64_t need = (t->size * f->cfg.bloom_bits_per_key + 255) / 256, blocks = 1;
-      while (blocks < need) blocks *= 2;
-      void *b = nullptr;
-      st = dev_alloc(f, &b, (size_t)blocks * 32, s);
-      if (st) break;
-      t->bloom = (uint32_t *)b;
+      const int64_t blocks = t->bloom_room_blocks;
+      if (!t->bloom_room || blocks != bloom_blocks_for(f, t->size)) {
+        st = set_error(BDL_EINTERNAL, "tree without bloom room");
+        break;
+      }
+      t->bloom = t->bloom_room;
       t->bloom_blocks = blocks;
       t->bloom_bytes = (size_t)blocks * 32;
       FillSeg z;                     // zeroed in one launch with the others
