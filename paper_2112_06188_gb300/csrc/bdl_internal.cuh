@@ -297,8 +297,8 @@ struct bdl_forest {
   uint64_t F = 0;
   int64_t live = 0;              // host mirror of the live count
   int64_t bytes_in_use = 0;
-  int64_t *pinned = nullptr;     // small pinned host scratch: [0, kPinnedFlags) insert flags,
-                                 // [500] the error word
+  int64_t *pinned = nullptr;     // pinned host scratch [kPinnedWords]: [0, kPinnedFlags) insert
+                                 // flags, [kPinnedErr] the error word
   int64_t *dev_small = nullptr;  // small device scratch for counts / flags
   unsigned long long *err = nullptr;  // device error word (inside dev_small)
   bool debug_check = false;      // BDL_DEBUG_CHECK=1: sync and check err after each call
@@ -326,7 +326,9 @@ ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s);
 // BDL_DEBUG_CHECK: wait for the call's kernels and report a bounds-check hit.
 int finish_call(bdl_forest *f, cudaStream_t s, int status);
 constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input order
-constexpr size_t kPinnedFlags = 256;           // insert-validation flags that fit the pinned scratch
+constexpr size_t kPinnedWords = 2048;          // a forest's pinned scratch, in int64 words
+constexpr size_t kPinnedFlags = 2040;          // insert-validation flags that fit in it
+constexpr size_t kPinnedErr = 2044;            // where the error word is read back
 int smem_subtree_capacity(int dim);
 
 // ---- build.cu ----

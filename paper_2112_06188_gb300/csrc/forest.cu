@@ -1257,11 +1257,11 @@ static int knn_plan_launch(bdl_knn_plan *P, cudaStream_t s) {
 // BDL_EINTERNAL if one of them recorded an out-of-range index.
 static int finish(bdl_forest *f, cudaStream_t s, int st) {
   if (st || !f->debug_check) return st;
-  st = cuda_check(cudaMemcpyAsync(f->pinned + 500, f->err, 8, cudaMemcpyDeviceToHost, s), "copy");
+  st = cuda_check(cudaMemcpyAsync(f->pinned + kPinnedErr, f->err, 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "sync");
   if (st) return st;
-  if (f->pinned[500])
-    return set_error(BDL_EINTERNAL, "device bounds check failed, code " + std::to_string(f->pinned[500]));
+  if (f->pinned[kPinnedErr])
+    return set_error(BDL_EINTERNAL, "device bounds check failed, code " + std::to_string(f->pinned[kPinnedErr]));
   return BDL_OK;
 }
 
@@ -1382,7 +1382,7 @@ int bdl_create(int dim, const bdl_config *cfg, const int32_t *pts, int64_t n, in
   cudaStream_t s = (cudaStream_t)stream;
   st = cuda_check(cudaGetDevice(&f->device), "cudaGetDevice");
   if (!st) st = get_pool(f->device, &f->pool);
-  if (!st) st = cuda_check(cudaMallocHost((void **)&f->pinned, 4096), "cudaMallocHost");
+  if (!st) st = cuda_check(cudaMallocHost((void **)&f->pinned, kPinnedWords * 8), "cudaMallocHost");
   void *small = nullptr;
   if (!st) st = dev_alloc(f, &small, 4096, s);
   f->dev_small = (int64_t *)small;
