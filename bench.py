@@ -336,7 +336,7 @@ def forests_config(a, n_gpus):
     return {"workload": "%d independent forests, dim 2 or 3, sizes log-uniform in [1000, 200000], "
                         "uniform int32 points; per step per forest insert 5-20%% of its size, erase "
                         "2-10%% of its live ids, k=%d NN for 1000-5000 live-set queries" % (a.forests, a.k),
-            "forests": a.forests, "k": a.k, "leaf_size": 16, "buffer_size": 1024,
+            "forests": a.forests, "k": a.k, "leaf_size": a.leaf, "buffer_size": 1024,
             "l2": "flushed between steps (256 MB write), inputs resident in HBM",
             "parallelism": "one independent set of forests per GPU" if n_gpus > 1 else "single GPU"}
 
@@ -396,9 +396,23 @@ def run_forests(a, rank, world, dist):
     nsteps = a.warmup + a.steps
     steps = [W.step() for _ in range(nsteps)]
     nf = a.forests
+    autotune = None
+    if a.leaf == "auto":
+        from paper_2112_06188_gb300.autotune import tune_leaf_size_forests
+        t0 = time.perf_counter()
+        T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        with torch.cuda.stream(stream):
+            tinit = [T(p) for p in W.initial]
+            tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in steps[:2]]
+            best, ms_by_leaf = tune_leaf_size_forests(W.dims, tinit, tsteps, a.k, device=dev, stream=stream)
+        del tinit, tsteps
+        a.leaf = best
+        autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
+                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
+    a.leaf = int(a.leaf)
     with torch.cuda.stream(stream):
-        A = [Forest(d, stream=stream, device=dev) for d in W.dims]
-        B = [Forest(d, stream=stream, device=dev) for d in W.dims]
+        A = [Forest(d, leaf_size=a.leaf, stream=stream, device=dev) for d in W.dims]
+        B = [Forest(d, leaf_size=a.leaf, stream=stream, device=dev) for d in W.dims]
         hA = (ctypes.c_void_p * nf)(*[f._h for f in A])
         hB = [f._h for f in B]
         init = FlatInputs([(p, np.zeros(0, np.int32), np.zeros((0, p.shape[1]), np.int32))
@@ -543,7 +557,7 @@ def run_forests(a, rank, world, dist):
     res = {"msA": msA, "msB": msB, "launchesA": launchesA // a.steps, "launchesB": launchesB // a.steps,
            "prof": prof, "clocks": clk, "identical": bool(identical), "knn_repeat": knn_repeat,
            "ops": sum(flat[i].ops for i in range(a.warmup, nsteps)) / a.steps,
-           "inserted": sum(x.n_ins), "erased": sum(x.n_era), "queries": sum(x.m),
+           "inserted": sum(x.n_ins), "erased": sum(x.n_era), "queries": sum(x.m), "autotune": autotune,
            "points": int(sum(f.size() for f in A))}
     for f in A + B:
         f.close()
@@ -581,7 +595,7 @@ def report_forests(a, res, world):
         "metric": METRIC, "value": round(value, 1), "unit": "ops/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(msA["step"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": forests_config(a, world),
+        "data": "synthetic", "config": dict(forests_config(a, world), leaf_autotune=res["autotune"]),
         "phase_ms": {k: round(v, 3) for k, v in msA.items()},
         "per_forest_calls": {"value": round(res["ops"] * world / (msB["step"] * 1e-3), 1), "unit": "ops/s",
                              "phase_ms": {k: round(v, 3) for k, v in msB.items()},

@@ -75,3 +75,43 @@ def synthetic_steps(dim, n0, batch, queries, nsteps, seed, device=None):
         T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
         steps.append((T(ins), T(era.astype(np.int32)), T(q)))
     return torch.from_numpy(pts).to(dev), steps
+
+
+def time_forests_step(dims, leaf, initial, steps, k, device=None, stream=None, split="object"):
+    """Mean milliseconds of one batched step (insert, erase, k-NN over all the
+    forests in one call each) for forests with leaf size `leaf`; `initial[i]`
+    is forest i's first points and every step a list of per-forest (insert
+    points, erase ids, queries), all device tensors.  The first step is a
+    warm-up."""
+    from .forest import erase_batch, insert_batch, knn_batch
+    stream = stream or torch.cuda.current_stream(device)
+    forests = [Forest(d, leaf_size=leaf, stream=stream, device=device, split=split) for d in dims]
+    try:
+        insert_batch(forests, initial, stream=stream)
+        times = []
+        for i, st in enumerate(steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            insert_batch(forests, [x for x, _, _ in st], stream=stream)
+            erase_batch(forests, [e for _, e, _ in st], stream=stream)
+            knn_batch(forests, [q for _, _, q in st], k, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if i:
+                times.append(a.elapsed_time(b))
+        return float(np.mean(times))
+    finally:
+        for f in forests:
+            f.close()
+
+
+def tune_leaf_size_forests(dims, initial, steps, k, candidates=CANDIDATES, device=None, stream=None,
+                           split="object"):
+    """The fastest leaf size among `candidates` for a batched many-forest
+    workload (one leaf size for all forests), and each candidate's mean step
+    time (ms)."""
+    if len(steps) < 2:
+        raise ValueError("need a warm-up step and at least one timed step")
+    ms = {L: time_forests_step(dims, L, initial, steps, k, device, stream, split) for L in candidates}
+    return min(ms, key=ms.get), ms
