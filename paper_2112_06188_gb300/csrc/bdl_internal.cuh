@@ -188,9 +188,78 @@ struct __align__(16) Node {
 // multiple of 16 bytes (so a 3-D point is one int4: x, y, z, id).
 __host__ __device__ constexpr int rec_ints(int dim) { return (dim + 1 + 3) / 4 * 4; }
 
-// Ints of one packed k-NN node record: left/right child codes, their live
-// counts and their boxes (lo[dim], hi[dim] each), padded to 32 bytes.
-__host__ __device__ constexpr int packed_node_ints(int dim) { return (4 + 4 * dim + 7) / 8 * 8; }
+// Packed k-NN node records.  A tree with h internal levels has one record
+// for the root and one for every internal node at a depth t with h - t even
+// (t > 0); a record describes its node's four descendants two levels down
+// (the root of an odd h: its two children), each an internal node that has a
+// record of its own or a leaf.  Ints of a record: the four entries' codes
+// (record slot, or -1 - leaf index), their live counts, then per coordinate
+// c the four entries' low bounds and the four high bounds, so that one
+// 16-byte load gives one bound of every entry.  32-byte aligned for every dim.
+__host__ __device__ constexpr int packed_node_ints(int dim) { return 8 + 8 * dim; }
+
+__host__ __device__ inline int64_t quad_count(int H) {   // (4^H - 1) / 3 nodes in H 4-ary levels
+  return (((int64_t)1 << (2 * H)) - 1) / 3;
+}
+
+// Position of node (level u, index i) in the vEB order of a complete 4-ary
+// tree of H levels, split into top and bottom levels as veb_slot does.
+__host__ __device__ inline int64_t veb4_slot(int H, int u, int64_t i) {
+  int64_t off = 0;
+  while (H > 1) {
+    const int Hb = veb_bottom(H);
+    const int Ht = H - Hb;
+    if (u < Ht) {
+      H = Ht;
+    } else {
+      const int uu = u - Ht;
+      const int64_t j = i >> (2 * uu);
+      off += quad_count(Ht) + j * quad_count(Hb);
+      i &= ((int64_t)1 << (2 * uu)) - 1;
+      u = uu;
+      H = Hb;
+    }
+  }
+  return off;
+}
+
+// Records of a tree with h internal levels.
+__host__ __device__ inline int64_t packed_nrec(int h) {
+  if (h <= 0) return 0;
+  if (h & 1) return 1 + 2 * quad_count((h - 1) / 2);
+  return quad_count(h / 2);
+}
+
+// Levels from the record of a node at depth t down to its entries.
+__host__ __device__ inline int packed_step(int h, int t) { return ((h & 1) && t == 0) ? 1 : 2; }
+
+// Slot of the record of the node at depth t, index i.  Even h: the records
+// form one complete 4-ary tree, in vEB order.  Odd h: the root's record, then
+// the 4-ary trees under its two children, each in vEB order.
+__host__ __device__ inline int64_t packed_slot(int h, int t, int64_t i) {
+  if (!(h & 1)) return veb4_slot(h / 2, t / 2, i);
+  if (t == 0) return 0;
+  const int64_t sub = i >> (t - 1), il = i & (((int64_t)1 << (t - 1)) - 1);
+  return 1 + sub * quad_count((h - 1) / 2) + veb4_slot((h - 1) / 2, (t - 1) / 2, il);
+}
+
+// The g-th record in level order: depth t and index i of its node.
+__host__ __device__ inline void packed_record_of(int h, int64_t g, int &t, int64_t &i) {
+  const int odd = h & 1;
+  if (odd && g == 0) {
+    t = 0;
+    i = 0;
+    return;
+  }
+  int64_t y = odd ? g - 1 : g;
+  int u = 0;
+  while (y >= ((int64_t)(1 + odd) << (2 * u))) {   // 2 * 4^u (odd h) or 4^u nodes on level u
+    y -= (int64_t)(1 + odd) << (2 * u);
+    ++u;
+  }
+  t = 2 * u + odd;
+  i = y;
+}
 
 struct TreeView {          // one static tree, device pointers
   int32_t *pts;            // [size][rec_ints(dim)]: coordinates, id (erased: id | kTomb)
@@ -199,7 +268,7 @@ struct TreeView {          // one static tree, device pointers
   int32_t *live;           // [nnodes]
   const int32_t *leaf_off; // [2^h + 1]
   const uint32_t *bloom;   // [blocks * 8] or nullptr
-  int32_t *pk;             // packed internal nodes for k-NN, vEB order of the h internal levels
+  int32_t *pk;             // packed k-NN node records (packed_slot order)
   int64_t size;
   int64_t nnodes;
   int64_t bloom_blocks;
@@ -242,7 +311,7 @@ struct Tree {
   int32_t *pts = nullptr;      // [size][rec_ints(dim)] in leaf order
   int32_t *box = nullptr, *live_nodes = nullptr, *leaf_off = nullptr;
   Node *node = nullptr;        // [nnodes], vEB order
-  int32_t *pk = nullptr;       // packed internal nodes (k-NN), (2^h - 1) records
+  int32_t *pk = nullptr;       // packed k-NN node records, packed_nrec(h) of them
   uint32_t *bloom = nullptr;   // the bloom filter once built (lazily), else nullptr
   uint32_t *bloom_room = nullptr;  // its place in the block (static trees)
   int64_t bloom_room_blocks = 0;

@@ -360,17 +360,25 @@ __global__ void k_bloom_build_many(const TreeSeg *segs, const int64_t *pre, int 
                           ((unsigned long long)bloom_word_bit(bits, 2 * w + 1) << 32));
 }
 
+// One thread per packed k-NN record of many trees (pre[j] .. pre[j+1]-1 are
+// tree j's records in level order): copy its entries' refreshed live counts.
 __global__ void k_pack_lives_many(const TreeSeg *segs, const int64_t *pre, int nseg) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= pre[nseg]) return;
   const int j = seg_find(pre, nseg, x);
   const TreeSeg &g = segs[j];
-  const int64_t gi = x - pre[j];                 // g-th internal node in BFS order
-  const int t = 63 - __clzll(gi + 1);
-  const int64_t i = gi + 1 - ((int64_t)1 << t);
-  const Node nd = g.node[veb_slot(g.h + 1, t, i)];
-  const int2 lv = make_int2(g.live[nd.l], g.live[nd.r]);
-  *reinterpret_cast<int2 *>(g.pk + veb_slot(g.h, t, i) * packed_node_ints(g.dim) + 2) = lv;
+  int t;
+  int64_t i;
+  packed_record_of(g.h, x - pre[j], t, i);   // the record's node, and its entries two levels
+  const int st = packed_step(g.h, t);        // down (one for an odd tree's root)
+  int4 lv = make_int4(0, 0, 0, 0);
+  lv.x = g.live[veb_slot(g.h + 1, t + st, (i << st) + 0)];
+  lv.y = g.live[veb_slot(g.h + 1, t + st, (i << st) + 1)];
+  if (st == 2) {
+    lv.z = g.live[veb_slot(g.h + 1, t + st, (i << st) + 2)];
+    lv.w = g.live[veb_slot(g.h + 1, t + st, (i << st) + 3)];
+  }
+  *reinterpret_cast<int4 *>(g.pk + packed_slot(g.h, t, i) * packed_node_ints(g.dim) + 4) = lv;
 }
 
 // One CTA per forest: keep its buffer ids that are still alive, in order;
@@ -464,7 +472,7 @@ int launch_bloom_build_many(const std::vector<TreeSeg> &segs, void *table,
 
 int launch_pack_lives_many(const std::vector<TreeSeg> &segs, void *table, cudaStream_t s) {
   std::vector<int64_t> pre(segs.size() + 1, 0);
-  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + (((int64_t)1 << segs[j].h) - 1);
+  for (size_t j = 0; j < segs.size(); ++j) pre[j + 1] = pre[j] + packed_nrec(segs[j].h);
   if (pre.back() == 0) return BDL_OK;
   int st = upload_table(segs, pre, table, s);
   if (st) return st;

@@ -305,7 +305,7 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
          b_node = a256((size_t)t->nnodes * 16),
          b_box = a256((size_t)t->nnodes * 2 * f->dim * 4), b_live = a256((size_t)t->nnodes * 4),
          b_leaf = a256((size_t)(t->nleaves + 1) * 4),
-         b_pk = a256((size_t)(t->nleaves - 1) * packed_node_ints(f->dim) * 4);
+         b_pk = a256((size_t)packed_nrec(t->h) * packed_node_ints(f->dim) * 4);
   shape_tree(f, t, size);
   // a static tree's bloom filter (Sec. V-A) is built lazily but its room is
   // part of the block, so building it needs no allocation

@@ -12,9 +12,13 @@
 //  * A subtree is skipped when its bounding box is farther than the current
 //    k-th distance (strictly) or when it holds no live point (the NULL
 //    subtree of Alg. 2).
-//  * Each internal node has a packed record holding both children's codes,
-//    live counts and boxes, so one visit is one 32-byte-aligned read; the
-//    records of a tree follow the vEB order of its internal levels.
+//  * The walk reads packed records, each holding the codes, live counts and
+//    boxes of the four descendants two levels below its node: one visit
+//    orders four subtrees by their box distance and halves the chain of
+//    dependent reads from root to leaf.  The records of a tree follow the
+//    vEB order of the 4-ary tree they form.
+//  * A counting instance of the kernel walks the binary nodes instead and
+//    counts visited nodes and examined leaf points (measurement runs).
 //  * Large query batches are first put in spatial order (counting sort on a
 //    Morton prefix) so that a warp's threads walk neighbouring paths.
 #include "bdl_internal.cuh"
@@ -114,9 +118,241 @@ __device__ __forceinline__ int knn_find(const int64_t *pre, int n, int64_t x) {
   return lo;
 }
 
+// (a, ca), (b, cb) in ascending order of the bound.
+__device__ __forceinline__ void cmp_swap(float &a, int &ca, float &b, int &cb) {
+  if (b < a) {
+    const float tf = a;
+    a = b;
+    b = tf;
+    const int ti = ca;
+    ca = cb;
+    cb = ti;
+  }
+}
+
+// The exact test of the points [pa, pz) of tree T's leaf order against the
+// query: a float filter first (the rounded sum of squares is within (D + 1) *
+// 2^-24 of the exact one, so after the 1 - 2^-18 scaling it exceeds the
+// rounded-up k-th distance only for a point whose exact distance exceeds the
+// k-th), then the exact int64 distance for the points that pass.  Erased
+// points (negative ids) are skipped.
+template <int D, bool STATS>
+__device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, const int32_t *q, int dim,
+                                          int rs, int k, TopK &best, unsigned long long &npts) {
+  for (int j = pa; j < pz; ++j) {
+    const int32_t *src = T.pts + (int64_t)j * rs;
+    int32_t id;
+    uint64_t s = 0;
+    if (D) {
+      int32_t p[D ? rec_ints(D) : 4];
+#pragma unroll
+      for (int c4 = 0; c4 < (D ? rec_ints(D) : 4); c4 += 4) {
+        int4 v = *reinterpret_cast<const int4 *>(src + c4);
+        p[c4] = v.x;
+        p[c4 + 1] = v.y;
+        p[c4 + 2] = v.z;
+        p[c4 + 3] = v.w;
+      }
+      id = p[D ? D : 0];
+      if (STATS) npts += id >= 0;
+      float sf = 0.f;
+#pragma unroll
+      for (int c = 0; c < (D ? D : 1); ++c) {
+        const float g = (float)(q[c] - p[c]);
+        sf = fmaf(g, g, sf);
+      }
+      if (sf * (1.0f - 3.814697265625e-06f) > best.kdf) continue;
+#pragma unroll
+      for (int c = 0; c < (D ? D : 1); ++c) {
+        int32_t g = q[c] - p[c];
+        s += (uint64_t)((int64_t)g * g);
+      }
+    } else {
+      id = src[dim];
+      if (STATS) npts += id >= 0;
+      for (int c = 0; c < dim; ++c) {
+        int32_t g = q[c] - src[c];
+        s += (uint64_t)((int64_t)g * g);
+      }
+    }
+    if (id < 0) continue;   // erased
+    if (best.better(s, id)) best.insert(s, id, k);
+  }
+}
+
+// Alg. 5 on tree T over the packed records, for whole warps in lockstep: each
+// lane walks its own depth-first order (nearest entry first, the next entry
+// to visit held in a register, the rest on a stack), and the leaves that come
+// due wait until two thirds of the working lanes have one, so that the warp
+// scans them together.  A record gives the bounds of four entries at once.
+template <int D>
+__device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, bool active,
+                                            const int32_t *q, int dim, int k, TopK &best,
+                                            uint64_t *stk) {
+  const int rec = packed_node_ints(dim);
+  const int rs = rec_ints(dim);
+  const float kInf = __int_as_float(0x7f800000);
+  const float kScale = 1.0f - 3.814697265625e-06f;   // 1 - 2^-18, as in box_mindist_lb
+  unsigned long long unused = 0;
+  int sp = 0;
+  uint64_t cur = 0;   // the next entry to visit (code >= 0: record; < 0: leaf -1-code)
+  bool hc = false;
+  if (active) {
+    cur = stack_entry(box_mindist_lb<D>(q, T.box, dim), T.h > 0 ? 0 : -1);
+    hc = true;
+  }
+  const int32_t nleaf = (int32_t)((int64_t)1 << T.h);
+  const int32_t nrec = (int32_t)packed_nrec(T.h);
+  int pa = 0, pz = 0;
+  bool pending = false;   // a leaf [pa, pz) is due but not scanned yet
+  while (true) {
+    const unsigned wm = __ballot_sync(0xffffffffu, pending || hc || sp > 0);
+    if (!wm) break;
+    const unsigned pm = __ballot_sync(0xffffffffu, pending);
+    if (3 * __popc(pm) >= 2 * __popc(wm)) {
+      // two thirds of the working lanes have a leaf due: scan them together
+      if (pending) scan_leaf<D, false>(T, pa, pz, q, dim, rs, k, best, unused);
+      pending = false;
+      continue;
+    }
+    // otherwise every lane without a due leaf takes one traversal step
+    if (pending || (!hc && sp == 0)) continue;
+    uint64_t e;
+    if (hc) {
+      e = cur;
+      hc = false;
+    } else {
+      --sp;
+      e = stk[sp];
+    }
+    const int code = (int)(uint32_t)e;
+    if (best.prune(__uint_as_float((uint32_t)(e >> 32)))) continue;
+    int leaf = -1;
+    if (code < 0) {
+      leaf = -1 - code;
+    } else if (code >= nrec || sp + 3 > kStack) {
+      atomicOr(J.err, code >= nrec ? kErrChild : kErrStack);
+    } else {
+      const int32_t *r = T.pk + (int64_t)code * rec;
+      const int4 cd = *reinterpret_cast<const int4 *>(r);
+      const int4 lv = *reinterpret_cast<const int4 *>(r + 4);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;   // box distances (see box_mindist_lb)
+#pragma unroll
+      for (int c = 0; c < (D ? D : kMaxDim); ++c) {
+        if (c < dim) {
+          const int4 lo = *reinterpret_cast<const int4 *>(r + 8 + 8 * c);
+          const int4 hi = *reinterpret_cast<const int4 *>(r + 12 + 8 * c);
+          const int32_t x = q[c];
+          const float g0 = (float)(max(lo.x - x, 0) + max(x - hi.x, 0));
+          const float g1 = (float)(max(lo.y - x, 0) + max(x - hi.y, 0));
+          const float g2 = (float)(max(lo.z - x, 0) + max(x - hi.z, 0));
+          const float g3 = (float)(max(lo.w - x, 0) + max(x - hi.w, 0));
+          s0 = fmaf(g0, g0, s0);
+          s1 = fmaf(g1, g1, s1);
+          s2 = fmaf(g2, g2, s2);
+          s3 = fmaf(g3, g3, s3);
+        }
+      }
+      // entries without live points (and the two unused ones of an odd
+      // tree's root) are never visited
+      float b0 = lv.x > 0 ? s0 * kScale : kInf, b1 = lv.y > 0 ? s1 * kScale : kInf;
+      float b2 = lv.z > 0 ? s2 * kScale : kInf, b3 = lv.w > 0 ? s3 * kScale : kInf;
+      int c0 = cd.x, c1 = cd.y, c2 = cd.z, c3 = cd.w;
+      // ascending by bound: five compare-exchanges
+      cmp_swap(b0, c0, b1, c1);
+      cmp_swap(b2, c2, b3, c3);
+      cmp_swap(b0, c0, b2, c2);
+      cmp_swap(b1, c1, b3, c3);
+      cmp_swap(b1, c1, b2, c2);
+      if (b3 != kInf && !best.prune(b3)) stk[sp++] = stack_entry(b3, c3);
+      if (b2 != kInf && !best.prune(b2)) stk[sp++] = stack_entry(b2, c2);
+      if (b1 != kInf && !best.prune(b1)) stk[sp++] = stack_entry(b1, c1);
+      if (b0 != kInf && !best.prune(b0)) {
+        if (c0 < 0) {
+          leaf = -1 - c0;   // nearest entry is a leaf: due now
+        } else {
+          cur = stack_entry(b0, c0);
+          hc = true;
+        }
+      }
+    }
+    if (leaf >= 0) {
+      if (leaf >= nleaf) {
+        atomicOr(J.err, kErrChild);
+      } else {
+        pa = T.leaf_off[leaf];
+        pz = T.leaf_off[leaf + 1];
+        if (pa < 0 || pz > T.size || pa > pz) atomicOr(J.err, kErrLeaf);
+        else pending = true;
+      }
+    }
+  }
+}
+
+// Alg. 5 on tree T as the binary tree it is, one lane on its own: the node
+// arrays (children, boxes, live counts) instead of the packed records, the
+// nearer child first, a leaf scanned as soon as it is reached.  It decides
+// every prune exactly as walk_packed would at the binary nodes, and counts
+// the nodes it visits (a node or leaf taken from the stack and not pruned, or
+// a nearer child that is a leaf) and the live leaf points it examines: the
+// counting instance of the kernel, for measurement runs.
+template <int D>
+__device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, const int32_t *q,
+                                           int dim, int k, TopK &best, uint64_t *stk,
+                                           unsigned long long &nvisit, unsigned long long &npts) {
+  const int rs = rec_ints(dim);
+  const float kInf = __int_as_float(0x7f800000);
+  const int32_t nleaf = (int32_t)((int64_t)1 << T.h);
+  int sp = 0;
+  stk[sp++] = stack_entry(box_mindist_lb<D>(q, T.box, dim), 0);   // code: node slot
+  while (sp > 0) {
+    const uint64_t e = stk[--sp];
+    const int v = (int)(uint32_t)e;
+    if (best.prune(__uint_as_float((uint32_t)(e >> 32)))) continue;
+    nvisit++;
+    if (v < 0 || v >= T.nnodes) {
+      atomicOr(J.err, kErrChild);
+      continue;
+    }
+    const Node nd = T.node[v];
+    int leaf = -1;
+    if (nd.l < 0) {
+      leaf = -1 - nd.l;
+    } else if (nd.l >= T.nnodes || nd.r < 0 || nd.r >= T.nnodes || sp + 2 > kStack) {
+      atomicOr(J.err, sp + 2 > kStack ? kErrStack : kErrChild);
+    } else {
+      const float ml = T.live[nd.l] > 0 ? box_mindist_lb<D>(q, T.box + (int64_t)nd.l * 2 * dim, dim) : kInf;
+      const float mr = T.live[nd.r] > 0 ? box_mindist_lb<D>(q, T.box + (int64_t)nd.r * 2 * dim, dim) : kInf;
+      const bool lfirst = ml <= mr;
+      const int vn = lfirst ? nd.l : nd.r, vf = lfirst ? nd.r : nd.l;
+      const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
+      if (mf != kInf && !best.prune(mf)) stk[sp++] = stack_entry(mf, vf);
+      if (mn != kInf && !best.prune(mn)) {
+        const int nl = T.node[vn].l;
+        if (nl < 0) {   // nearer child is a leaf: scanned now
+          nvisit++;
+          leaf = -1 - nl;
+        } else {
+          stk[sp++] = stack_entry(mn, vn);
+        }
+      }
+    }
+    if (leaf >= 0) {
+      if (leaf >= nleaf) {
+        atomicOr(J.err, kErrChild);
+      } else {
+        const int pa = T.leaf_off[leaf], pz = T.leaf_off[leaf + 1];
+        if (pa < 0 || pz > T.size || pa > pz) atomicOr(J.err, kErrLeaf);
+        else scan_leaf<D, true>(T, pa, pz, q, dim, rs, k, best, npts);
+      }
+    }
+  }
+}
+
 // Query t of job J (one forest's batch) against the trees trees[0 ..
-// J.ntrees).  Called by whole warps of one job, which stay resident and
-// converged until each of their lanes is done.
+// J.ntrees), then the buffer.  The timed instance (STATS false) is called by
+// whole warps of one job, which stay resident and converged until each of
+// their lanes is done; the counting instance walks each lane on its own.
 template <int D, bool STATS>
 __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees, int64_t t, int k,
                                           unsigned long long *stats) {
@@ -129,10 +365,9 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
   int32_t *out_ids = J.oi;
   int64_t *out_d2 = J.od;
   const bool active = t < m;
+  if (STATS && !active) return;
   const int64_t qi = active ? (perm ? perm[t] : t) : 0;
   const int dim = D ? D : J.dim;
-  const int rec = packed_node_ints(dim);
-  const int rs = rec_ints(dim);
   int32_t q[D ? D : kMaxDim];
 #pragma unroll
   for (int c = 0; c < (D ? D : kMaxDim); ++c)
@@ -141,136 +376,13 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
   best.init(s_d, s_id);
   unsigned long long nvisit = 0, npts = 0;
   uint64_t stk[kStack];   // (distance bits << 32) | code
-  const float kInf = __int_as_float(0x7f800000);
 
   const int ntrees = J.ntrees;
   for (int ti = 0; ti < ntrees; ++ti) {
     const TreeView &T = trees[ti];
     if (T.live[0] <= 0) continue;
-    // code >= 0: internal node record; code < 0: leaf -1-code
-    int sp = 0;
-    if (active) {
-      stk[0] = stack_entry(box_mindist_lb<D>(q, T.box, dim), T.h > 0 ? 0 : -1);
-      sp = 1;
-    }
-    const int32_t ninternal = (int32_t)(((int64_t)1 << T.h) - 1);
-    int pa = 0, pz = 0;
-    bool pending = false;   // a leaf [pa, pz) is due but not scanned yet
-    while (true) {
-      const unsigned wm = __ballot_sync(0xffffffffu, pending || sp > 0);
-      if (!wm) break;
-      const unsigned pm = __ballot_sync(0xffffffffu, pending);
-      if (3 * __popc(pm) >= 2 * __popc(wm)) {
-        // two thirds of the working lanes have a leaf due: scan them together
-        if (pending) {
-          for (int j = pa; j < pz; ++j) {
-            const int32_t *src = T.pts + (int64_t)j * rs;
-            int32_t id;
-            uint64_t s = 0;
-            if (D) {
-              int32_t p[D ? rec_ints(D) : 4];
-#pragma unroll
-              for (int c4 = 0; c4 < (D ? rec_ints(D) : 4); c4 += 4) {
-                int4 v = *reinterpret_cast<const int4 *>(src + c4);
-                p[c4] = v.x;
-                p[c4 + 1] = v.y;
-                p[c4 + 2] = v.z;
-                p[c4 + 3] = v.w;
-              }
-              id = p[D ? D : 0];
-              if (STATS) npts += id >= 0;
-              // float filter first: the rounded sum of squares is within
-              // (D + 1) * 2^-24 of the exact one, so after the 1 - 2^-18
-              // scaling it exceeds the rounded-up k-th distance only for a
-              // point whose exact distance exceeds the k-th; the exact int64
-              // distance is computed for the rest
-              float sf = 0.f;
-#pragma unroll
-              for (int c = 0; c < (D ? D : 1); ++c) {
-                const float g = (float)(q[c] - p[c]);
-                sf = fmaf(g, g, sf);
-              }
-              if (sf * (1.0f - 3.814697265625e-06f) > best.kdf) continue;
-#pragma unroll
-              for (int c = 0; c < (D ? D : 1); ++c) {
-                int32_t g = q[c] - p[c];
-                s += (uint64_t)((int64_t)g * g);
-              }
-            } else {
-              id = src[dim];
-              if (STATS) npts += id >= 0;
-              for (int c = 0; c < dim; ++c) {
-                int32_t g = q[c] - src[c];
-                s += (uint64_t)((int64_t)g * g);
-              }
-            }
-            if (id < 0) continue;   // erased
-            if (best.better(s, id)) best.insert(s, id, k);
-          }
-          pending = false;
-        }
-        continue;
-      }
-      // otherwise every lane without a due leaf takes one traversal step
-      if (pending || sp == 0) continue;
-      --sp;
-      const uint64_t e = stk[sp];
-      const int code = (int)(uint32_t)e;
-      if (best.prune(__uint_as_float((uint32_t)(e >> 32)))) continue;
-      if (STATS) nvisit++;
-      int leaf = -1;
-      if (code < 0) {
-        leaf = -1 - code;
-      } else if (code >= ninternal || sp + 2 > kStack) {
-        atomicOr(J.err, code >= ninternal ? kErrChild : kErrStack);
-      } else {
-        const int32_t *r = T.pk + (int64_t)code * rec;
-        int4 hdr;
-        float ml, mr;
-        if (D) {
-          // the whole 32-byte-aligned record in 16-byte loads
-          int32_t rr[D ? packed_node_ints(D) : 4];
-#pragma unroll
-          for (int c4 = 0; c4 < (D ? packed_node_ints(D) : 4); c4 += 4) {
-            const int4 v = *reinterpret_cast<const int4 *>(r + c4);
-            rr[c4] = v.x;
-            rr[c4 + 1] = v.y;
-            rr[c4 + 2] = v.z;
-            rr[c4 + 3] = v.w;
-          }
-          hdr = make_int4(rr[0], rr[1], rr[2], rr[3]);
-          ml = hdr.z > 0 ? box_mindist_lb<D>(q, rr + 4, dim) : kInf;
-          mr = hdr.w > 0 ? box_mindist_lb<D>(q, rr + 4 + 2 * (D ? D : 1), dim) : kInf;
-        } else {
-          hdr = *reinterpret_cast<const int4 *>(r);
-          ml = hdr.z > 0 ? box_mindist_lb<D>(q, r + 4, dim) : kInf;
-          mr = hdr.w > 0 ? box_mindist_lb<D>(q, r + 4 + 2 * dim, dim) : kInf;
-        }
-        const bool lfirst = ml <= mr;
-        const int vn = lfirst ? hdr.x : hdr.y, vf = lfirst ? hdr.y : hdr.x;
-        const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
-        if (mf != kInf && !best.prune(mf)) { stk[sp] = stack_entry(mf, vf); sp++; }
-        if (mn != kInf && !best.prune(mn)) {
-          if (vn < 0) {          // nearer child is a leaf: due now
-            if (STATS) nvisit++;
-            leaf = -1 - vn;
-          } else {
-            stk[sp] = stack_entry(mn, vn);
-            sp++;
-          }
-        }
-      }
-      if (leaf >= 0) {
-        if (leaf > ninternal) {
-          atomicOr(J.err, kErrChild);
-        } else {
-          pa = T.leaf_off[leaf];
-          pz = T.leaf_off[leaf + 1];
-          if (pa < 0 || pz > T.size || pa > pz) atomicOr(J.err, kErrLeaf);
-          else pending = true;
-        }
-      }
-    }
+    if (STATS) walk_nodes<D>(J, T, q, dim, k, best, stk, nvisit, npts);
+    else walk_packed<D>(J, T, active, q, dim, k, best, stk);
   }
   if (!active) return;
   // the buffer tree: exact scan of its points
@@ -351,46 +463,41 @@ void launch_one(const KnnOne &P, int k, unsigned long long *stats, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------
-// packed node records: one per internal node, in the vEB order of the tree's
-// h internal levels (a complete tree of its own)
+// packed node records (packed_node_ints): one per record node, built from the
+// trees' node boxes and live counts
 // ---------------------------------------------------------------------------
 
-// One thread per internal node of many trees (table entry j owns the work
-// items pre[j] .. pre[j+1]-1, one per internal node of tree j).
+// One thread per record of many trees (table entry j owns the work items
+// pre[j] .. pre[j+1]-1, one per record of tree j, in level order).
 __global__ void k_pack_nodes(const TreeSeg *segs, const int64_t *pre, int nseg) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= pre[nseg]) return;
   const int j = knn_find(pre, nseg, x);
   const TreeSeg &T = segs[j];
-  const Node *node = T.node;
   const int32_t *box = T.box, *live = T.live;
   const int h = T.h, dim = T.dim;
-  int32_t *pk = T.pk;
-  const int64_t g = x - pre[j];
-  const int t = 63 - __clzll(g + 1);          // depth of the g-th internal node (BFS order)
-  const int64_t i = g + 1 - ((int64_t)1 << t);
-  const int64_t v = veb_slot(h + 1, t, i);    // slot among all nodes
-  const int64_t p = veb_slot(h, t, i);        // slot among internal nodes
-  const int rec = packed_node_ints(dim);
-  const int rs = rec_ints(dim);
-  int32_t *r = pk + p * rec;
-  const Node nd = node[v];
-  const int2 ch = make_int2(nd.l, nd.r);
-  int code[2];
-  if (t + 1 < h) {
-    code[0] = (int)veb_slot(h, t + 1, 2 * i);
-    code[1] = (int)veb_slot(h, t + 1, 2 * i + 1);
-  } else {
-    code[0] = (int)(-1 - 2 * i);
-    code[1] = (int)(-2 - 2 * i);
-  }
-  r[0] = code[0];
-  r[1] = code[1];
-  r[2] = live[ch.x];
-  r[3] = live[ch.y];
-  for (int c = 0; c < 2 * dim; ++c) {
-    r[4 + c] = box[(int64_t)ch.x * 2 * dim + c];
-    r[4 + 2 * dim + c] = box[(int64_t)ch.y * 2 * dim + c];
+  int t;
+  int64_t i;
+  packed_record_of(h, x - pre[j], t, i);
+  const int e = packed_step(h, t);
+  int32_t *r = T.pk + packed_slot(h, t, i) * packed_node_ints(dim);
+  for (int a = 0; a < 4; ++a) {
+    int code = 0, lv = 0;
+    const int32_t *bx = nullptr;
+    if (a < (1 << e)) {   // entry a: descendant (t + e, i * 2^e + a)
+      const int tc = t + e;
+      const int64_t ci = (i << e) + a;
+      code = tc == h ? (int)(-1 - ci) : (int)packed_slot(h, tc, ci);
+      const int64_t v = veb_slot(h + 1, tc, ci);
+      lv = live[v];
+      bx = box + v * 2 * dim;
+    }
+    r[a] = code;
+    r[4 + a] = lv;
+    for (int c = 0; c < dim; ++c) {
+      r[8 + 8 * c + a] = bx ? bx[c] : INT32_MAX;
+      r[12 + 8 * c + a] = bx ? bx[dim + c] : INT32_MIN;
+    }
   }
 }
 
@@ -605,7 +712,7 @@ void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<T
     g.live = t->live_nodes;
     g.pk = t->pk;
     segs.push_back(g);
-    pre.push_back(pre.back() + (((int64_t)1 << t->h) - 1));
+    pre.push_back(pre.back() + packed_nrec(t->h));
   }
 }
 
