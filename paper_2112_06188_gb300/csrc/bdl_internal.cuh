@@ -427,6 +427,7 @@ struct EraseCall {
   const int32_t *list;     // ids to erase (each live, each once)
   int64_t n;
   uint64_t seed;           // the forest's bloom hash seed
+  const int64_t *n_dev;    // if set: the list's length on the device (<= n)
 };
 struct EraseJob {          // device form of an EraseCall
   const TreeView *trees;
@@ -436,6 +437,7 @@ struct EraseJob {          // device form of an EraseCall
   const int32_t *list;
   int64_t n;
   uint64_t seed;
+  const int64_t *n_dev;
 };
 size_t erase_table_bytes(const std::vector<EraseCall> &calls);
 // Bloom probe, descent and tombstone for every call in one launch; the job
@@ -479,6 +481,7 @@ struct TreeSeg {           // one tree: bloom builds, record packing, live refre
   const int32_t *live;
   int32_t *pk;
   uint64_t seed;           // bloom hash seed (bloom builds)
+  const int64_t *gate;     // bloom builds: skipped when *gate == 0 (nullptr: always built)
 };
 struct BufSeg {            // one forest's buffer and roots
   int32_t *buf;
@@ -546,9 +549,12 @@ size_t query_sort_bytes(int64_t m, int dim);
 void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,
                        cudaStream_t s);
 // The same order for the points named by ids[m] (coordinates in coords):
-// out[m] receives the ids themselves, reordered.
+// out[m] receives the ids themselves, reordered.  With m_dev, only the first
+// min(*m_dev, m) ids are sorted (a count still on the device); out's tail past
+// them is left as it was.
 void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int dim,
-                       void *scratch, int32_t *out, cudaStream_t s);
+                       void *scratch, int32_t *out, cudaStream_t s,
+                       const int64_t *m_dev = nullptr);
 
 }  // namespace bdl
 

@@ -34,7 +34,8 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
   const EraseJob &F = jobs[lo];
   const int lane = threadIdx.x & 31;
   const int64_t i = (w - job_warp[lo]) * 32 + lane;
-  bool pending = i < F.n;
+  const int64_t n = F.n_dev ? min(*F.n_dev, F.n) : F.n;
+  bool pending = i < n;
   int32_t id = pending ? F.list[i] : 0;
   const int32_t *xq = F.idtab + (int64_t)id * F.dim;
   int32_t path[kMaxLevel + 2];
@@ -224,6 +225,7 @@ int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
     J.list = c.list;
     J.seed = c.seed;
     J.n = c.fv->ntrees ? c.n : 0;
+    J.n_dev = c.n_dev;
     for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
     warp[j + 1] = warp[j] + (J.n + 31) / 32;
   }
@@ -348,6 +350,7 @@ __global__ void k_bloom_build_many(const TreeSeg *segs, const int64_t *pre, int 
   if (x >= pre[nseg]) return;
   const int j = seg_find(pre, nseg, x);
   const TreeSeg &g = segs[j];
+  if (g.gate && *g.gate == 0) return;   // its forest's batch erased nothing
   const int32_t id = g.pts[(x - pre[j]) * rec_ints(g.dim) + g.dim];
   if (id < 0) return;
   int64_t blk;

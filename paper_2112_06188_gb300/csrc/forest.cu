@@ -838,10 +838,10 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
 
 static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s);
 
-// Erase_L on nf forests: one marking pass and one host sync to learn what was
-// erased, lazily built blooms, one descent launch, one live-count refresh,
-// one buffer compaction, one more sync for the counts; reinsertion of trees
-// below half then runs per forest (Alg. 4).
+// Erase_L on nf forests: one marking pass (its counts stay on the device),
+// lazily built blooms, one descent launch, one live-count refresh, one buffer
+// compaction, one host sync for the counts; reinsertion of trees below half
+// then runs for all forests together (Alg. 4).
 static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, const int64_t *n,
                       int64_t *out_n, cudaStream_t s) {
   for (int i = 0; i < nf; ++i) {
@@ -875,21 +875,18 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   }
   cudaMemsetAsync(counts, 0, mk.size() * 8, s);
   st = launch_erase_mark_many(mk, table, s);
-  std::vector<int64_t> ne(mk.size());
-  if (!st) st = cuda_check(cudaMemcpyAsync(ne.data(), counts, ne.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
-  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
-  std::vector<int> act;             // indices into mk of forests that erased something
-  for (size_t j = 0; j < mk.size(); ++j) {
-    if (out_n) out_n[mk_forest[j]] = ne[j];
-    F[mk_forest[j]]->live -= ne[j];
-    if (ne[j] > 0) F[mk_forest[j]]->version++;
-    if (ne[j] > 0) act.push_back((int)j);
-  }
-  if (act.empty()) return BDL_OK;
+  // Every forest with a nonempty batch takes part from here on without a wait
+  // for the counts: the launches are sized by the batch lengths and read the
+  // counts on the device, and a forest whose batch erased nothing is left as
+  // it was (its blooms get built, which an erase reaching it does anyway).
+  const int64_t *ne_dev = (const int64_t *)counts;
+  std::vector<int> act(mk.size());   // indices into mk of the forests taking part
+  for (size_t j = 0; j < mk.size(); ++j) act[j] = (int)j;
   // 2. lazily build the bloom filter of every nonempty tree (Sec. V-A)
   std::vector<TreeSeg> blooms;
   std::vector<FillSeg> zeros;
+  std::vector<std::pair<int, Tree *>> fresh;   // (index into mk, tree) of the blooms built here
   for (int j : act) {
     bdl_forest *f = F[mk_forest[j]];
     for (int i = 0; i < kMaxLevel && !st; ++i) {
@@ -903,6 +900,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       t->bloom = t->bloom_room;
       t->bloom_blocks = blocks;
       t->bloom_bytes = (size_t)blocks * 32;
+      fresh.emplace_back(j, t);
       FillSeg z;                     // zeroed in one launch with the others
       memset(&z, 0, sizeof(z));
       z.kind = kFillZero;
@@ -917,6 +915,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       g.bloom = t->bloom;
       g.blocks = blocks;
       g.seed = f->cfg.hash_seed;
+      g.gate = ne_dev + j;            // built only if the batch erases something
       blooms.push_back(g);
     }
   }
@@ -942,15 +941,16 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     bdl_forest *f = F[mk_forest[j]];
     views[a] = forest_view(f);
     const int32_t *order = mk[j].list;
-    if (ne[j] >= kSortMinQueries) {
+    const int64_t nj = mk[j].n;       // the owned ids are the first ne_dev[j] of the list
+    if (nj >= kSortMinQueries) {
       void *sorted = nullptr;
-      if (tmp.get(a256((size_t)ne[j] * 4) + query_sort_bytes(ne[j], f->dim), &sorted) == BDL_OK) {
-        launch_point_sort(f->idtab, mk[j].list, ne[j], f->dim,
-                          (char *)sorted + a256((size_t)ne[j] * 4), (int32_t *)sorted, s);
+      if (tmp.get(a256((size_t)nj * 4) + query_sort_bytes(nj, f->dim), &sorted) == BDL_OK) {
+        launch_point_sort(f->idtab, mk[j].list, nj, f->dim, (char *)sorted + a256((size_t)nj * 4),
+                          (int32_t *)sorted, s, ne_dev + j);
         order = (const int32_t *)sorted;
       }
     }
-    calls.push_back(EraseCall{&views[a], order, ne[j], f->cfg.hash_seed});
+    calls.push_back(EraseCall{&views[a], order, nj, f->cfg.hash_seed, ne_dev + j});
   }
   {
     void *et = nullptr;
@@ -995,15 +995,21 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   }
   st = tmp.get(table_bytes(bufs.size(), sizeof(BufSeg)), &bt2);
   if (!st) st = launch_buffer_compact_many(bufs, bt2, s);
-  std::vector<int64_t> ho(act.size() * (kMaxLevel + 1));
+  std::vector<int64_t> ho(act.size() * (kMaxLevel + 1)), ne(mk.size());
   if (!st) st = cuda_check(cudaMemcpyAsync(ho.data(), outs, ho.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaMemcpyAsync(ne.data(), counts, ne.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
   // 5. new counts; trees below half capacity are emptied and their points
   //    reinserted (Alg. 4), all forests' reinsertions built together
   std::vector<bdl_forest *> touched;
   for (size_t a = 0; a < act.size(); ++a) {
-    bdl_forest *f = F[mk_forest[act[a]]];
+    const int j = act[a];
+    bdl_forest *f = F[mk_forest[j]];
+    if (out_n) out_n[mk_forest[j]] = ne[j];
+    f->live -= ne[j];
+    if (ne[j] == 0) continue;   // nothing erased: counts and trees as they were
+    f->version++;
     const int64_t *o = &ho[a * (kMaxLevel + 1)];
     if (o[0] != f->nbuf) f->buf_dirty = true;
     f->nbuf = o[0];
@@ -1012,6 +1018,14 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       if (f->trees[i]) f->trees[i]->live = o[1 + r++];
     touched.push_back(f);
   }
+  // a forest whose batch erased nothing had its new blooms skipped on the
+  // device: they stay unbuilt, as if the erase had not reached the forest
+  for (const auto &ft : fresh)
+    if (ne[ft.first] == 0) {
+      ft.second->bloom = nullptr;
+      ft.second->bloom_blocks = 0;
+      ft.second->bloom_bytes = 0;
+    }
   st = reinsert_low(touched, s);
   if (st) return st;
   return cuda_check(cudaGetLastError(), "erase");

@@ -183,7 +183,7 @@ __device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, con
 // Alg. 5 on tree T over the packed records, for whole warps in lockstep: each
 // lane walks its own depth-first order (nearest entry first, the next entry
 // to visit held in a register, the rest on a stack), and the leaves that come
-// due wait until two thirds of the working lanes have one, so that the warp
+// due wait until half of the working lanes have one, so that the warp
 // scans them together.  A record gives the bounds of four entries at once.
 template <int D>
 __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, bool active,
@@ -209,8 +209,8 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
     const unsigned wm = __ballot_sync(0xffffffffu, pending || hc || sp > 0);
     if (!wm) break;
     const unsigned pm = __ballot_sync(0xffffffffu, pending);
-    if (3 * __popc(pm) >= 2 * __popc(wm)) {
-      // two thirds of the working lanes have a leaf due: scan them together
+    if (2 * __popc(pm) >= __popc(wm)) {
+      // half of the working lanes have a leaf due: scan them together
       if (pending) scan_leaf<D, false>(T, pa, pz, q, dim, rs, k, best, unused);
       pending = false;
       continue;
@@ -528,9 +528,10 @@ __device__ __forceinline__ const int32_t *point_row(const int32_t *coords, const
   return coords + (ids ? (int64_t)ids[i] : i) * dim;
 }
 
-__global__ void k_qkey_hist(const int32_t *coords, const int32_t *ids, int64_t m, int dim, int B,
-                            uint32_t *hist) {
+__global__ void k_qkey_hist(const int32_t *coords, const int32_t *ids, int64_t m,
+                            const int64_t *m_dev, int dim, int B, uint32_t *hist) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m_dev && i >= *m_dev) return;
   if (i < m) atomicAdd(&hist[morton_key(point_row(coords, ids, i, dim), dim, B)], 1u);
 }
 
@@ -594,10 +595,11 @@ __global__ void k_scan_top(uint32_t *bsum, int64_t nb) {
 }
 
 // out[pos] = i (query order) or ids[i] (the ids themselves, reordered)
-__global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m, int dim, int B,
-                           uint32_t *offs, const uint32_t *bsum, int32_t *out) {
+__global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m,
+                           const int64_t *m_dev, int dim, int B, uint32_t *offs,
+                           const uint32_t *bsum, int32_t *out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+  if (i >= m || (m_dev && i >= *m_dev)) return;
   uint32_t key = morton_key(point_row(coords, ids, i, dim), dim, B);
   uint32_t pos = bsum[key / kScanPer] + atomicAdd(&offs[key], 1u);
   if (pos < m) out[pos] = ids ? ids[i] : (int32_t)i;
@@ -729,7 +731,7 @@ size_t query_sort_bytes(int64_t m, int dim) {
 }
 
 void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int dim,
-                       void *scratch, int32_t *out, cudaStream_t s) {
+                       void *scratch, int32_t *out, cudaStream_t s, const int64_t *m_dev) {
   const int B = morton_bits_per_dim(dim);
   const int64_t nbins = (int64_t)1 << (B * dim);
   const int64_t nb = (nbins + kScanPer - 1) / kScanPer;   // <= 256
@@ -737,10 +739,10 @@ void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int
   uint32_t *bsum = (uint32_t *)((char *)scratch + ((size_t)nbins * 4 + 255) / 256 * 256);
   cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s);
   const unsigned g = (unsigned)((m + 255) / 256);
-  { KScope ks_(kK_qsort, s); k_qkey_hist<<<g, 256, 0, s>>>(coords, ids, m, dim, B, hist); }
+  { KScope ks_(kK_qsort, s); k_qkey_hist<<<g, 256, 0, s>>>(coords, ids, m, m_dev, dim, B, hist); }
   { KScope ks_(kK_qsort, s); k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum); }
   { KScope ks_(kK_qsort, s); k_scan_top<<<1, 1024, 0, s>>>(bsum, nb); }
-  { KScope ks_(kK_qsort, s); k_qscatter<<<g, 256, 0, s>>>(coords, ids, m, dim, B, hist, bsum, out); }
+  { KScope ks_(kK_qsort, s); k_qscatter<<<g, 256, 0, s>>>(coords, ids, m, m_dev, dim, B, hist, bsum, out); }
 }
 
 void launch_query_sort(const int32_t *q, int64_t m, int dim, void *scratch, int32_t *perm,

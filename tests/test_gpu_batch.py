@@ -167,6 +167,32 @@ def test_batch_mixed_dims_and_configs():
     w.close()
 
 
+def test_batch_erase_where_some_forests_erase_nothing():
+    """In one erase batch, the forests whose ids are all dead or absent are left
+    exactly as their single calls leave them (lazy blooms still unbuilt), while
+    the others erase, including some already erased ids again."""
+    nf = 8
+    w = Workload(nf, 2000, 20000, dims=(2, 3), seed=17)
+    run_insert(w, [w.points(i, int(w.sizes[i])) for i in range(nf)])
+    for step in range(2):
+        ids = []
+        for i in range(nf):
+            lid = w.live[i].live_ids()
+            n_ids = len(w.live[i].alive)
+            if (i + step) % 2:
+                ids.append(np.array([n_ids + 10, -5, n_ids + 10, n_ids], np.int32))
+            else:
+                ids.append(inputs.sample_ids(lid, len(lid) // 5, seed=10 * step + i))
+        run_erase(w, ids)
+        for i in range(nf):
+            same_state(w.A[i], w.B[i], "step %d forest %d" % (step, i))
+        run_erase(w, ids)             # the same batches again: nothing left to erase
+        for i in range(nf):
+            same_state(w.A[i], w.B[i], "step %d again, forest %d" % (step, i))
+        run_knn(w, 6, 100, 2000)
+    w.close()
+
+
 def test_batch_large_queries_sorted_path():
     """Query batches above the spatial-sort threshold in some forests, below it in others."""
     w = Workload(4, 40000, 120000, dims=(3,), seed=9)

@@ -237,6 +237,33 @@ def test_edge_cases():
     assert_same_knn(g, o, q, 32)
 
 
+def test_erase_batches_that_erase_nothing():
+    """A batch with no live id (never inserted, negative, already erased,
+    repeated) changes nothing, not even the lazy bloom filters (Sec. V-A):
+    they are built by the first erase that erases something."""
+    dim = 3
+    g, o = make(dim, 16, 64)
+    p = inputs.uniform_points(5000, dim, seed=21)
+    g.insert(to_dev(p))
+    o.insert(p)
+    dead = np.array([50000, 70000, -1, 123456, 50000], np.int32)   # never inserted
+    assert g.erase(to_dev(dead)) == o.erase(dead) == 0
+    assert_same_forest(g, o)
+    assert all(g.tree(lvl)["bloom"] is None for lvl in o.tree_levels())
+    ids = np.arange(0, 5000, 7, dtype=np.int32)
+    assert g.erase(to_dev(ids)) == o.erase(ids) == len(ids)
+    assert_same_forest(g, o)
+    assert all(g.tree(lvl)["bloom"] is not None for lvl in o.tree_levels())
+    again = np.concatenate([ids[:50], ids[:50], dead])
+    assert g.erase(to_dev(again)) == o.erase(again) == 0
+    p2 = inputs.uniform_points(3000, dim, seed=23)   # new trees: blooms unbuilt again
+    g.insert(to_dev(p2))
+    o.insert(p2)
+    assert g.erase(to_dev(again)) == o.erase(again) == 0
+    assert_same_forest(g, o)
+    assert_same_knn(g, o, inputs.uniform_points(300, dim, seed=22), 10)
+
+
 def test_host_buffers_end_to_end():
     """The public API with host (numpy) arrays copies in and out itself."""
     dim = 3
