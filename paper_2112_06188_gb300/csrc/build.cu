@@ -14,7 +14,8 @@
 //    that moves whole records into the other staging buffer.
 //  * Once segments fit in shared memory, one CTA builds each remaining
 //    subtree entirely on chip (radix select on the composite key with
-//    per-level digit widths, rank-counting for segments <= 64 points),
+//    per-level digit widths; a bitonic sort across one warp for segments
+//    <= 64 points),
 //    writes leaves, bounding boxes and live counts, and stores the points in
 //    leaf order.
 //  * Node slots follow the vEB layout in closed form (veb_slot), children are
@@ -29,7 +30,7 @@ namespace {
 
 constexpr int kItems = 8;          // records per thread in the tiled kernels
 constexpr int kSubThreads = 1024;  // threads of the subtree kernel
-constexpr int kWarpMode = 64;      // segments this small use rank counting
+constexpr int kWarpMode = 64;      // segments this small are sorted by one warp
 constexpr int kMaxRadixSegs = 128; // segments per level in radix mode (cap / 64)
 
 struct SegState {
@@ -252,23 +253,28 @@ __global__ void k_level_bucket(const LvParams P, int64_t nseg) {
   }
   const bool hit = inc >= r && inc - sum < r;
   const unsigned m = __ballot_sync(0xffffffffu, hit);
-  if (!hit || lane != __ffs(m) - 1) return;
-  uint32_t below = inc - sum;
-  const uint32_t *bins = P.hist + gs * kHistBins + lane * kRun;
-  for (int j = 0; j < kRun; ++j) {
-    const uint32_t v = bins[j];
-    if (below + v >= r) {
-      SegState &S = P.seg[gs];
-      S.bucket = lane * kRun + j;
-      S.nbucket = (int32_t)v;
-      S.rank = (int64_t)(r - below);
-      S.cand_n = 0;
-      S.lcur = 0;
-      S.rcur = 0;
-      return;
+  uint32_t *bins = P.hist + gs * kHistBins + lane * kRun;
+  if (hit && lane == __ffs(m) - 1) {
+    uint32_t below = inc - sum;
+    for (int j = 0; j < kRun; ++j) {
+      const uint32_t v = bins[j];
+      if (below + v >= r) {
+        SegState &S = P.seg[gs];
+        S.bucket = lane * kRun + j;
+        S.nbucket = (int32_t)v;
+        S.rank = (int64_t)(r - below);
+        S.cand_n = 0;
+        S.lcur = 0;
+        S.rcur = 0;
+        break;
+      }
+      below += v;
     }
-    below += v;
   }
+  // leave the bins zeroed for the next level's histogram
+  uint4 *zrun = reinterpret_cast<uint4 *>(bins);
+#pragma unroll
+  for (int j = 0; j < kRun / 4; ++j) zrun[j] = make_uint4(0, 0, 0, 0);
 }
 
 // Gather the (low coordinate bits, id) keys of every record in its segment's
@@ -520,6 +526,40 @@ struct SubParams {
   const int64_t *sub_blk;      // [ntrees + 1] prefix of 2^g subtrees per tree
 };
 
+// Ascending bitonic sort of one 64-bit word per lane across a warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t x, int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const uint64_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+      const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+      x = keep_min ? min(x, y) : max(x, y);
+    }
+  return x;
+}
+
+// Ascending bitonic sort of 64 words across a warp, lane l holding elements
+// 2l (x0) and 2l + 1 (x1).
+__device__ __forceinline__ void warp_sort64(uint64_t &x0, uint64_t &x1, int lane) {
+  const int e = 2 * lane;
+#pragma unroll
+  for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 1; stride >>= 1) {
+      const uint64_t y0 = __shfl_xor_sync(0xffffffffu, x0, stride >> 1);
+      const uint64_t y1 = __shfl_xor_sync(0xffffffffu, x1, stride >> 1);
+      const bool keep_min = ((e & stride) == 0) == ((e & size) == 0);
+      x0 = keep_min ? min(x0, y0) : max(x0, y0);
+      x1 = keep_min ? min(x1, y1) : max(x1, y1);
+    }
+    const uint64_t lo = min(x0, x1), hi = max(x0, x1);   // stride 1: inside the lane
+    const bool up = (e & size) == 0;
+    x0 = up ? lo : hi;
+    x1 = up ? hi : lo;
+  }
+}
+
 __device__ __forceinline__ uint64_t skey(const int32_t *sc, const int32_t *sid, int cap, int c,
                                          int it) {
   return comp_key(sc[c * cap + it], sid[it]);
@@ -732,36 +772,36 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       __syncthreads();
       unsigned char *ts = segid; segid = segid_n; segid_n = ts;
     } else {
-      // ---------------- warp mode: rank counting per segment --------------
+      // ---------------- warp mode: one warp sorts each segment -------------
+      // Words (key << 13 | position) are distinct and order like the keys
+      // (positions < cap <= 8192); a bitonic network across the warp sorts
+      // them, so the segment comes out in key order and its median is at
+      // rank ceil(z/2) - 1.
       for (int s = warp; s < nseg; s += nwarps) {
         int64_t a64, z64;
         seg_range(m0, u, s, a64, z64);
-        int a = (int)a64, z = (int)z64;
-        bool va = lane < z, vb = lane + 32 < z;
+        const int a = (int)a64, z = (int)z64;
         if (z > 64) { if (lane == 0) atomicOr(T.err, kErrPartition); continue; }
-        uint64_t ka = va ? skey(sc, sid, cap, c, cur[a + lane]) : ~0ull;
-        uint64_t kb = vb ? skey(sc, sid, cap, c, cur[a + 32 + lane]) : ~0ull;
-        int ra = 0, rb = 0;
-        int z1 = min(z, 32);
-        for (int y = 0; y < z1; ++y) {
-          uint64_t ky = __shfl_sync(0xffffffffu, ka, y);
-          ra += ky < ka;
-          rb += ky < kb;
+        const int mr = ((z + 1) >> 1) - 1;
+        uint64_t med = 0;
+        if (z <= 32) {
+          uint64_t x = lane < z ? (skey(sc, sid, cap, c, cur[a + lane]) << 13) | cur[a + lane] : ~0ull;
+          x = warp_sort32(x, lane);
+          if (lane < z) nxt[a + lane] = (uint16_t)(x & 8191u);
+          med = __shfl_sync(0xffffffffu, x, mr);
+        } else {
+          const int e0 = 2 * lane, e1 = 2 * lane + 1;
+          uint64_t x0 = e0 < z ? (skey(sc, sid, cap, c, cur[a + e0]) << 13) | cur[a + e0] : ~0ull;
+          uint64_t x1 = e1 < z ? (skey(sc, sid, cap, c, cur[a + e1]) << 13) | cur[a + e1] : ~0ull;
+          warp_sort64(x0, x1, lane);
+          if (e0 < z) nxt[a + e0] = (uint16_t)(x0 & 8191u);
+          if (e1 < z) nxt[a + e1] = (uint16_t)(x1 & 8191u);
+          med = __shfl_sync(0xffffffffu, (mr & 1) ? x1 : x0, mr >> 1);
         }
-        for (int y = 32; y < z; ++y) {
-          uint64_t ky = __shfl_sync(0xffffffffu, kb, y - 32);
-          ra += ky < ka;
-          rb += ky < kb;
-        }
-        uint16_t pa = va ? cur[a + lane] : 0, pbv = vb ? cur[a + 32 + lane] : 0;
-        if (va) nxt[a + ra] = pa;
-        if (vb) nxt[a + rb] = pbv;
-        int mr = ((z + 1) >> 1) - 1;
-        int64_t bfs = (i0 << u) + s;
-        if ((va && ra == mr) || (vb && rb == mr)) {
-          int64_t v = veb_slot(l, t, bfs);
-          o.node[v] = Node{(va && ra == mr) ? ka : kb, (int32_t)veb_slot(l, t + 1, 2 * bfs),
-                           (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
+        if (lane == 0) {
+          const int64_t bfs = (i0 << u) + s;
+          o.node[veb_slot(l, t, bfs)] = Node{med >> 13, (int32_t)veb_slot(l, t + 1, 2 * bfs),
+                                             (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
         }
       }
       __syncthreads();
@@ -1046,12 +1086,12 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   stg[0] = (int32_t *)p; p += stg_bytes;
   stg[1] = (int32_t *)p; p += stg_bytes;
   uint64_t *cand = (uint64_t *)p; p += cand_bytes;
-  uint32_t *hist = (uint32_t *)p; p += hist_bytes;
   SegState *seg = (SegState *)p; p += seg_bytes;
-  unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;
+  uint32_t *hist = (uint32_t *)p; p += hist_bytes;   // zeroed here, then by each level's
+  unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;   // bucket pass
   unsigned char *plan = p;
   st = h2d(plan, img.bytes.data(), img.bytes.size(), s);
-  if (!st) st = cuda_check(cudaMemsetAsync(cursor, 0, cursor_bytes, s), "memset");
+  if (!st) st = cuda_check(cudaMemsetAsync(hist, 0, hist_bytes + cursor_bytes, s), "memset");
   if (st) {
     dev_free(af, block, total, s);
     return st;
@@ -1101,7 +1141,6 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     P.lt = (const LvTree *)(plan + o_lt) + L.lt;
     P.act_seg = d_pre + L.seg;
     P.act_tile = d_pre + L.tile;
-    cudaMemsetAsync(hist, 0, (size_t)L.nseg * kHistBins * 4, s);
     { KScope ks_(kK_level_hist, s); k_level_hist<<<(unsigned)L.ntile, 512, 0, s>>>(P); }
     { KScope ks_(kK_level_bucket, s);
       k_level_bucket<<<(unsigned)ceil_div(L.nseg, 8), 256, 0, s>>>(P, L.nseg); }

@@ -1120,24 +1120,27 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
     if (m[i] > 0 && (!q[i] || !oi[i] || !od[i])) return set_error(BDL_EINVAL, "NULL pointer");
   }
   if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
-  refresh_btrees(F, nf, s);
   Temp tmp(F[0], s);
+  // large batches run in spatial order so that neighbouring threads walk
+  // neighbouring paths; results are written back in input order.  The sorts
+  // need nothing from the forests, so they go first and the device sorts
+  // while the host plans the buffer trees' rebuilds.
+  std::vector<int32_t *> perm(nf, nullptr);
+  for (int i = 0; i < nf; ++i) {
+    if (m[i] < kSortMinQueries) continue;
+    void *scratch = nullptr;
+    if (tmp.get(query_sort_bytes(m[i], F[i]->dim), &scratch) == BDL_OK) {
+      perm[i] = (int32_t *)scratch;
+      launch_query_sort(q[i], m[i], F[i]->dim, (char *)scratch + a256((size_t)m[i] * 4), perm[i], s);
+    }
+  }
+  refresh_btrees(F, nf, s);
   std::vector<ForestView> views(nf);
   std::vector<KnnCall> calls;
   for (int i = 0; i < nf; ++i) {
     if (m[i] == 0) continue;
     views[i] = knn_view(F[i], false, s);
-    // large batches run in spatial order so that neighbouring threads walk
-    // neighbouring paths; results are written back in input order
-    int32_t *perm = nullptr;
-    if (m[i] >= kSortMinQueries) {
-      void *scratch = nullptr;
-      if (tmp.get(query_sort_bytes(m[i], F[i]->dim), &scratch) == BDL_OK) {
-        perm = (int32_t *)scratch;
-        launch_query_sort(q[i], m[i], F[i]->dim, (char *)scratch + a256((size_t)m[i] * 4), perm, s);
-      }
-    }
-    calls.push_back(KnnCall{&views[i], q[i], perm, m[i], oi[i], od[i]});
+    calls.push_back(KnnCall{&views[i], q[i], perm[i], m[i], oi[i], od[i]});
   }
   int st = BDL_OK;
   std::vector<int> dims;
