@@ -264,6 +264,28 @@ def test_erase_batches_that_erase_nothing():
     assert_same_knn(g, o, inputs.uniform_points(300, dim, seed=22), 10)
 
 
+@pytest.mark.parametrize("dim", [2, 3, 4])
+def test_knn_counting_instance(dim):
+    """With visit counting on, k-NN runs its counting instance (a plain walk of
+    the binary nodes instead of the packed records): the rows are the same as
+    the timed instance's and the oracle's, and every query is counted."""
+    g, o = make(dim, 16, 256)
+    n = 40000
+    p = inputs.uniform_points(n, dim, seed=31)
+    g.insert(to_dev(p))
+    o.insert(p)
+    ids = inputs.sample_ids(np.arange(n, dtype=np.int32), 9000, seed=32)
+    assert g.erase(to_dev(ids)) == o.erase(ids)
+    q = inputs.uniform_points(5000, dim, seed=33)
+    gi, gd = assert_same_knn(g, o, q, 7)
+    g.knn_stats(True)
+    si, sd = g.knn(to_dev(q), 7)
+    nodes, points, nq = g.knn_stats()
+    g.knn_stats(False)
+    assert np.array_equal(si.cpu().numpy(), gi) and np.array_equal(sd.cpu().numpy(), gd)
+    assert nq == len(q) and nodes >= len(q) and points >= 7 * len(q)
+
+
 def test_host_buffers_end_to_end():
     """The public API with host (numpy) arrays copies in and out itself."""
     dim = 3
