@@ -13,10 +13,13 @@
 // segment at level t is s = j * 2^t + i (tree j, node i of depth t), and its
 // child's is 2s or 2s + 1.  Per level:
 //   k_sp_minmax  -- min and max of the split coordinate per segment (block-,
-//                   then warp-aggregated atomics);
+//                   then warp-aggregated atomics), for the first level only;
 //   k_sp_scatter -- left records fill the child's range from its start, right
 //                   ones from its end (aggregated atomic cursors); records of
 //                   a tree whose children are leaves go straight to the tree;
+//                   the others also give their child segment's min and max of
+//                   the next level's split coordinate, so that level needs no
+//                   pass of its own;
 //   k_sp_split   -- the node's key and children, the children's bounds, and
 //                   the leaf offsets of trees that end here.
 // Order inside a child is not kept (the sets are what the rule fixes).  Then
@@ -148,13 +151,19 @@ __global__ void k_sp_roots(const SpTree *T, int ntree, int64_t *lo, int32_t *n) 
   }
 }
 
-__global__ void k_sp_level_init(int64_t N, int32_t *mn, int32_t *mx, uint32_t *curL, uint32_t *curR) {
+// Cursors of the N segments of this level; empty bounds for the Nb segments
+// whose min and max are gathered next (by k_sp_minmax or by the scatter).
+__global__ void k_sp_level_init(int64_t N, uint32_t *curL, uint32_t *curR, int64_t Nb, int32_t *mn,
+                                int32_t *mx) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
-  mn[s] = INT32_MAX;
-  mx[s] = INT32_MIN;
-  curL[s] = 0;
-  curR[s] = 0;
+  if (s < N) {
+    curL[s] = 0;
+    curR[s] = 0;
+  }
+  if (s < Nb) {
+    mn[s] = INT32_MAX;
+    mx[s] = INT32_MIN;
+  }
 }
 
 __global__ void __launch_bounds__(kT) k_sp_minmax(const int32_t *stg, const int32_t *seg, int64_t A, int rs,
@@ -208,9 +217,10 @@ __global__ void __launch_bounds__(kT) k_sp_scatter(const int32_t *stg, const int
                                                    int c, int t, const int32_t *mn, const int32_t *mx,
                                                    const int64_t *lo, const int32_t *n, uint32_t *curL,
                                                    uint32_t *curR, const SpTree *T, int32_t *stg_out,
-                                                   int32_t *seg_out) {
+                                                   int32_t *seg_out, int32_t *mn_next, int32_t *mx_next) {
   __shared__ uint32_t s_cnt[2][kT / 32];
   __shared__ uint32_t s_base[2];
+  __shared__ int32_t s_bnd[4][kT / 32];   // per warp: left min, left max, right min, right max
   const int rs = rec_ints(dim);
   const int64_t p0 = (int64_t)blockIdx.x * kT;
   const int64_t p = p0 + threadIdx.x;
@@ -222,25 +232,50 @@ __global__ void __launch_bounds__(kT) k_sp_scatter(const int32_t *stg, const int
   const bool left = act && x <= ((act ? mn[s] + mx[s] : 0) >> 1);
   const bool right = act && !left;
   const unsigned lt_mask = (1u << lane) - 1;
+  // the next level's split coordinate, for the records whose children split on
+  const int cn = (t + 1) % dim;
+  const bool more = act && t + 2 <= T[s >> t].h;
+  const int32_t xn = more ? stg[p * rs + cn] : 0;
   uint32_t rank = 0;
   if (__syncthreads_and(!act || s == s0)) {
     const unsigned bl = __ballot_sync(0xffffffffu, left), br = __ballot_sync(0xffffffffu, right);
+    const int32_t lmn = __reduce_min_sync(0xffffffffu, more && left ? xn : INT32_MAX);
+    const int32_t lmx = __reduce_max_sync(0xffffffffu, more && left ? xn : INT32_MIN);
+    const int32_t rmn = __reduce_min_sync(0xffffffffu, more && right ? xn : INT32_MAX);
+    const int32_t rmx = __reduce_max_sync(0xffffffffu, more && right ? xn : INT32_MIN);
     if (lane == 0) {
       s_cnt[0][warp] = __popc(bl);
       s_cnt[1][warp] = __popc(br);
+      s_bnd[0][warp] = lmn;
+      s_bnd[1][warp] = lmx;
+      s_bnd[2][warp] = rmn;
+      s_bnd[3][warp] = rmx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       uint32_t tl = 0, tr = 0;
+      int32_t a0 = INT32_MAX, a1 = INT32_MIN, a2 = INT32_MAX, a3 = INT32_MIN;
       for (int w = 0; w < kT / 32; ++w) {
         const uint32_t a = s_cnt[0][w], b = s_cnt[1][w];
         s_cnt[0][w] = tl;
         s_cnt[1][w] = tr;
         tl += a;
         tr += b;
+        a0 = min(a0, s_bnd[0][w]);
+        a1 = max(a1, s_bnd[1][w]);
+        a2 = min(a2, s_bnd[2][w]);
+        a3 = max(a3, s_bnd[3][w]);
       }
       s_base[0] = tl ? atomicAdd(&curL[s0], tl) : 0;
       s_base[1] = tr ? atomicAdd(&curR[s0], tr) : 0;
+      if (a0 <= a1) {
+        atomicMin(&mn_next[2 * s0], a0);
+        atomicMax(&mx_next[2 * s0], a1);
+      }
+      if (a2 <= a3) {
+        atomicMin(&mn_next[2 * s0 + 1], a2);
+        atomicMax(&mx_next[2 * s0 + 1], a3);
+      }
     }
     __syncthreads();
     rank = left ? s_base[0] + s_cnt[0][warp] + __popc(bl & lt_mask)
@@ -254,6 +289,14 @@ __global__ void __launch_bounds__(kT) k_sp_scatter(const int32_t *stg, const int
     if (act && lane == leader) base = atomicAdd(left ? &curL[s] : &curR[s], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
     rank = base + __popc(peers & lt_mask);
+    // the group's bounds of the next coordinate (every lane of a group is in
+    // the same tree, so `more` is the same for all of them)
+    const int32_t gmn = __reduce_min_sync(peers, more ? xn : INT32_MAX);
+    const int32_t gmx = __reduce_max_sync(peers, more ? xn : INT32_MIN);
+    if (more && lane == leader) {
+      atomicMin(&mn_next[2 * s + (left ? 0 : 1)], gmn);
+      atomicMax(&mx_next[2 * s + (left ? 0 : 1)], gmx);
+    }
   }
   if (!act) return;
   const int j = s >> t;
@@ -436,7 +479,7 @@ int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt, con
     pack_nodes_entries(trees, dim, pk, pk_pre);
   }
   const size_t b_pk = al256(pk.size() * sizeof(TreeSeg)), b_pkpre = al256(pk_pre.size() * 8);
-  const size_t total = 2 * b_stg + 2 * b_seg + 4 * b_i32 + 2 * (b_i64 + b_i32) + b_tr + b_ga + b_gpre + b_lpre +
+  const size_t total = 2 * b_stg + 2 * b_seg + 6 * b_i32 + 2 * (b_i64 + b_i32) + b_tr + b_ga + b_gpre + b_lpre +
                        b_cur + b_pk + b_pkpre;
   void *block = nullptr;
   int st = dev_alloc(af, &block, total, s);
@@ -452,7 +495,11 @@ int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt, con
   stg[1] = (int32_t *)take(b_stg);
   seg[0] = (int32_t *)take(b_seg);
   seg[1] = (int32_t *)take(b_seg);
-  int32_t *mn = (int32_t *)take(b_i32), *mx = (int32_t *)take(b_i32);
+  int32_t *mn[2], *mx[2];   // split-coordinate bounds of this level's and the next level's segments
+  mn[0] = (int32_t *)take(b_i32);
+  mx[0] = (int32_t *)take(b_i32);
+  mn[1] = (int32_t *)take(b_i32);
+  mx[1] = (int32_t *)take(b_i32);
   uint32_t *curL = (uint32_t *)take(b_i32), *curR = (uint32_t *)take(b_i32);
   int64_t *lo[2];
   int32_t *nn[2];
@@ -493,23 +540,26 @@ int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt, con
     const int64_t A = tr[nact[t] - 1].toff + tr[nact[t] - 1].size;   // records still splitting
     const int c = t % dim;
     const int cur = t & 1, nxt = cur ^ 1;
-    {
+    if (t == 0) {   // the first level's bounds by a pass of their own; later ones come from the scatter
       KScope ks_(kK_sp_minmax, s);
-      k_sp_level_init<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(N, mn, mx, curL, curR);
+      k_sp_level_init<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(0, curL, curR, N, mn[cur], mx[cur]);
+      k_sp_minmax<<<(unsigned)cdiv(A, kT), kT, 0, s>>>(stg[cur], seg[cur], A, rs, c, mn[cur], mx[cur]);
     }
+    const int64_t Nn = t + 1 < hmax ? (int64_t)nact[t + 1] << (t + 1) : 0;
     {
       KScope ks_(kK_sp_minmax, s);
-      k_sp_minmax<<<(unsigned)cdiv(A, kT), kT, 0, s>>>(stg[cur], seg[cur], A, rs, c, mn, mx);
+      k_sp_level_init<<<(unsigned)cdiv(std::max(N, Nn), 256), 256, 0, s>>>(N, curL, curR, Nn, mn[nxt], mx[nxt]);
     }
     {
       KScope ks_(kK_sp_scatter, s);
-      k_sp_scatter<<<(unsigned)cdiv(A, kT), kT, 0, s>>>(stg[cur], seg[cur], A, dim, c, t, mn, mx, lo[cur], nn[cur],
-                                                        curL, curR, d_tr, stg[nxt], seg[nxt]);
+      k_sp_scatter<<<(unsigned)cdiv(A, kT), kT, 0, s>>>(stg[cur], seg[cur], A, dim, c, t, mn[cur], mx[cur], lo[cur],
+                                                        nn[cur], curL, curR, d_tr, stg[nxt], seg[nxt], mn[nxt],
+                                                        mx[nxt]);
     }
     {
       KScope ks_(kK_sp_split, s);
-      k_sp_split<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(t, N, mn, mx, lo[cur], nn[cur], curL, curR, d_tr, lo[nxt],
-                                                       nn[nxt]);
+      k_sp_split<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(t, N, mn[cur], mx[cur], lo[cur], nn[cur], curL, curR, d_tr,
+                                                       lo[nxt], nn[nxt]);
     }
   }
   // ---- boxes, live counts, packed records ----
