@@ -294,6 +294,7 @@ enum : unsigned long long {
   kErrStack = 4,       // traversal stack full
   kErrPartition = 8,   // partition destination outside its segment
   kErrGather = 16,     // gather destination outside its tree
+  kErrLiveCount = 32,  // a packed record's live count differs from its node's (debug check)
 };
 
 // ---------------------------------------------------------------------------
@@ -428,6 +429,7 @@ struct EraseCall {
   int64_t n;
   uint64_t seed;           // the forest's bloom hash seed
   const int64_t *n_dev;    // if set: the list's length on the device (<= n)
+  int records;             // 1: also keep the packed k-NN records' live counts current
 };
 struct EraseJob {          // device form of an EraseCall
   const TreeView *trees;
@@ -438,6 +440,7 @@ struct EraseJob {          // device form of an EraseCall
   int64_t n;
   uint64_t seed;
   const int64_t *n_dev;
+  int32_t records;
 };
 size_t erase_table_bytes(const std::vector<EraseCall> &calls);
 // Bloom probe, descent and tombstone for every call in one launch; the job
@@ -482,6 +485,7 @@ struct TreeSeg {           // one tree: bloom builds, record packing, live refre
   int32_t *pk;
   uint64_t seed;           // bloom hash seed (bloom builds)
   const int64_t *gate;     // bloom builds: skipped when *gate == 0 (nullptr: always built)
+  unsigned long long *err; // live refreshes: compare and flag instead of write (debug check)
 };
 struct BufSeg {            // one forest's buffer and roots
   int32_t *buf;

@@ -20,6 +20,9 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // filter (one 32-byte sector); on a hit descend by the composite key to the
 // unique leaf, find the id, tombstone it and decrement the live counts along
 // the path.  A live id that no tree holds is in the buffer.
+// REC: some job keeps its packed k-NN records' live counts (the instance
+// without that code is used when none does)
+template <bool REC>
 __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, int njobs) {
   // every warp belongs to one job (one forest's erase list): the per-tree
   // loop below is warp-synchronous
@@ -61,6 +64,7 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
   for (int ti = 0; ti < F.ntrees; ++ti) {
     const TreeView &T = F.trees[ti];
     bool found = false;
+    int64_t leaf_at = 0;   // the leaf's index among the 2^h leaves
     if (pending) {
       if ((maybe_mask >> ti) & 1) {
         int v = 0, depth = 0;
@@ -76,6 +80,7 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
           if (v < 0 || v >= T.nnodes || depth > T.h) { ok = false; break; }
         }
         int leaf = -1 - nd.l;
+        leaf_at = leaf;
         int a = 0, z = 0;
         if (ok && leaf < ((int64_t)1 << T.h)) {
           a = T.leaf_off[leaf];
@@ -97,10 +102,24 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
     }
     unsigned fm = __ballot_sync(0xffffffffu, found);
     if (found) {
+      // live counts on the path: the nodes', and (when the job keeps them)
+      // the packed k-NN record entries' for the nodes that are entries
+      // (depth d >= 1 with h - d even: entry (i & 3) of the record two levels
+      // up, or (i & 1) of the root's record for d = 1)
+      const int rec = packed_node_ints(F.dim);
       for (int d = 0; d <= T.h; ++d) {
         int v = path[d];
         unsigned peers = __match_any_sync(fm, v);
-        if (lane == __ffs(peers) - 1) atomicSub(&T.live[v], __popc(peers));
+        if (lane == __ffs(peers) - 1) {
+          const int cnt = __popc(peers);
+          atomicSub(&T.live[v], cnt);
+          if (REC && F.records && d >= 1 && ((T.h - d) & 1) == 0) {
+            const int e = d == 1 ? 1 : 2;
+            const int64_t at = leaf_at >> (T.h - d);   // the node's index at depth d
+            const int64_t r = packed_slot(T.h, d - e, at >> e);
+            atomicSub(&T.pk[r * rec + 4 + (int)(at & ((1 << e) - 1))], cnt);
+          }
+        }
       }
       pending = false;
     }
@@ -226,15 +245,23 @@ int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
     J.seed = c.seed;
     J.n = c.fv->ntrees ? c.n : 0;
     J.n_dev = c.n_dev;
+    J.records = c.records;
     for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
     warp[j + 1] = warp[j] + (J.n + 31) / 32;
   }
   if (warp[n] == 0) return BDL_OK;
   int st = h2d(table, img.data(), img.size(), s);
   if (st) return st;
+  bool rec = false;
+  for (const auto &c : calls) rec = rec || c.records;
   KScope ks_(kK_erase_locate, s);
-  k_erase_locate<<<(unsigned)cdiv(warp[n] * 32, 128), 128, 0, s>>>(
-      (const EraseJob *)table, (const int64_t *)((char *)table + n * sizeof(EraseJob)), (int)n);
+  const unsigned grid = (unsigned)cdiv(warp[n] * 32, 128);
+  const EraseJob *djobs = (const EraseJob *)table;
+  const int64_t *jw = (const int64_t *)((char *)table + n * sizeof(EraseJob));
+  if (rec)
+    k_erase_locate<true><<<grid, 128, 0, s>>>(djobs, jw, (int)n);
+  else
+    k_erase_locate<false><<<grid, 128, 0, s>>>(djobs, jw, (int)n);
   return cuda_check(cudaGetLastError(), "erase kernel");
 }
 
@@ -364,7 +391,9 @@ __global__ void k_bloom_build_many(const TreeSeg *segs, const int64_t *pre, int 
 }
 
 // One thread per packed k-NN record of many trees (pre[j] .. pre[j+1]-1 are
-// tree j's records in level order): copy its entries' refreshed live counts.
+// tree j's records in level order): its entries' live counts from the nodes'.
+// With segs[j].err set, compare instead of copy and flag a difference (the
+// erase keeps both up to date; this is the debug check of that).
 __global__ void k_pack_lives_many(const TreeSeg *segs, const int64_t *pre, int nseg) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= pre[nseg]) return;
@@ -381,7 +410,13 @@ __global__ void k_pack_lives_many(const TreeSeg *segs, const int64_t *pre, int n
     lv.z = g.live[veb_slot(g.h + 1, t + st, (i << st) + 2)];
     lv.w = g.live[veb_slot(g.h + 1, t + st, (i << st) + 3)];
   }
-  *reinterpret_cast<int4 *>(g.pk + packed_slot(g.h, t, i) * packed_node_ints(g.dim) + 4) = lv;
+  int4 *dst = reinterpret_cast<int4 *>(g.pk + packed_slot(g.h, t, i) * packed_node_ints(g.dim) + 4);
+  if (!g.err) {
+    *dst = lv;
+  } else {
+    const int4 have = *dst;
+    if (have.x != lv.x || have.y != lv.y || have.z != lv.z || have.w != lv.w) atomicOr(g.err, kErrLiveCount);
+  }
 }
 
 // One CTA per forest: keep its buffer ids that are still alive, in order;

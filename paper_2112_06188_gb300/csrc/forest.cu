@@ -936,6 +936,14 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   //    launch); a large batch descends in spatial order
   std::vector<ForestView> views(act.size());
   std::vector<EraseCall> calls;
+  // The packed k-NN records' live counts: a small batch (under 1/128 of the
+  // forest) updates them on its descent paths, a larger one has every record
+  // refreshed from the nodes afterwards, whichever touches less.
+  std::vector<int> incremental(act.size());
+  for (size_t a = 0; a < act.size(); ++a) {
+    const bdl_forest *f = F[mk_forest[act[a]]];
+    incremental[a] = mk[act[a]].n * 128 < f->live;
+  }
   for (size_t a = 0; a < act.size(); ++a) {
     const int j = act[a];
     bdl_forest *f = F[mk_forest[j]];
@@ -950,7 +958,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
         order = (const int32_t *)sorted;
       }
     }
-    calls.push_back(EraseCall{&views[a], order, nj, f->cfg.hash_seed, ne_dev + j});
+    calls.push_back(EraseCall{&views[a], order, nj, f->cfg.hash_seed, ne_dev + j, incremental[a]});
   }
   {
     void *et = nullptr;
@@ -958,7 +966,8 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     if (!st) st = launch_erase_jobs(calls, et, s);
     if (st) return st;
   }
-  // 4. refresh the k-NN records' live counts; compact the buffers; counts back
+  // 4. the records' live counts (refreshed, or checked in debug runs when the
+  //    descent kept them); compact the buffers; counts back
   std::vector<TreeSeg> lives;
   std::vector<BufSeg> bufs;
   void *outs = nullptr;
@@ -976,6 +985,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       Tree *t = f->trees[i];
       if (!t) continue;
       b.roots[b.ntrees++] = t->live_nodes;
+      if (incremental[a] && !f->debug_check) continue;
       TreeSeg g;
       memset(&g, 0, sizeof(g));
       g.dim = f->dim;
@@ -983,6 +993,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       g.node = t->node;
       g.live = t->live_nodes;
       g.pk = t->pk;
+      g.err = incremental[a] ? f->err : nullptr;
       lives.push_back(g);
     }
     bufs.push_back(b);

@@ -286,6 +286,35 @@ def test_knn_counting_instance(dim):
     assert nq == len(q) and nodes >= len(q) and points >= 7 * len(q)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_small_erase_batches(dim):
+    """Erase batches under 1/128 of the forest keep the packed k-NN records'
+    live counts on their descent paths (debug runs compare every record with
+    its nodes after each erase); results stay the oracle's."""
+    g, o = make(dim, 8, 128)
+    n = 60000
+    p = inputs.uniform_points(n, dim, seed=41)
+    g.insert(to_dev(p))
+    o.insert(p)
+    live = np.arange(n, dtype=np.int32)
+    q = inputs.uniform_points(2000, dim, seed=42)
+    for step in range(12):
+        ids = inputs.sample_ids(live, 60 + 17 * step, seed=43 + step)
+        ids = np.concatenate([ids, ids[:5], np.array([n + 7, -2], np.int32)])   # repeats, dead ids
+        assert g.erase(to_dev(ids)) == o.erase(ids)
+        live = np.setdiff1d(live, ids)
+        if step % 4 == 3:
+            assert_same_forest(g, o)
+            assert_same_knn(g, o, q, 9)
+    ins = inputs.uniform_points(3000, dim, seed=44)     # new trees, then more small erases
+    g.insert(to_dev(ins))
+    o.insert(ins)
+    ids = inputs.sample_ids(np.arange(n + 3000, dtype=np.int32), 300, seed=45)
+    assert g.erase(to_dev(ids)) == o.erase(ids)
+    assert_same_forest(g, o)
+    assert_same_knn(g, o, q, 9)
+
+
 def test_host_buffers_end_to_end():
     """The public API with host (numpy) arrays copies in and out itself."""
     dim = 3
