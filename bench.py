@@ -295,38 +295,67 @@ def run_ours(a, rank, world, dist):
     nodes, points, nq = f.knn_stats()
     f.knn_stats(False)
 
-    # end to end through the public API with host buffers, copies timed
+    # end to end through the public API from pinned host buffers: every step's
+    # inputs are copied in and its k-NN rows copied out inside the timed
+    # region.  Steps are pipelined the way a server would run them: the next
+    # step's inputs come in and the previous step's rows go out on copy
+    # streams while a step computes (two device buffer sets, events between).
     e2e_ms = []
     h2d = d2h = 0
-    for i in range(a.warmup + a.steps, a.warmup + a.steps + a.e2e_steps):
-        ins, era, q = W.steps[i]
+    K = a.e2e_steps
+    if K > 0:
         import torch as _t
-        ins_h = _t.from_numpy(ins).pin_memory()
-        era_h = _t.from_numpy(era).pin_memory()
-        q_h = _t.from_numpy(q).pin_memory()
-        oi_h = _t.empty((a.queries, a.k), dtype=_t.int32).pin_memory()
-        od_h = _t.empty((a.queries, a.k), dtype=_t.int64).pin_memory()
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        stream.synchronize()
+        idx = list(range(a.warmup + a.steps, a.warmup + a.steps + K))
+        hin = [tuple(_t.from_numpy(x).pin_memory() for x in W.steps[i]) for i in idx]
+        hout = [(_t.empty((a.queries, a.k), dtype=_t.int32).pin_memory(),
+                 _t.empty((a.queries, a.k), dtype=_t.int64).pin_memory()) for _ in range(2)]
+        din = [tuple(_t.empty_like(x, device=dev) for x in hin[0]) for _ in range(2)]
+        dout = [(_t.empty((a.queries, a.k), dtype=_t.int32, device=dev),
+                 _t.empty((a.queries, a.k), dtype=_t.int64, device=dev)) for _ in range(2)]
+        h2s, d2s = _t.cuda.Stream(dev), _t.cuda.Stream(dev)
+        ev_in = [_t.cuda.Event() for _ in range(2)]     # inputs of buffer set b arrived
+        ev_used = [_t.cuda.Event() for _ in range(2)]   # the step on set b has finished its k-NN
+        ev_out = [_t.cuda.Event() for _ in range(2)]    # rows of set b copied out
+
+        def load(j):
+            b = j & 1
+            h2s.wait_event(ev_used[b])                  # set b's previous step is done with it
+            with _t.cuda.stream(h2s):
+                for xd, xh in zip(din[b], hin[j]):
+                    xd.copy_(xh, non_blocking=True)
+            ev_in[b].record(h2s)
+
+        _t.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        f.insert(ins_h)
-        f.erase(era_h)
-        with torch.cuda.stream(stream):
-            gi, gd = f.knn(q_h.to(dev, non_blocking=True), a.k)
-            oi_h.copy_(gi, non_blocking=True)
-            od_h.copy_(gd, non_blocking=True)
+        load(0)
+        for j in range(K):
+            b = j & 1
+            if j + 1 < K:
+                load(j + 1)
+            stream.wait_event(ev_in[b])
+            with _t.cuda.stream(stream):
+                flush.zero_()
+            f.insert(din[b][0])
+            f.erase(din[b][1])
+            stream.wait_event(ev_out[b])                # set b's previous rows are out
+            f.knn(din[b][2], a.k, out=dout[b])
+            ev_used[b].record(stream)
+            d2s.wait_event(ev_used[b])
+            with _t.cuda.stream(d2s):
+                hout[b][0].copy_(dout[b][0], non_blocking=True)
+                hout[b][1].copy_(dout[b][1], non_blocking=True)
+            ev_out[b].record(d2s)
+        d2s.synchronize()
         stream.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        h2d = ins.nbytes + era.nbytes + q.nbytes
-        d2h = oi_h.numel() * 4 + od_h.numel() * 8   # the k-NN rows (insert ids are known on the host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3 / K)
+        h2d = sum(x.numel() * x.element_size() for x in hin[0])
+        d2h = hout[0][0].numel() * 4 + hout[0][1].numel() * 8   # the k-NN rows (insert ids are known)
     f.close()
 
     ops_per_step = 2 * a.batch + a.queries
     res = {
         "ms": ms, "launches": launches, "prof": prof, "clocks": clk, "wall": wall,
         "knn_stats": (nodes, points, nq), "e2e_ms": statistics.mean(e2e_ms) if e2e_ms else None,
-        "e2e_ms_all": [round(x, 3) for x in e2e_ms],
         "h2d": h2d, "d2h": d2h, "ops_per_step": ops_per_step, "autotune": autotune,
     }
     return res
@@ -1063,7 +1092,8 @@ def main():
     if res["e2e_ms"]:
         out["e2e"] = {"value": round(ops / (res["e2e_ms"] * 1e-3), 1), "unit": "ops/s",
                       "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"],
-                      "ms_per_step": round(res["e2e_ms"], 3), "ms_steps": res["e2e_ms_all"]}
+                      "ms_per_step": round(res["e2e_ms"], 3), "steps": a.e2e_steps,
+                      "pipelined": "next inputs in and previous rows out on copy streams during each step"}
     if world == 1 and not a.no_cpu_baseline:
         times, ops_c, sample = oracle_sample(a, 2)
         v = ops_c / (sum(times) / len(times))
