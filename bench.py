@@ -436,7 +436,7 @@ def run_forests(a, rank, world, dist):
         T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
         with torch.cuda.stream(stream):
             tinit = [T(p) for p in W.initial]
-            tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in steps[:2]]
+            tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in steps[:4]]
             best, ms_by_leaf = tune_leaf_size_forests(W.dims, tinit, tsteps, a.k, device=dev, stream=stream)
         del tinit, tsteps
         a.leaf = best

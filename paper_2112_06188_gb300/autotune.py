@@ -7,7 +7,10 @@ The k-NN answers do not depend on it (they are the exact k nearest by
 workload by measurement: for every candidate, build a forest on the
 workload's own initial points and time a few steps of it (one insert batch,
 one erase batch, one k-NN batch) with CUDA events; the fastest mean step
-wins.  Every step runs in the CUDA library; this module only times calls.
+wins, except that the default leaf size is kept unless another candidate is
+faster by more than TIE (step times of neighbouring leaf sizes are often
+within the noise of a few steps).  Every step runs in the CUDA library; this
+module only times calls.
 """
 import numpy as np
 import torch
@@ -16,6 +19,16 @@ from . import inputs
 from .forest import Forest
 
 CANDIDATES = (8, 16, 32)
+DEFAULT = 16
+TIE = 0.01
+
+
+def choose(ms):
+    """The leaf size to use given {candidate: mean step ms}."""
+    best = min(ms, key=ms.get)
+    if DEFAULT in ms and ms[best] > ms[DEFAULT] * (1.0 - TIE):
+        return DEFAULT
+    return best
 
 
 def time_steps(dim, leaf, initial, steps, k, device=None, stream=None, split="object"):
@@ -51,8 +64,7 @@ def tune_leaf_size(dim, initial, steps, k, candidates=CANDIDATES, device=None, s
     if len(steps) < 2:
         raise ValueError("need a warm-up step and at least one timed step")
     ms = {L: time_steps(dim, L, initial, steps, k, device, stream, split) for L in candidates}
-    best = min(ms, key=ms.get)
-    return best, ms
+    return choose(ms), ms
 
 
 def synthetic_steps(dim, n0, batch, queries, nsteps, seed, device=None):
@@ -114,4 +126,4 @@ def tune_leaf_size_forests(dims, initial, steps, k, candidates=CANDIDATES, devic
     if len(steps) < 2:
         raise ValueError("need a warm-up step and at least one timed step")
     ms = {L: time_forests_step(dims, L, initial, steps, k, device, stream, split) for L in candidates}
-    return min(ms, key=ms.get), ms
+    return choose(ms), ms

@@ -24,8 +24,7 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // without that code is used when none does)
 template <bool REC>
 __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, int njobs) {
-  // every warp belongs to one job (one forest's erase list): the per-tree
-  // loop below is warp-synchronous
+  // every warp belongs to one job (one forest's erase list)
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= job_warp[njobs]) return;
   int lo = 0, hi = njobs - 1;
@@ -61,67 +60,77 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
       maybe_mask |= (uint64_t)maybe << ti;
     }
   }
-  for (int ti = 0; ti < F.ntrees; ++ti) {
+  // Each lane walks its own maybe-trees, largest first, until it finds its
+  // id: the lanes of a warp descend different trees at the same time (an id
+  // is in one tree; the warp's ids are spread over several).
+  bool found = false;
+  int fti = 0;            // the tree that held the id
+  int64_t leaf_at = 0;    // its leaf's index among that tree's 2^h leaves
+  uint64_t mm = pending ? maybe_mask : 0;
+  while (mm) {
+    const int ti = __ffsll((long long)mm) - 1;
+    mm &= mm - 1;
     const TreeView &T = F.trees[ti];
-    bool found = false;
-    int64_t leaf_at = 0;   // the leaf's index among the 2^h leaves
-    if (pending) {
-      if ((maybe_mask >> ti) & 1) {
-        int v = 0, depth = 0;
-        Node nd;
-        bool ok = true;
-        while (true) {
-          path[depth] = v;
-          nd = T.node[v];
-          if (nd.l < 0) break;
-          uint64_t key = comp_key(xq[depth % F.dim], id);
-          v = key > nd.key ? nd.r : nd.l;
-          depth++;
-          if (v < 0 || v >= T.nnodes || depth > T.h) { ok = false; break; }
-        }
-        int leaf = -1 - nd.l;
-        leaf_at = leaf;
-        int a = 0, z = 0;
-        if (ok && leaf < ((int64_t)1 << T.h)) {
-          a = T.leaf_off[leaf];
-          z = T.leaf_off[leaf + 1];
-          if (a < 0 || z > T.size || a > z) { a = z = 0; atomicOr(F.err, kErrLeaf); }
-        } else {
-          atomicOr(F.err, kErrChild);
-        }
-        const int rs = rec_ints(F.dim);
-        for (int j = a; j < z; ++j) {
-          int32_t *slot = T.pts + (int64_t)j * rs + F.dim;
-          if (*slot == id) {
-            *slot = (int32_t)((uint32_t)id | kTomb);
-            found = true;
-            break;
-          }
-        }
+    int v = 0, depth = 0;
+    Node nd;
+    bool ok = true;
+    while (true) {
+      path[depth] = v;
+      nd = T.node[v];
+      if (nd.l < 0) break;
+      uint64_t key = comp_key(xq[depth % F.dim], id);
+      v = key > nd.key ? nd.r : nd.l;
+      depth++;
+      if (v < 0 || v >= T.nnodes || depth > T.h) { ok = false; break; }
+    }
+    const int leaf = -1 - nd.l;
+    int a = 0, z = 0;
+    if (ok && leaf < ((int64_t)1 << T.h)) {
+      a = T.leaf_off[leaf];
+      z = T.leaf_off[leaf + 1];
+      if (a < 0 || z > T.size || a > z) { a = z = 0; atomicOr(F.err, kErrLeaf); }
+    } else {
+      atomicOr(F.err, kErrChild);
+    }
+    const int rs = rec_ints(F.dim);
+    for (int j = a; j < z; ++j) {
+      int32_t *slot = T.pts + (int64_t)j * rs + F.dim;
+      if (*slot == id) {
+        *slot = (int32_t)((uint32_t)id | kTomb);
+        found = true;
+        break;
       }
     }
-    unsigned fm = __ballot_sync(0xffffffffu, found);
     if (found) {
-      // live counts on the path: the nodes', and (when the job keeps them)
-      // the packed k-NN record entries' for the nodes that are entries
-      // (depth d >= 1 with h - d even: entry (i & 3) of the record two levels
-      // up, or (i & 1) of the root's record for d = 1)
-      const int rec = packed_node_ints(F.dim);
-      for (int d = 0; d <= T.h; ++d) {
-        int v = path[d];
-        unsigned peers = __match_any_sync(fm, v);
-        if (lane == __ffs(peers) - 1) {
-          const int cnt = __popc(peers);
-          atomicSub(&T.live[v], cnt);
-          if (REC && F.records && d >= 1 && ((T.h - d) & 1) == 0) {
-            const int e = d == 1 ? 1 : 2;
-            const int64_t at = leaf_at >> (T.h - d);   // the node's index at depth d
-            const int64_t r = packed_slot(T.h, d - e, at >> e);
-            atomicSub(&T.pk[r * rec + 4 + (int)(at & ((1 << e) - 1))], cnt);
-          }
-        }
+      fti = ti;
+      leaf_at = leaf;
+      break;
+    }
+  }
+  // live counts on the path: the nodes', and (when the job keeps them) the
+  // packed k-NN record entries' for the nodes that are entries (depth d >= 1
+  // with h - d even: entry (i & 3) of the record two levels up, or (i & 1) of
+  // the root's record for d = 1); lanes at the same node of the same tree add
+  // up their counts first
+  const int fh = found ? F.trees[fti].h : -1;
+  const int maxh = __reduce_max_sync(0xffffffffu, fh);
+  const int rec = packed_node_ints(F.dim);
+  for (int d = 0; d <= maxh; ++d) {
+    const bool act = d <= fh;
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    if (!act) continue;
+    const int v = path[d];
+    const unsigned peers = __match_any_sync(am, ((unsigned long long)fti << 32) | (uint32_t)v);
+    if (lane == __ffs(peers) - 1) {
+      const TreeView &T = F.trees[fti];
+      const int cnt = __popc(peers);
+      atomicSub(&T.live[v], cnt);
+      if (REC && F.records && d >= 1 && ((T.h - d) & 1) == 0) {
+        const int e = d == 1 ? 1 : 2;
+        const int64_t at = leaf_at >> (T.h - d);   // the node's index at depth d
+        const int64_t r = packed_slot(T.h, d - e, at >> e);
+        atomicSub(&T.pk[r * rec + 4 + (int)(at & ((1 << e) - 1))], cnt);
       }
-      pending = false;
     }
   }
 }
