@@ -325,7 +325,9 @@ int bdl_bloom_export(const bdl_forest *f, int level, uint32_t *words_host, bdl_s
 /* Totals over every bdl_knn call of this forest since the last reset when
  * counting is on: out[0] = tree nodes visited, out[1] = leaf points examined,
  * out[2] = queries.  bdl_knn_stats(f, 1/0, NULL) switches counting on/off and
- * resets; counting adds atomics and is meant for measurement runs only. */
+ * resets.  While counting is on, k-NN runs a counting instance of the kernel
+ * (the same rows, from a plain one-lane walk of the binary nodes, with
+ * atomics): meant for measurement runs only. */
 int bdl_knn_stats(bdl_forest *f, int enable, int64_t *out_host);
 
 /* Number of kernels this library has launched in the process. */
