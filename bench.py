@@ -850,7 +850,8 @@ def run_sweep(a):
     stream = torch.cuda.Stream(dev)
     n = 10_000_000
     sets = {"2-D clusters": (2, inputs.gaussian_clusters(n, 2, seed=21)),
-            "7-D uniform": (7, inputs.uniform_points(n, 7, seed=22))}
+            "7-D uniform": (7, inputs.uniform_points(n, 7, seed=22)),
+            "7-D clusters": (7, inputs.gaussian_clusters(n, 7, seed=23))}
 
     def timed(fn):
         a_ = torch.cuda.Event(enable_timing=True)
@@ -900,7 +901,7 @@ def run_sweep(a):
     return {"metric": METRIC, "value": best, "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "sweeps on 10M points (2-D clusters, 7-D uniform): insert and erase "
+            "config": {"workload": "sweeps on 10M points (2-D clusters, 7-D uniform, 7-D clusters): insert and erase "
                                    "throughput vs batch size, k-NN graph throughput vs k after 5% insert "
                                    "batches", "split": a.split, "leaf_size": 16, "buffer_size": 1024,
                        "batches": list(SWEEP_BATCHES), "ks": list(SWEEP_KS)},
