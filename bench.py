@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--k", type=int, default=None, help="default 10 (forest10m), 8 (forests)")
     ap.add_argument("--dim", type=int, default=3)
     ap.add_argument("--leaf", default="auto",
-                    help="leaf size, or 'auto': autotuned in {8, 16, 32} on this workload before timing")
+                    help="leaf size, or 'auto': autotuned in {8, 12, 16, 24, 32} on this workload before timing")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end steps after the timed ones (default: as many as --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,7 +221,7 @@ def run_ours(a, rank, world, dist):
         from paper_2112_06188_gb300.autotune import tune_leaf_size
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:3]]
+            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:5]]
             best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream,
                                               split=a.split)
         del tsteps

@@ -18,7 +18,7 @@ import torch
 from . import inputs
 from .forest import Forest
 
-CANDIDATES = (8, 16, 32)
+CANDIDATES = (8, 12, 16, 24, 32)
 DEFAULT = 16
 TIE = 0.01
 
