@@ -908,9 +908,10 @@ def run_sweep(a):
             "sweep": out, "clocks": clk}
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, leaf):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
-    when the summary is missing or the kernel source changed since the capture."""
+    when the summary is missing, was captured at another leaf size, or the
+    kernel source changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "%s_3d_10M.md" % kernel)
     try:
@@ -918,7 +919,10 @@ def recorded_traffic(kernel):
     except OSError:
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines()
-                  if line.startswith(("kernel_source:", "source_sha256_16:", "dram_bytes_per_launch:")))
+                  if line.startswith(("kernel_source:", "source_sha256_16:", "dram_bytes_per_launch:",
+                                      "leaf_size:")))
+    if fields.get("leaf_size", "").strip() != str(leaf):
+        return None
     try:
         src = open(os.path.join(ROOT, fields["kernel_source"].strip()), "rb").read()
     except (KeyError, OSError):
@@ -949,7 +953,7 @@ def roofline(a, res, peaks):
         return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(name) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
+    traffic = recorded_traffic(name, a.leaf) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "when" in peaks else "fallback",
