@@ -221,7 +221,7 @@ def run_ours(a, rank, world, dist):
         from paper_2112_06188_gb300.autotune import tune_leaf_size
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:5]]
+            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:9]]
             best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream,
                                               split=a.split)
         del tsteps
