@@ -29,6 +29,13 @@
  *  - Device memory of the forest comes from a CUDA stream-ordered memory pool
  *    owned by the library (one per device), optionally capped per forest by
  *    bdl_config.hbm_budget_bytes.
+ *  - Kernels check their indexes: one that finds an index outside its buffers
+ *    skips the access and sets a bit in the forest's device error word.  With
+ *    the environment variable BDL_DEBUG_CHECK=1 (read at bdl_create) every call
+ *    waits for its kernels and returns BDL_EINTERNAL when a bit is set (1 child
+ *    slot, 2 leaf range, 4 traversal stack, 8 partition, 16 gather, 32 a packed
+ *    k-NN record's live count differs from its node's), with the bits in
+ *    bdl_last_error().
  */
 #ifndef BDL_H
 #define BDL_H
