@@ -1,6 +1,6 @@
 // Host-side check of the library's layout arithmetic (bdl_internal.cuh):
-// the binary vEB slots, and the packed k-NN records' level order, slots and
-// entries.  Prints the number of violations; exit status 0 when there are none.
+// the binary vEB slots, the segments of a level, the tree height, and the
+// packed k-NN records' level order, slots and entries.  Prints the number of violations; exit status 0 when there are none.
 #include <cstdio>
 #include <vector>
 
@@ -25,6 +25,36 @@ int main() {
         else seen[v] = 1;
       }
   }
+  // segments of a tree over s points (reading G3: the left child of a
+  // segment of m points holds ceil(m / 2) of them): seg_range and seg_of agree,
+  // segments tile [0, s), and children split their parent that way
+  for (int64_t sz : {1, 2, 3, 7, 16, 17, 100, 1000, 4097}) {
+    for (int t = 0; t <= 8; ++t) {
+      int64_t next = 0;
+      for (int64_t i = 0; i < ((int64_t)1 << t); ++i) {
+        int64_t st, m;
+        seg_range(sz, t, i, st, m);
+        if (st != next || m < 0) ++bad;
+        next = st + m;
+        int64_t l0, lm, r0, rm;
+        seg_range(sz, t + 1, 2 * i, l0, lm);
+        seg_range(sz, t + 1, 2 * i + 1, r0, rm);
+        if (l0 != st || lm != (m + 1) / 2 || r0 != st + lm || rm != m - lm) ++bad;
+        for (int64_t p = st; p < st + m; ++p) {
+          int64_t a2, m2;
+          if (seg_of(sz, t, p, a2, m2) != i || a2 != st || m2 != m) ++bad;
+        }
+      }
+      if (next != sz) ++bad;
+    }
+  }
+  // split levels h = ceil(log2(ceil(s / L)))
+  for (int64_t sz = 1; sz <= 5000; sz += 37)
+    for (int L : {2, 8, 16, 24, 32}) {
+      const int h = tree_height(sz, L);
+      const int64_t leaves = (sz + L - 1) / L;
+      if (((int64_t)1 << h) < leaves || (h > 0 && ((int64_t)1 << (h - 1)) >= leaves)) ++bad;
+    }
   // packed records of a tree with h internal levels
   for (int h = 0; h <= 20; ++h) {
     const int64_t n = packed_nrec(h);

@@ -1,7 +1,8 @@
 """The library's layout arithmetic, compiled from its own header and run on
 the host: the vEB slot function against the paper's worked example and as a
-bijection, and the packed k-NN record numbering (every record once, entries
-that are records or leaves two levels down)."""
+bijection, the segments of a level (left child ceil(m/2), reading G3), the
+tree height, and the packed k-NN record numbering (every record once,
+entries that are records or leaves two levels down)."""
 import os
 import shutil
 import subprocess
