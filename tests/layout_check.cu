@@ -1,6 +1,7 @@
 // Host-side check of the library's layout arithmetic (bdl_internal.cuh):
-// the binary vEB slots, the segments of a level, the tree height, and the
-// packed k-NN records' level order, slots and entries.  Prints the number of violations; exit status 0 when there are none.
+// the binary vEB slots, the segments of a level, the tree height, the bloom
+// hash's SplitMix64 mixer, and the packed k-NN records' level order, slots
+// and entries.  Prints the number of violations; exit status 0 when there are none.
 #include <cstdio>
 #include <vector>
 
@@ -55,6 +56,8 @@ int main() {
       const int64_t leaves = (sz + L - 1) / L;
       if (((int64_t)1 << h) < leaves || (h > 0 && ((int64_t)1 << (h - 1)) >= leaves)) ++bad;
     }
+  // the bloom hash's mixer: SplitMix64's published first output for seed 0
+  if (splitmix64(0) != 0xe220a8397b1dcdafull) ++bad;
   // packed records of a tree with h internal levels
   for (int h = 0; h <= 20; ++h) {
     const int64_t n = packed_nrec(h);
