@@ -192,6 +192,23 @@ def max_over_ranks(ms, dist, device):
     return dict(zip(PHASES, tt.tolist()))
 
 
+def rank0_choice(value, dist, device):
+    """Rank 0's integer `value` on every rank (an autotuned parameter, so that
+    all ranks do the same work)."""
+    import torch
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    dist.broadcast(t, 0)
+    return int(t.item())
+
+
+def slowest(value, dist, device):
+    """The maximum of a per-rank time over all ranks."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def job_throughput(ops_per_step_per_rank, world, ms_step):
     """Whole-job rate: every rank's operations over the slowest rank's step time."""
     return ops_per_step_per_rank * world / (ms_step * 1e-3)
@@ -225,6 +242,8 @@ def run_ours(a, rank, world, dist):
             best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream,
                                               split=a.split)
         del tsteps
+        if dist:
+            best = rank0_choice(best, dist, dev)
         a.leaf = best
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
                     "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
@@ -348,6 +367,8 @@ def run_ours(a, rank, world, dist):
         d2s.synchronize()
         stream.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3 / K)
+        if dist:   # the slowest rank's time, as for the device-timed steps
+            e2e_ms[-1] = slowest(e2e_ms[-1], dist, dev)
         h2d = sum(x.numel() * x.element_size() for x in hin[0])
         d2h = hout[0][0].numel() * 4 + hout[0][1].numel() * 8   # the k-NN rows (insert ids are known)
     f.close()
@@ -439,6 +460,8 @@ def run_forests(a, rank, world, dist):
             tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in steps[:4]]
             best, ms_by_leaf = tune_leaf_size_forests(W.dims, tinit, tsteps, a.k, device=dev, stream=stream)
         del tinit, tsteps
+        if dist:
+            best = rank0_choice(best, dist, dev)
         a.leaf = best
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
                     "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
