@@ -839,7 +839,8 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
 static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s);
 
 // Erase_L on nf forests: one marking pass (its counts stay on the device),
-// lazily built blooms, one descent launch, one live-count refresh, one buffer
+// lazily built blooms, one descent launch, the k-NN records' live counts
+// (refreshed, or kept on the descent paths of small batches), one buffer
 // compaction, one host sync for the counts; reinsertion of trees below half
 // then runs for all forests together (Alg. 4).
 static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, const int64_t *n,
@@ -879,7 +880,8 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   // Every forest with a nonempty batch takes part from here on without a wait
   // for the counts: the launches are sized by the batch lengths and read the
   // counts on the device, and a forest whose batch erased nothing is left as
-  // it was (its blooms get built, which an erase reaching it does anyway).
+  // it was (its new blooms are skipped on the device and unmarked after the
+  // sync below).
   const int64_t *ne_dev = (const int64_t *)counts;
   std::vector<int> act(mk.size());   // indices into mk of the forests taking part
   for (size_t j = 0; j < mk.size(); ++j) act[j] = (int)j;
