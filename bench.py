@@ -626,6 +626,7 @@ def forests_cpu_sample(a, nsample=16):
     from paper_2112_06188_gb300 import inputs
     W = inputs.ForestsWorkload(nf=a.forests, seed=4)
     step = W.step()
+    nsample = min(nsample, a.forests)
     os_ = []
     for i in range(nsample):
         o = OracleForest(W.dims[i], leaf_size=16, buffer_size=1024)
