@@ -451,6 +451,8 @@ def run_forests(a, rank, world, dist):
     steps = [W.step() for _ in range(nsteps)]
     nf = a.forests
     autotune = None
+    if a.leaf == "auto" and nsteps < 2:
+        a.leaf = 16                      # too few steps to time a candidate: the default
     if a.leaf == "auto":
         from paper_2112_06188_gb300.autotune import tune_leaf_size_forests
         t0 = time.perf_counter()
