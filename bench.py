@@ -227,7 +227,8 @@ def run_ours(a, rank, world, dist):
     torch.cuda.set_device(dev)
     capi.load()
     stream = torch.cuda.Stream(dev)
-    nsteps = a.warmup + a.steps + a.e2e_steps + 1
+    # warm-up, timed (profiled), timed again without profiling, end to end
+    nsteps = a.warmup + 2 * a.steps + a.e2e_steps + 1
     W = StepInputs(a.n0, a.batch, a.queries, a.dim, nsteps, seed=2 + 17 * rank)
 
     def H2D(x):
@@ -235,18 +236,24 @@ def run_ours(a, rank, world, dist):
 
     autotune = None
     if a.leaf == "auto":
-        from paper_2112_06188_gb300.autotune import tune_leaf_size
+        from paper_2112_06188_gb300.autotune import CONFIG_CANDIDATES, choose, tune_leaf_size
         t0 = time.perf_counter()
+        # the tuning forest and steps come from a seed of their own: the
+        # timed steps are never seen before they are timed
+        TW = StepInputs(a.n0, a.batch, a.queries, a.dim, 9, seed=7919 + 17 * rank)
         with torch.cuda.stream(stream):
-            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps[:9]]
-            best, ms_by_leaf = tune_leaf_size(a.dim, H2D(W.initial), tsteps, a.k, device=dev, stream=stream,
+            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in TW.steps]
+            best, ms_by_leaf = tune_leaf_size(a.dim, H2D(TW.initial), tsteps, a.k, device=dev, stream=stream,
                                               split=a.split)
-        del tsteps
+        del tsteps, TW
         if dist:
             best = rank0_choice(best, dist, dev)
         a.leaf = best
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
-                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
+                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2),
+                    "inputs": "own seed (7919), 8 timed steps after one warm-up; not the timed steps",
+                    "config_set": {"candidates": list(CONFIG_CANDIDATES),
+                                   "chosen": choose({L: ms_by_leaf[L] for L in CONFIG_CANDIDATES})}}
     a.leaf = int(a.leaf)
     with torch.cuda.stream(stream):
         f = Forest(a.dim, leaf_size=a.leaf, buffer_size=1024, stream=stream, device=dev, split=a.split)
@@ -255,6 +262,7 @@ def run_ours(a, rank, world, dist):
         out_ids = torch.empty((a.queries, a.k), dtype=torch.int32, device=dev)
         out_d2 = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        counts = torch.zeros(3, dtype=torch.int64, device=dev)
     stream.synchronize()
 
     def step(i):
@@ -269,6 +277,14 @@ def run_ours(a, rank, world, dist):
         ev[3].record(stream)
         return ev
 
+    def phase_ms(evs):
+        t_ins = [e[0].elapsed_time(e[1]) for e in evs]
+        t_era = [e[1].elapsed_time(e[2]) for e in evs]
+        t_knn = [e[2].elapsed_time(e[3]) for e in evs]
+        t_step = [x + y + z for x, y, z in zip(t_ins, t_era, t_knn)]
+        return {"step": statistics.mean(t_step), "insert": statistics.mean(t_ins),
+                "erase": statistics.mean(t_era), "knn": statistics.mean(t_knn)}, t_step
+
     for i in range(a.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -281,38 +297,40 @@ def run_ours(a, rank, world, dist):
     torch.cuda.synchronize(dev)
     clocks.start()
     capi.bdl_profile(True)
-    launches0 = capi.bdl_launch_count()
     evs = []
     t0 = time.perf_counter()
     for i in range(a.warmup, a.warmup + a.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         evs.append(step(i))
+        # this step's k-NN visits, by the counting instance on the same forest
+        # and queries, after the step's last event (outside the timed intervals)
+        f.knn_count(dev_steps[i][2], a.k, counts, out=(out_ids, out_d2))
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
-    launches = capi.bdl_launch_count() - launches0
-    prof = capi.bdl_profile_read()
+    prof = capi.bdl_profile_read_bytes()
     capi.bdl_profile(False)
     clk = clocks.stop()
     if dist:
         dist.barrier()
-
-    t_ins = [e[0].elapsed_time(e[1]) for e in evs]
-    t_era = [e[1].elapsed_time(e[2]) for e in evs]
-    t_knn = [e[2].elapsed_time(e[3]) for e in evs]
-    t_step = [x + y + z for x, y, z in zip(t_ins, t_era, t_knn)]
-    ms_step = sum(t_step) / len(t_step)
-    ms = {"step": ms_step, "insert": sum(t_ins) / len(t_ins), "erase": sum(t_era) / len(t_era),
-          "knn": sum(t_knn) / len(t_knn)}
+    # the step's own launches (the counting runs are not part of it)
+    launches = sum(v[1] for kname, v in prof.items() if kname != "k_knn_count")
+    prof = {kname: v for kname, v in prof.items() if kname != "k_knn_count"}
+    ms, t_steps = phase_ms(evs)
     if dist:
         ms = max_over_ranks(ms, dist, dev)
+    nodes, points, nq = (int(x) for x in counts.cpu().tolist())
 
-    # k-NN visit counts for the algorithmic bytes (separate, untimed launch)
-    f.knn_stats(True)
-    f.knn(dev_steps[a.warmup + a.steps - 1][2], a.k, out=(out_ids, out_d2))
-    stream.synchronize()
-    nodes, points, nq = f.knn_stats()
-    f.knn_stats(False)
+    # the same steps without per-launch profiling events, on the next inputs
+    evs2 = []
+    for i in range(a.warmup + a.steps, a.warmup + 2 * a.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        evs2.append(step(i))
+    torch.cuda.synchronize(dev)
+    ms_plain, _ = phase_ms(evs2)
+    if dist:
+        ms_plain = max_over_ranks(ms_plain, dist, dev)
 
     # end to end through the public API from pinned host buffers: every step's
     # inputs are copied in and its k-NN rows copied out inside the timed
@@ -324,7 +342,8 @@ def run_ours(a, rank, world, dist):
     K = a.e2e_steps
     if K > 0:
         import torch as _t
-        idx = list(range(a.warmup + a.steps, a.warmup + a.steps + K))
+        first = a.warmup + 2 * a.steps
+        idx = list(range(first, first + K))
         hin = [tuple(_t.from_numpy(x).pin_memory() for x in W.steps[i]) for i in idx]
         hout = [(_t.empty((a.queries, a.k), dtype=_t.int32).pin_memory(),
                  _t.empty((a.queries, a.k), dtype=_t.int64).pin_memory()) for _ in range(2)]
@@ -375,8 +394,9 @@ def run_ours(a, rank, world, dist):
 
     ops_per_step = 2 * a.batch + a.queries
     res = {
-        "ms": ms, "launches": launches, "prof": prof, "clocks": clk, "wall": wall,
-        "knn_stats": (nodes, points, nq), "e2e_ms": statistics.mean(e2e_ms) if e2e_ms else None,
+        "ms": ms, "ms_plain": ms_plain, "t_steps": t_steps, "launches": launches, "prof": prof,
+        "clocks": clk, "wall": wall, "knn_stats": (nodes, points, nq),
+        "e2e_ms": statistics.mean(e2e_ms) if e2e_ms else None,
         "h2d": h2d, "d2h": d2h, "ops_per_step": ops_per_step, "autotune": autotune,
     }
     return res
@@ -958,44 +978,82 @@ def recorded_traffic(kernel, leaf):
     return int(fields["dram_bytes_per_launch"])
 
 
-def roofline(a, res, peaks):
-    """Dominant kernel of the timed region against the measured HBM peak."""
+ROOFLINE_KERNELS = ("k_knn", "k_subtree", "k_level_partition", "k_erase_locate", "k_bloom_build")
+
+
+def rec_bytes(dim):
+    """Bytes of one point record in a tree: d coordinates and the id, padded to
+    a multiple of 16 bytes (the leaf scan reads whole records)."""
+    return 4 * ((dim + 1 + 3) // 4 * 4)
+
+
+def rooflines(a, res, peaks):
+    """Each hot kernel of the timed region against the measured HBM peak:
+    achieved = algorithmic bytes summed over the timed steps / the kernel's
+    device time summed over the same steps (CUDA events around every launch).
+    The bytes of k_knn come from the counting instance run on every timed
+    step's forest and queries (4d + 12k per query, 32 per visited node, one
+    record per examined leaf point); the others' from the library's own
+    per-launch figures (bdl_profile_read_bytes)."""
     prof = res["prof"]
-    if not prof:
-        return None
-    name, (tot_ms, nlaunch) = max(prof.items(), key=lambda kv: kv[1][0])
-    per_launch_ms = tot_ms / nlaunch
-    d, k = a.dim, a.k
-    R = 4 * d + 4
-    nodes, points, nq = res["knn_stats"]
-    algo = None
-    if name == "k_knn" and nq:
-        # per query: query in, k results out, one 32-B sector per visited node,
-        # one record per examined leaf point
-        per_q = 4 * d + 12 * k + 32 * nodes / nq + R * points / nq
-        algo = per_q * a.queries
     peak = peaks.get("hbm_gbs")
-    if algo is None or not peak:
-        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
-                "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
-    achieved = algo / (per_launch_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(name, a.leaf) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "when" in peaks else "fallback",
-            "ms_per_launch": round(per_launch_ms, 4),
-            "algorithmic_bytes_per_launch": int(algo),
-            "knn_visits_per_query": {"nodes": round(nodes / nq, 2), "leaf_points": round(points / nq, 2)}}
+    src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "when" in peaks else "fallback"
+    nodes, points, nq = res["knn_stats"]
+    out = []
+    for name in ROOFLINE_KERNELS:
+        if name not in prof:
+            continue
+        tot_ms, nl, algo = prof[name]
+        extra = {}
+        if name == "k_knn":
+            if not nq:
+                continue
+            algo = nq * (4 * a.dim + 12 * a.k) + 32 * nodes + rec_bytes(a.dim) * points
+            extra = {"knn_visits_per_query": {"nodes": round(nodes / nq, 2), "leaf_points": round(points / nq, 2)},
+                     "queries_counted": nq}
+        if not algo or not tot_ms or not peak:
+            continue
+        achieved = algo / (tot_ms * 1e-3) / 1e9
+        traffic = recorded_traffic(name, a.leaf) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
+        e = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+             "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
+             "ms_per_launch": round(tot_ms / nl, 4), "launches_per_step": round(nl / a.steps, 2),
+             "ms_per_step": round(tot_ms / a.steps, 4),
+             "algorithmic_bytes_per_launch": int(algo / nl)}
+        e.update(extra)
+        out.append(e)
+    return out
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def oracle_sample(a, nsteps, seed=2):
     """Time the oracle on a 1/10-scale step: forest of n0/10 points, then per
-    step insert batch/10, erase batch/10, k-NN for queries/10."""
+    step insert batch/10, erase batch/10, k-NN for queries/10.  Returns the
+    per-step times, the operations per step, a description, and the last
+    step's k-NN rerun on all host cores (queries/s, threads)."""
     from oracle.oracle import OracleForest
+    from oracle.threads import oracle_knn
     n0, b, m = a.n0 // 10, a.batch // 10, a.queries // 10
     W = StepInputs(n0, b, m, a.dim, nsteps, seed=seed)
     o = OracleForest(a.dim, leaf_size=16 if a.leaf == "auto" else int(a.leaf), buffer_size=1024, split=a.split)
@@ -1010,7 +1068,24 @@ def oracle_sample(a, nsteps, seed=2):
     ops = 2 * b + m
     sample = ("1/10-scale step on one host core: forest of %d points, insert %d, erase %d, "
               "k=%d NN for %d queries" % (n0, b, b, a.k, m))
-    return times, ops, sample
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle_knn(o, W.steps[-1][2], a.k, threads=threads)
+    allc = {"queries_per_s": round(m / (time.perf_counter() - t0), 1), "threads": threads,
+            "what": "the last sample step's k-NN batch split over host threads (the oracle's k-NN only reads "
+                    "the forest)"}
+    return times, ops, sample, allc
+
+
+def cpu_baseline_line(a):
+    """The oracle's cpu_baseline: median of three 1/10-scale steps after one
+    warm-up step (the paper's protocol, Sec. VI), on one core."""
+    times, ops, sample, allc = oracle_sample(a, 4)
+    med = statistics.median(times[1:])
+    return {"value": round(ops / med, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
+            "sample": sample + "; median of 3 steps after one warm-up step",
+            "step_s": [round(t, 3) for t in times[1:]], "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "knn_all_cores": allc}
 
 
 def run_reference(a, rank):
@@ -1042,7 +1117,7 @@ def run_reference(a, rank):
         print(json.dumps(out), flush=True)
         return
     W = a.warmup
-    times, ops, sample = oracle_sample(a, W + a.steps)
+    times, ops, sample, allc = oracle_sample(a, W + a.steps)
     t = times[W:]
     ms = 1e3 * sum(t) / len(t)
     value = ops / (ms * 1e-3)
@@ -1051,7 +1126,8 @@ def run_reference(a, rank):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
            "data": "synthetic", "config": workload_config(a, a.gpus),
            "cpu_baseline": {"value": round(value, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+                            "knn_all_cores": allc},
            "e2e": {"value": round(value, 1), "unit": "ops/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -1115,9 +1191,18 @@ def main():
         "gpu_launches": res["launches"],
         "kernel_ms": {k: [round(v[0] / a.steps, 4), v[1] // a.steps] for k, v in
                       sorted(res["prof"].items(), key=lambda kv: -kv[1][0])},
-        "roofline": roofline(a, res, peaks),
+        "profiling": "every launch of the timed steps bracketed by CUDA events (per-kernel times, rooflines); "
+                     "unprofiled_ms_per_step: the next %d steps without them" % a.steps,
+        "unprofiled_ms_per_step": round(res["ms_plain"]["step"], 3),
+        "unprofiled_phase_ms": {k: round(v, 3) for k, v in res["ms_plain"].items()},
+        "step_ms_min_max": [round(min(res["t_steps"]), 3), round(max(res["t_steps"]), 3)],
         "clocks": res["clocks"],
     }
+    rl = rooflines(a, res, peaks)
+    if rl:
+        dom = max(rl, key=lambda e: e["ms_per_step"])
+        out["roofline"] = dom
+        out["rooflines"] = rl
     if res["autotune"]:
         out["config"]["leaf_autotune"] = res["autotune"]
     if res["e2e_ms"]:
@@ -1126,10 +1211,7 @@ def main():
                       "ms_per_step": round(res["e2e_ms"], 3), "steps": a.e2e_steps,
                       "pipelined": "next inputs in and previous rows out on copy streams during each step"}
     if world == 1 and not a.no_cpu_baseline:
-        times, ops_c, sample = oracle_sample(a, 2)
-        v = ops_c / (sum(times) / len(times))
-        out["cpu_baseline"] = {"value": round(v, 1), "unit": "ops/s", "cores": 1, "kind": "oracle",
-                               "sample": sample}
+        out["cpu_baseline"] = cpu_baseline_line(a)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -30,12 +30,13 @@
  *    owned by the library (one per device), optionally capped per forest by
  *    bdl_config.hbm_budget_bytes.
  *  - Kernels check their indexes: one that finds an index outside its buffers
- *    skips the access and sets a bit in the forest's device error word.  With
- *    the environment variable BDL_DEBUG_CHECK=1 (read at bdl_create) every call
- *    waits for its kernels and returns BDL_EINTERNAL when a bit is set (1 child
+ *    skips the access and sets a bit in the forest's device error word (1 child
  *    slot, 2 leaf range, 4 traversal stack, 8 partition, 16 gather, 32 a packed
- *    k-NN record's live count differs from its node's), with the bits in
- *    bdl_last_error().
+ *    k-NN record's live count differs from its node's).  bdl_insert and
+ *    bdl_erase read the word at the waits they make and return BDL_EINTERNAL
+ *    when a bit is set, with the bits in bdl_last_error(); bdl_poll_error reads
+ *    it on demand.  With the environment variable BDL_DEBUG_CHECK=1 (read at
+ *    bdl_create) every call also waits for its own kernels and checks the word.
  */
 #ifndef BDL_H
 #define BDL_H
@@ -329,6 +330,28 @@ int bdl_tree_export(const bdl_forest *f, int level, int64_t *key_host, int32_t *
  * bdl_tree_info); BDL_EINVAL if it has not been built. */
 int bdl_bloom_export(const bdl_forest *f, int level, uint32_t *words_host, bdl_stream_t stream);
 
+/* kNN_L like bdl_knn, run by the counting instance of the kernel (a plain
+ * one-lane walk of the binary nodes with the same pruning rule, Alg. 5 /
+ * Sec. IV-A3), which returns the same rows and adds, with device atomics,
+ * the tree nodes it visits to counts_dev[0], the live leaf points it examines
+ * to counts_dev[1] and the queries to counts_dev[2].  counts_dev is a device
+ * array of three uint64 (8-byte aligned) owned by the caller, who zeroes it;
+ * nothing is waited for.  Measurement only: these counts give the
+ * algorithmic bytes of a k-NN launch (4d + 12k per query, 32 per node, one
+ * record per leaf point).  Under profiling its launches are reported as
+ * "k_knn_count", apart from the timed instance "k_knn". */
+int bdl_knn_count(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_ids_dev,
+                  int64_t *out_d2_dev, uint64_t *counts_dev, bdl_stream_t stream);
+
+/* Wait for `stream` and read the forest's device error word (bit codes as
+ * in the conventions above) into *out_bits_host (may be NULL): BDL_OK if no
+ * bit is set, else BDL_EINTERNAL.  The word is sticky.  bdl_insert and
+ * bdl_erase read it at the waits they make anyway (insert: the word as it
+ * stood before the call's own kernels; erase: after them) and fail with
+ * BDL_EINTERNAL when it is set; this call is the poll for k-NN callers, whose
+ * calls never wait. */
+int bdl_poll_error(const bdl_forest *f, uint64_t *out_bits_host, bdl_stream_t stream);
+
 /* Totals over every bdl_knn call of this forest since the last reset when
  * counting is on: out[0] = tree nodes visited, out[1] = leaf points examined,
  * out[2] = queries.  bdl_knn_stats(f, 1/0, NULL) switches counting on/off and
@@ -347,6 +370,21 @@ uint64_t bdl_launch_count(void);
  * ms and the launch count since the last call, then clears the records. */
 int bdl_profile(int enable);
 int bdl_profile_read(double *ms_host, int64_t *launches_host, int cap);
+/* bdl_profile_read plus, per kernel, the summed algorithmic bytes of the
+ * recorded launches (bytes_host may be NULL): the least DRAM traffic the
+ * launch's work implies, computed by the library from the sizes it knows when
+ * it launches (records per level, ids, points), for the roofline fraction
+ * achieved = bytes / time.  Per record of d coordinates: the global build
+ * levels' histogram and candidate passes read its split coordinate (4 B) and
+ * the partition reads and writes it ((d + 1) words each way); the on-chip
+ * subtree build reads it from staging and writes it in leaf order, plus every
+ * node below the global levels (16-byte node, 2d-word box, live count) and
+ * the leaf offsets; per erased id (batch length): 4d for its coordinates, a
+ * 32-byte bloom block per tree and a descent (16 B per level and the leaf's
+ * records) of a tree chosen in proportion to the trees' sizes; per bloom key
+ * 4 + 32.  Kernels without a stated figure (k_knn among them: its bytes come
+ * from bdl_knn_count) report 0. */
+int bdl_profile_read_bytes(double *ms_host, int64_t *launches_host, double *bytes_host, int cap);
 
 /* Kernel ids are 0 .. bdl_kernel_count()-1; bdl_kernel_name gives each one's
  * name (e.g. "k_knn"). */

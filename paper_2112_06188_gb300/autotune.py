@@ -19,6 +19,7 @@ from . import inputs
 from .forest import Forest
 
 CANDIDATES = (8, 12, 16, 24, 32)
+CONFIG_CANDIDATES = (8, 16, 32)   # the leaf sizes the 10M-point 3-D workload names
 DEFAULT = 16
 TIE = 0.01
 

@@ -22,6 +22,7 @@ SYMBOLS = [
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
     "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
     "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy", "bdl_next_id",
+    "bdl_knn_count", "bdl_poll_error", "bdl_profile_read_bytes",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -112,6 +113,9 @@ def load(path=None):
         "bdl_knn_plan_launch": (i32, [P, P]),
         "bdl_knn_plan_destroy": (i32, [P]),
         "bdl_next_id": (i32, [P, P]),
+        "bdl_knn_count": (i32, [P, P, i64, i32, P, P, P, P]),
+        "bdl_poll_error": (i32, [P, P, P]),
+        "bdl_profile_read_bytes": (i32, [P, P, P, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -168,6 +172,19 @@ def bdl_erase(f, ids_dev, n, stream):
 
 def bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
     return load().bdl_knn(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream)
+
+
+def bdl_knn_count(f, q_dev, m, k, out_ids_dev, out_d2_dev, counts_dev, stream):
+    """bdl_knn by the counting instance: adds (nodes, points, queries) into the
+    device array counts_dev[3] (uint64)."""
+    return load().bdl_knn_count(f, q_dev, m, k, out_ids_dev, out_d2_dev, counts_dev, stream)
+
+
+def bdl_poll_error(f, stream):
+    """Returns (status, device error word bits); waits for the stream."""
+    bits = ctypes.c_uint64(0)
+    st = load().bdl_poll_error(f, _ref(bits), stream)
+    return st, bits.value
 
 
 def bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):
@@ -323,6 +340,16 @@ def bdl_profile_read():
     cnt = (ctypes.c_int64 * n)()
     check(load().bdl_profile_read(ms, cnt, n), "bdl_profile_read")
     return {bdl_kernel_name(i): (ms[i], cnt[i]) for i in range(n) if cnt[i]}
+
+
+def bdl_profile_read_bytes():
+    """{kernel name: (total ms, launches, algorithmic bytes)} since the last read."""
+    n = load().bdl_kernel_count()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    by = (ctypes.c_double * n)()
+    check(load().bdl_profile_read_bytes(ms, cnt, by, n), "bdl_profile_read_bytes")
+    return {bdl_kernel_name(i): (ms[i], cnt[i], by[i]) for i in range(n) if cnt[i]}
 
 
 def bdl_kernel_count():

@@ -26,7 +26,10 @@ extern std::atomic<uint64_t> g_launches;
 
 // Every kernel launch of the library goes through a KScope: it counts the
 // launch and, while profiling is on, brackets it with CUDA events on the
-// launching stream so per-kernel device times can be read back.
+// launching stream so per-kernel device times can be read back, together
+// with the launch's algorithmic bytes (the minimum DRAM traffic its work
+// implies, computed from the sizes the host knows at launch; 0 where not
+// stated).
 enum KernelId : int {
   kK_gather_cleared,
   kK_gather_pool,
@@ -57,11 +60,12 @@ enum KernelId : int {
   kK_sp_scatter,
   kK_sp_split,
   kK_sp_box,
+  kK_knn_count,
   kKernelCount
 };
 extern const char *const kKernelNames[kKernelCount];
 struct KScope {
-  KScope(int kid, cudaStream_t s);
+  KScope(int kid, cudaStream_t s, double bytes = 0);
   ~KScope();
   int rec;
   cudaStream_t s;
@@ -399,6 +403,7 @@ constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input o
 constexpr size_t kPinnedWords = 2048;          // a forest's pinned scratch, in int64 words
 constexpr size_t kPinnedFlags = 2040;          // insert-validation flags that fit in it
 constexpr size_t kPinnedErr = 2044;            // where the error word is read back
+constexpr int kBufOutWords = kMaxLevel + 2;    // per forest: buffer size, root live counts, error word
 int smem_subtree_capacity(int dim);
 
 // ---- build.cu ----
@@ -464,6 +469,8 @@ struct FillSeg {           // `count` work items of one kind
   int64_t first;           // pool tail: range start; iota / alive: first id
   int64_t from;            // pool tail: first pool entry copied
   uint32_t *alive;         // alive: the forest's bitmap
+  const unsigned long long *errw;  // append: the forest's device error word; a set word
+                                   // sets bit 1 of *flag
 };
 struct MarkSeg {           // one forest's erase batch
   uint32_t *alive;
@@ -491,7 +498,9 @@ struct BufSeg {            // one forest's buffer and roots
   int32_t *buf;
   int64_t nbuf;
   const uint32_t *alive;
-  int64_t *out;            // out[0] = new nbuf, out[1 + t] = live count of tree t
+  int64_t *out;            // out[0] = new nbuf, out[1 + t] = live count of tree t,
+                           // out[kMaxLevel + 1] = the forest's device error word
+  const unsigned long long *errw;
   int32_t ntrees, pad_;
   const int32_t *roots[kMaxLevel];
 };

@@ -1016,7 +1016,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   }
   // per global level: the trees still above the on-chip size, with segment
   // and tile prefixes; the same trees get their global nodes boxed bottom-up
-  struct LevelHost { int nact; size_t act, seg, tile, node, lt; int64_t nseg, ntile; };
+  struct LevelHost { int nact; size_t act, seg, tile, node, lt; int64_t nseg, ntile, recs; };
   std::vector<LevelHost> lv(gmax);
   std::vector<int32_t> act_all;
   std::vector<LvTree> lt_all;
@@ -1028,10 +1028,12 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     L.act = act_all.size();
     L.lt = lt_all.size();
     int64_t segs = 0, tiles = 0;
+    L.recs = 0;
     std::vector<int64_t> sp{0}, tp{0}, np{0};
     for (int j = 0; j < ntree; ++j) {
       if (bt[j].g <= it) continue;
       act_all.push_back(j);
+      L.recs += bt[j].s;
       LvTree T;
       T.base = bt[j].base;
       T.s = bt[j].s;
@@ -1113,12 +1115,19 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     G.cl = (const DCleared *)(plan + o_dc);
     G.cl_blk = (const int64_t *)(plan + o_clb);
     G.pool_off = (const int64_t *)(plan + o_pool);
+    // algorithmic bytes: every cleared record read, every live one written
+    // to staging (d + 1 words); a pool entry's coordinates gathered from the
+    // id table and written
+    double cl_read = 0, cl_live = 0;
+    for (auto &c : cl) cl_read += (double)c.size;
+    for (auto &b : bt) cl_live += (double)b.from_cleared;
+    const double rin = 4.0 * rec_ints(dim), rst = 4.0 * (dim + 1);
     if (cl_blk.back()) {
-      KScope ks_(kK_gather_cleared, s);
+      KScope ks_(kK_gather_cleared, s, cl_read * rin + cl_live * rst);
       k_gather_cleared<<<(unsigned)cl_blk.back(), TB, 0, s>>>(G);
     }
     if (pool_off.back()) {
-      KScope ks_(kK_gather_pool, s);
+      KScope ks_(kK_gather_pool, s, (double)pool_off.back() * (4.0 * dim + rst));
       k_gather_pool<<<(unsigned)ceil_div(pool_off.back(), 256), 256, 0, s>>>(G, pool_off.back());
     }
   }
@@ -1141,12 +1150,17 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     P.lt = (const LvTree *)(plan + o_lt) + L.lt;
     P.act_seg = d_pre + L.seg;
     P.act_tile = d_pre + L.tile;
-    { KScope ks_(kK_level_hist, s); k_level_hist<<<(unsigned)L.ntile, 512, 0, s>>>(P); }
+    // algorithmic bytes per record of the level: the split coordinate (4)
+    // for the histogram and the candidate gather; the record (d + 1 words)
+    // read and written by the partition
+    const double recs = (double)L.recs;
+    { KScope ks_(kK_level_hist, s, recs * 4); k_level_hist<<<(unsigned)L.ntile, 512, 0, s>>>(P); }
     { KScope ks_(kK_level_bucket, s);
       k_level_bucket<<<(unsigned)ceil_div(L.nseg, 8), 256, 0, s>>>(P, L.nseg); }
-    { KScope ks_(kK_level_collect, s); k_level_collect<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
+    { KScope ks_(kK_level_collect, s, recs * 4);
+      k_level_collect<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
     { KScope ks_(kK_level_select, s); k_level_select<<<(unsigned)L.nseg, 256, 0, s>>>(P, L.nseg); }
-    { KScope ks_(kK_level_partition, s);
+    { KScope ks_(kK_level_partition, s, recs * 8.0 * (dim + 1));
       k_level_partition<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
   }
 
@@ -1168,7 +1182,15 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
       dev_free(af, block, total, s);
       return cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
     }
-    KScope ks_(kK_subtree, s);
+    // algorithmic bytes: every record read from staging (d + 1 words) and
+    // written in leaf order (rec_ints words); every node below the global
+    // levels written (16-byte node, box, live count); the leaf offsets
+    double sub_bytes = 0;
+    for (auto &b : bt)
+      sub_bytes += (double)b.s * 4.0 * ((dim + 1) + rec_ints(dim)) +
+                   (double)(((int64_t)2 << b.h) - ((int64_t)1 << b.g)) * (16.0 + 8.0 * dim + 4.0) +
+                   4.0 * (double)(((int64_t)1 << b.h) + 1);
+    KScope ks_(kK_subtree, s, sub_bytes);
     k_subtree<<<(unsigned)sub_blk.back(), kSubThreads, smem, s>>>(P);
   }
 

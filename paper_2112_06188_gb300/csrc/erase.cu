@@ -263,7 +263,24 @@ int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
   if (st) return st;
   bool rec = false;
   for (const auto &c : calls) rec = rec || c.records;
-  KScope ks_(kK_erase_locate, s);
+  // algorithmic bytes per erased id: its coordinates (4d), one 32-byte bloom
+  // block per tree, and the descent of the tree that holds it -- one 16-byte
+  // node per level and its leaf's records -- weighted by the trees' sizes
+  // (the ids of a batch are spread over the trees in proportion to them);
+  // the batch length stands for the count of ids the alive filter keeps
+  double eb = 0;
+  for (const auto &c : calls) {
+    const ForestView &fv = *c.fv;
+    double tot = 0, desc = 0;
+    for (int t = 0; t < fv.ntrees; ++t) tot += (double)fv.tree[t].size;
+    for (int t = 0; t < fv.ntrees && tot > 0; ++t) {
+      const TreeView &T = fv.tree[t];
+      const double leaf = (double)T.size / (double)((int64_t)1 << T.h);
+      desc += (double)T.size / tot * (16.0 * (T.h + 1) + 4.0 * rec_ints(fv.dim) * leaf);
+    }
+    eb += (double)(fv.ntrees ? c.n : 0) * (4.0 * fv.dim + 32.0 * fv.ntrees + desc);
+  }
+  KScope ks_(kK_erase_locate, s, eb);
   const unsigned grid = (unsigned)cdiv(warp[n] * 32, 128);
   const EraseJob *djobs = (const EraseJob *)table;
   const int64_t *jw = (const int64_t *)((char *)table + n * sizeof(EraseJob));
@@ -342,6 +359,7 @@ __global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
       // before the flag is read back only ever sees grid coordinates
       g.dst[i] = min(max(v, 0), (1 << kCoordBits) - 1);
       if (v < 0 || v >= (1 << kCoordBits)) atomicOr(g.flag, 1ull);
+      if (i == 0 && g.errw && *g.errw) atomicOr(g.flag, 2ull);
       break;
     }
     case kFillPoolTail: g.dst[i] = pool_entry(g, g.from + i); break;
@@ -456,7 +474,10 @@ __global__ void k_buffer_compact_many(const BufSeg *segs) {
     if (threadIdx.x == 0) base += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) g.out[0] = base;
+  if (threadIdx.x == 0) {
+    g.out[0] = base;
+    g.out[kMaxLevel + 1] = g.errw ? (int64_t)*g.errw : 0;
+  }
   for (int t = threadIdx.x; t < g.ntrees; t += blockDim.x) g.out[1 + t] = g.roots[t][0];
 }
 
@@ -511,7 +532,8 @@ int launch_bloom_build_many(const std::vector<TreeSeg> &segs, void *table,
   if (pre.back() == 0) return BDL_OK;
   int st = upload_table(segs, pre, table, s);
   if (st) return st;
-  KScope ks_(kK_bloom_build, s);
+  // algorithmic bytes per point: its id and one 32-byte block
+  KScope ks_(kK_bloom_build, s, (double)pre.back() * 36.0);
   k_bloom_build_many<<<(unsigned)cdiv(pre.back(), 256), 256, 0, s>>>(
       (const TreeSeg *)table, table_pre(segs, table), (int)segs.size());
   return cuda_check(cudaGetLastError(), "bloom kernel");

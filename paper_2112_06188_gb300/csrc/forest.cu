@@ -53,12 +53,14 @@ const char *const kKernelNames[kKernelCount] = {
     "k_sp_scatter",
     "k_sp_split",
     "k_sp_box",
+    "k_knn_count",
 };
 
 // ---- live per-kernel timing (CUDA events on the launching stream) ----
 struct ProfRec {
   int kid;
   cudaEvent_t a, b;
+  double bytes;    // algorithmic bytes of the launch (0: not stated)
 };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
@@ -76,11 +78,11 @@ static cudaEvent_t take_event() {
   return e;
 }
 
-KScope::KScope(int kid, cudaStream_t st) : rec(-1), s(st) {
+KScope::KScope(int kid, cudaStream_t st, double bytes) : rec(-1), s(st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  ProfRec r{kid, take_event(), take_event()};
+  ProfRec r{kid, take_event(), take_event(), bytes};
   cudaEventRecord(r.a, s);
   g_prof.push_back(r);
   rec = (int)g_prof.size() - 1;
@@ -745,6 +747,7 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
     g.count = n[i] * F[i]->dim;
     g.src = pts[i];
     g.dst = F[i]->idtab + F[i]->next_id * F[i]->dim;
+    g.errw = F[i]->err;            // the flags also carry the error word of earlier work
     app.push_back(g);
   }
   if (app.empty()) return BDL_OK;
@@ -775,11 +778,19 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   }
   if (!st && !ahead) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
+  // flag bit 0: a coordinate off the grid; bit 1: the forest's device error
+  // word was set by earlier work (a kernel found an index outside its buffers)
   auto off_grid = [&]() {
     for (size_t j = 0; j < app.size(); ++j)
-      if (hf[j]) return true;
+      if (hf[j] & 1) return true;
     return false;
   };
+  auto dev_error = [&]() {
+    for (size_t j = 0; j < app.size(); ++j)
+      if (hf[j] & 2) return true;
+    return false;
+  };
+  if (!ahead && dev_error()) return set_error(BDL_EINTERNAL, "device error word set by earlier work");
   if (!ahead && off_grid()) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
   // 2. plan every forest (Alg. 3), allocating the new trees
   std::vector<InsertPlan> plans(nf);
@@ -820,9 +831,10 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   if (ahead) {
     const int es = cuda_check(cudaEventSynchronize(F[0]->ev_flags), "cudaEventSynchronize");
     if (!st) st = es;
-    if (!st && off_grid()) {
+    if (!st && (off_grid() || dev_error())) {
       for (auto &ip : plans)
         if (ip.f) drop_plan(ip, s);
+      if (dev_error()) return set_error(BDL_EINTERNAL, "device error word set by earlier work");
       return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
     }
   }
@@ -973,7 +985,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   std::vector<TreeSeg> lives;
   std::vector<BufSeg> bufs;
   void *outs = nullptr;
-  st = tmp.get(act.size() * (kMaxLevel + 1) * 8, &outs);
+  st = tmp.get(act.size() * kBufOutWords * 8, &outs);
   if (st) return st;
   for (size_t a = 0; a < act.size(); ++a) {
     bdl_forest *f = F[mk_forest[act[a]]];
@@ -982,7 +994,8 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     b.buf = f->buf;
     b.nbuf = f->nbuf;
     b.alive = f->alive;
-    b.out = (int64_t *)outs + a * (kMaxLevel + 1);
+    b.out = (int64_t *)outs + a * kBufOutWords;
+    b.errw = f->err;
     for (int i = kMaxLevel - 1; i >= 0; --i) {
       Tree *t = f->trees[i];
       if (!t) continue;
@@ -1008,7 +1021,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   }
   st = tmp.get(table_bytes(bufs.size(), sizeof(BufSeg)), &bt2);
   if (!st) st = launch_buffer_compact_many(bufs, bt2, s);
-  std::vector<int64_t> ho(act.size() * (kMaxLevel + 1)), ne(mk.size());
+  std::vector<int64_t> ho(act.size() * kBufOutWords), ne(mk.size());
   if (!st) st = cuda_check(cudaMemcpyAsync(ho.data(), outs, ho.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st) st = cuda_check(cudaMemcpyAsync(ne.data(), counts, ne.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -1016,14 +1029,16 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   // 5. new counts; trees below half capacity are emptied and their points
   //    reinserted (Alg. 4), all forests' reinsertions built together
   std::vector<bdl_forest *> touched;
+  int64_t dev_err = 0;
   for (size_t a = 0; a < act.size(); ++a) {
     const int j = act[a];
     bdl_forest *f = F[mk_forest[j]];
     if (out_n) out_n[mk_forest[j]] = ne[j];
     f->live -= ne[j];
+    const int64_t *o = &ho[a * kBufOutWords];
+    dev_err |= o[kMaxLevel + 1];
     if (ne[j] == 0) continue;   // nothing erased: counts and trees as they were
     f->version++;
-    const int64_t *o = &ho[a * (kMaxLevel + 1)];
     if (o[0] != f->nbuf) f->buf_dirty = true;
     f->nbuf = o[0];
     int r = 0;
@@ -1039,6 +1054,10 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       ft.second->bloom_blocks = 0;
       ft.second->bloom_bytes = 0;
     }
+  // a kernel of this call or an earlier one found an index outside its
+  // buffers: the counts above are applied, the rebuilds are not attempted
+  if (dev_err)
+    return set_error(BDL_EINTERNAL, "device bounds check failed, code " + std::to_string(dev_err));
   st = reinsert_low(touched, s);
   if (st) return st;
   return cuda_check(cudaGetLastError(), "erase");
@@ -1125,7 +1144,8 @@ static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s) {
 // kNN_L on nf forests: stale buffer trees rebuilt in shared builds, then one
 // k-NN launch per dimension over every forest's queries.
 static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const int64_t *m, int k,
-                    int32_t *const *oi, int64_t *const *od, cudaStream_t s) {
+                    int32_t *const *oi, int64_t *const *od, cudaStream_t s,
+                    unsigned long long *counts = nullptr) {
   if (k < 1 || k > kMaxK) return set_error(BDL_EINVAL, "k must be in 1..32");
   for (int i = 0; i < nf; ++i) {
     if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
@@ -1140,7 +1160,7 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
   // while the host plans the buffer trees' rebuilds.
   std::vector<int32_t *> perm(nf, nullptr);
   for (int i = 0; i < nf; ++i) {
-    if (m[i] < kSortMinQueries) continue;
+    if (m[i] < kSortMinQueries || counts) continue;   // the counting walk is per lane: no order needed
     void *scratch = nullptr;
     if (tmp.get(query_sort_bytes(m[i], F[i]->dim), &scratch) == BDL_OK) {
       perm[i] = (int32_t *)scratch;
@@ -1166,6 +1186,7 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
       if (c.fv->dim == d) g.push_back(c);
     for (int i = 0; i < nf; ++i)
       if (F[i]->dim == d && F[i]->knn_stats) stats = F[i]->knn_stats;
+    if (counts) stats = counts;
     void *table = nullptr;
     const size_t tb = knn_table_bytes(g);
     if (tb) st = tmp.get(tb, &table);
@@ -1358,10 +1379,15 @@ int bdl_profile(int enable) {
 }
 
 int bdl_profile_read(double *ms, int64_t *launches, int cap) {
+  return bdl_profile_read_bytes(ms, launches, nullptr, cap);
+}
+
+int bdl_profile_read_bytes(double *ms, int64_t *launches, double *bytes, int cap) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (int i = 0; i < cap && i < kKernelCount; ++i) {
     if (ms) ms[i] = 0;
     if (launches) launches[i] = 0;
+    if (bytes) bytes[i] = 0;
   }
   for (auto &r : g_prof) {
     int st = cuda_check(cudaEventSynchronize(r.b), "cudaEventSynchronize");
@@ -1372,6 +1398,7 @@ int bdl_profile_read(double *ms, int64_t *launches, int cap) {
     if (r.kid < cap) {
       if (ms) ms[r.kid] += t;
       if (launches) launches[r.kid] += 1;
+      if (bytes) bytes[r.kid] += r.bytes;
     }
   }
   prof_reset();
@@ -1469,6 +1496,28 @@ int bdl_knn_batch(bdl_forest *const *forests, int nf, const int32_t *const *q, c
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(forests[0]->device);
   return finish_many(forests, nf, s, knn_many(forests, nf, q, m, k, out_ids, out_d2, s));
+}
+
+int bdl_knn_count(bdl_forest *f, const int32_t *q, int64_t m, int k, int32_t *out_ids, int64_t *out_d2,
+                  uint64_t *counts_dev, bdl_stream_t stream) {
+  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
+  if (!counts_dev || ((uintptr_t)counts_dev & 7)) return set_error(BDL_EINVAL, "counts_dev must be an aligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(f->device);
+  return finish(f, s, knn_many(&f, 1, &q, &m, k, &out_ids, &out_d2, s, (unsigned long long *)counts_dev));
+}
+
+int bdl_poll_error(const bdl_forest *f, uint64_t *out_bits, bdl_stream_t stream) {
+  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
+  DeviceGuard g(f->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = cuda_check(cudaMemcpyAsync(f->pinned + kPinnedErr, f->err, 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "sync");
+  if (st) return st;
+  const uint64_t bits = (uint64_t)f->pinned[kPinnedErr];
+  if (out_bits) *out_bits = bits;
+  if (bits) return set_error(BDL_EINTERNAL, "device bounds check failed, code " + std::to_string(bits));
+  return BDL_OK;
 }
 
 int bdl_knn_plan_create(bdl_forest *const *forests, int nf, const int32_t *const *q, const int64_t *m, int k,

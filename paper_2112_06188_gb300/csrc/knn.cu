@@ -443,7 +443,7 @@ template <int D>
 void launch_d(const KnnJob *jobs, const int64_t *job_warp, int njobs, int64_t warps, int k,
               unsigned long long *stats, cudaStream_t s) {
   const size_t smem = (size_t)k * kKnnThreads * 12;   // <= 48 KB for k <= 32
-  KScope ks_(kK_knn, s);
+  KScope ks_(stats ? kK_knn_count : kK_knn, s);
   const unsigned grid = (unsigned)((warps * 32 + kKnnThreads - 1) / kKnnThreads);
   if (stats)
     k_knn<D, true><<<grid, kKnnThreads, smem, s>>>(jobs, job_warp, njobs, k, stats);
@@ -454,7 +454,7 @@ void launch_d(const KnnJob *jobs, const int64_t *job_warp, int njobs, int64_t wa
 template <int D>
 void launch_one(const KnnOne &P, int k, unsigned long long *stats, cudaStream_t s) {
   const size_t smem = (size_t)k * kKnnThreads * 12;
-  KScope ks_(kK_knn, s);
+  KScope ks_(stats ? kK_knn_count : kK_knn, s);
   const unsigned grid = (unsigned)((P.job.m + kKnnThreads - 1) / kKnnThreads);
   if (stats)
     k_knn_one<D, true><<<grid, kKnnThreads, smem, s>>>(P, k, stats);

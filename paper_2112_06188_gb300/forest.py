@@ -27,6 +27,41 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+GRID = 1 << 20                      # coordinates lie in [0, 2^20)
+I32_MIN, I32_MAX = -(1 << 31), (1 << 31) - 1
+
+
+def _int_tensor(x):
+    """x as a torch tensor of an integer dtype (numpy arrays, lists and tensors
+    accepted; floating-point or boolean data is refused rather than rounded)."""
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x))
+    x = torch.as_tensor(x)
+    if x.dtype.is_floating_point or x.dtype.is_complex or x.dtype == torch.bool:
+        raise TypeError("integer data expected, got %s" % x.dtype)
+    return x
+
+
+def _narrow_i32(x, lo, hi, what):
+    """x cast to int32, after checking (when the cast would narrow) that every
+    value lies in [lo, hi]: a wider value must not wrap onto another one."""
+    if x.dtype == torch.int32:
+        return x
+    if x.numel():
+        mn, mx = (int(v) for v in torch.aminmax(x))
+        if mn < lo or mx > hi:
+            raise ValueError("%s outside [%d, %d] (got %d .. %d)" % (what, lo, hi, mn, mx))
+    return x.to(torch.int32)
+
+
+def _coords_i32(x):
+    return _narrow_i32(_int_tensor(x), 0, GRID - 1, "coordinates")
+
+
+def _ids_i32(x):
+    return _narrow_i32(_int_tensor(x), I32_MIN, I32_MAX, "ids")
+
+
 class Forest:
     """A batch-dynamic kd-tree forest resident on one GPU."""
 
@@ -68,14 +103,15 @@ class Forest:
     def _stream(self):
         return self.stream if self.stream is not None else torch.cuda.current_stream(self.device)
 
-    def _dev(self, x, dtype):
-        """Device tensor of x; host data goes through pinned memory on the forest's stream."""
-        if isinstance(x, np.ndarray):
-            x = torch.from_numpy(np.ascontiguousarray(x))
-        x = torch.as_tensor(x)
+    def _dev(self, x):
+        """Contiguous int32 tensor of x (already narrowed) on the forest's
+        device; host data goes through pinned memory on the forest's stream,
+        a tensor on another GPU is copied over."""
         if x.is_cuda:
-            return x.to(dtype).contiguous()
-        x = x.to(dtype).contiguous()
+            if x.device != self.device:
+                x = x.to(self.device)
+            return x.contiguous()
+        x = x.contiguous()
         if not x.is_pinned():
             x = x.pin_memory()
         with torch.cuda.stream(self._stream()):
@@ -90,7 +126,7 @@ class Forest:
         device; for host points a host tensor, known without a device read:
         the ids are consecutive)."""
         on_host = not (isinstance(points, torch.Tensor) and points.is_cuda)
-        p = self._dev(points, torch.int32).reshape(-1, self.dim)
+        p = self._dev(_coords_i32(points)).reshape(-1, self.dim)
         if on_host:
             capi.check(capi.bdl_insert(self._h, _ptr(p), p.shape[0], None, _stream_handle(self.stream)),
                        "bdl_insert")
@@ -104,7 +140,7 @@ class Forest:
 
     def erase(self, ids):
         """Erase_L: returns the number of points erased."""
-        i = self._dev(ids, torch.int32).reshape(-1)
+        i = self._dev(_ids_i32(ids)).reshape(-1)
         st, n = capi.bdl_erase(self._h, _ptr(i), i.shape[0], _stream_handle(self.stream))
         capi.check(st, "bdl_erase")
         return n
@@ -112,13 +148,14 @@ class Forest:
     def knn(self, queries, k, out=None):
         """kNN_L: (ids [m,k] int32, d2 [m,k] int64), sorted by (d2, id)."""
         on_host = not (isinstance(queries, torch.Tensor) and queries.is_cuda)
-        q = self._dev(queries, torch.int32).reshape(-1, self.dim)
+        q = self._dev(_coords_i32(queries)).reshape(-1, self.dim)
         m = q.shape[0]
         if out is None:
             oi = torch.empty((m, k), dtype=torch.int32, device=self.device)
             od = torch.empty((m, k), dtype=torch.int64, device=self.device)
         else:
             oi, od = out
+            _check_out(oi, od, m, k, self.device)
         capi.check(capi.bdl_knn(self._h, _ptr(q), m, k, _ptr(oi), _ptr(od),
                                 _stream_handle(self.stream)), "bdl_knn")
         if on_host:
@@ -174,6 +211,30 @@ class Forest:
                     box=box.reshape(nn, 2 * d), node_live=nlive, leaf_off=leaf_off,
                     ids=real, dead=dead, bloom=bloom)
 
+    def knn_count(self, queries, k, counts, out=None):
+        """kNN_L through the counting instance (same rows); adds the nodes
+        visited, live leaf points examined and queries to `counts`, a (3,)
+        int64 device tensor the caller zeroes.  Measurement only."""
+        q = self._dev(_coords_i32(queries)).reshape(-1, self.dim)
+        m = q.shape[0]
+        if out is None:
+            out = (torch.empty((m, k), dtype=torch.int32, device=self.device),
+                   torch.empty((m, k), dtype=torch.int64, device=self.device))
+        _check_out(out[0], out[1], m, k, self.device)
+        if counts.dtype != torch.int64 or counts.numel() != 3 or counts.device != self.device:
+            raise ValueError("counts must be a (3,) int64 tensor on the forest's device")
+        capi.check(capi.bdl_knn_count(self._h, _ptr(q), m, k, _ptr(out[0]), _ptr(out[1]), _ptr(counts),
+                                      _stream_handle(self.stream)), "bdl_knn_count")
+        return out
+
+    def poll_error(self):
+        """The device error word (0 when no kernel found an index outside its
+        buffers); waits for the forest's stream."""
+        st, bits = capi.bdl_poll_error(self._h, _stream_handle(self.stream))
+        if st not in (capi.BDL_OK, capi.BDL_EINTERNAL):
+            capi.check(st, "bdl_poll_error")
+        return bits
+
     def knn_stats(self, enable=None):
         """enable=True/False switches per-query visit counting on/off (and resets);
         enable=None reads (nodes visited, leaf points examined, queries)."""
@@ -184,6 +245,20 @@ class Forest:
             return tuple(int(x) for x in out)
         capi.check(capi.bdl_knn_stats(self._h, 1 if enable else 0, None), "bdl_knn_stats")
         return None
+
+
+def _check_out(oi, od, m, k, device):
+    """The caller's output buffers of a k-NN call: contiguous (m, k) int32 ids
+    and int64 squared distances on the forest's device (the kernel writes
+    m * k entries of each)."""
+    for t, dt, name in ((oi, torch.int32, "ids"), (od, torch.int64, "d2")):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("out %s must be a tensor" % name)
+        if t.dtype != dt or tuple(t.shape) != (m, k) or not t.is_contiguous():
+            raise ValueError("out %s must be a contiguous (%d, %d) %s tensor, got %s %s" %
+                             (name, m, k, dt, tuple(t.shape), t.dtype))
+        if not t.is_cuda or t.device != torch.device(device):
+            raise ValueError("out %s must be on %s, not %s" % (name, device, t.device))
 
 
 # --- batched forests: one call for many independent forests -----------------
@@ -197,7 +272,7 @@ def _batch_stream(forests, stream):
 def insert_batch(forests, points, stream=None):
     """Insert_L on every forest; points[i] is a device tensor [n_i, dim_i].
     Returns the list of id tensors."""
-    ps = [p.to(torch.int32).contiguous().reshape(-1, f.dim) for f, p in zip(forests, points)]
+    ps = [f._dev(_coords_i32(p)).reshape(-1, f.dim) for f, p in zip(forests, points)]
     ids = [torch.empty(p.shape[0], dtype=torch.int32, device=p.device) for p in ps]
     capi.check(capi.bdl_insert_batch([f._h for f in forests], [_addr(p) for p in ps],
                                      [p.shape[0] for p in ps], [_addr(i) for i in ids],
@@ -207,7 +282,7 @@ def insert_batch(forests, points, stream=None):
 
 def erase_batch(forests, ids, stream=None):
     """Erase_L on every forest; returns the list of counts erased."""
-    ts = [i.to(torch.int32).contiguous().reshape(-1) for i in ids]
+    ts = [f._dev(_ids_i32(i)).reshape(-1) for f, i in zip(forests, ids)]
     st, n = capi.bdl_erase_batch([f._h for f in forests], [_addr(t) for t in ts],
                                  [t.shape[0] for t in ts], _batch_stream(forests, stream))
     capi.check(st, "bdl_erase_batch")
@@ -217,10 +292,13 @@ def erase_batch(forests, ids, stream=None):
 def knn_batch(forests, queries, k, out=None, stream=None):
     """kNN_L on every forest; queries[i] is a device tensor [m_i, dim_i].
     Returns a list of (ids [m_i, k], d2 [m_i, k])."""
-    qs = [q.to(torch.int32).contiguous().reshape(-1, f.dim) for f, q in zip(forests, queries)]
+    qs = [f._dev(_coords_i32(q)).reshape(-1, f.dim) for f, q in zip(forests, queries)]
     if out is None:
         out = [(torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device),
                 torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)) for q in qs]
+    else:
+        for f, q, (oi, od) in zip(forests, qs, out):
+            _check_out(oi, od, q.shape[0], k, f.device)
     capi.check(capi.bdl_knn_batch([f._h for f in forests], [_addr(q) for q in qs],
                                   [q.shape[0] for q in qs], k, [_addr(o[0]) for o in out],
                                   [_addr(o[1]) for o in out], _batch_stream(forests, stream)),
@@ -242,6 +320,9 @@ class KnnPlan:
         if out is None:
             out = [(torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device),
                     torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)) for q in self.queries]
+        else:
+            for f, q, (oi, od) in zip(forests, self.queries, out):
+                _check_out(oi, od, q.shape[0], k, f.device)
         self.out = out
         self.forests = list(forests)
         st, h = capi.bdl_knn_plan_create([f._h for f in forests], [_addr(q) for q in self.queries],
