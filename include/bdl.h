@@ -201,10 +201,16 @@ int bdl_knn_plan_destroy(bdl_knn_plan *plan);
  * Requests take effect in submission order with exactly the results the
  * plain calls give when issued one by one in that order; the server batches
  * them for the device as they arrive (continuous batching):
- *  - consecutive k-NN requests with the same k go out as one k-NN launch;
+ *  - consecutive k-NN requests go out as one k-NN launch: with one k up to
+ *    max_group_queries queries, with different k up to 32,768 queries in all
+ *    (launched with the largest k, each request's rows cut to its own k --
+ *    the k nearest by (d2, id) are the first k of the larger list);
  *  - consecutive inserts go out as one Insert_L of their concatenated points
  *    (same ids, same live set);
- *  - erases run one by one.
+ *  - consecutive erases go out as one Erase_L of all their ids, marked
+ *    request by request in order, so that each request's count is the number
+ *    of its ids that were live after the erases before it (an id named twice
+ *    counts for the first request).
  * A request is admitted -- its device buffers allocated and its input
  * copied in -- only while fewer than max_inflight requests are in flight and
  * their buffers fit in staging_budget_bytes; inputs of later requests and
@@ -247,7 +253,7 @@ typedef struct {
     int32_t serial;             /* 1 = one request at a time, no batching (comparison path) */
     int64_t staging_budget_bytes; /* device bytes of the requests in flight; default 1 GiB */
     int64_t max_group_queries;  /* k-NN queries per launch; default 2^20 */
-    int64_t max_group_points;   /* points per merged insert; default 2^21 */
+    int64_t max_group_points;   /* points per merged insert, ids per merged erase; default 2^21 */
 } bdl_server_config;
 
 /* Fill *cfg with the defaults above. */
@@ -385,6 +391,15 @@ int bdl_profile_read(double *ms_host, int64_t *launches_host, int cap);
  * 4 + 32.  Kernels without a stated figure (k_knn among them: its bytes come
  * from bdl_knn_count) report 0. */
 int bdl_profile_read_bytes(double *ms_host, int64_t *launches_host, double *bytes_host, int cap);
+
+/* The recorded launches since profiling was switched on or last read, in
+ * launch order (a trace, for finding the gaps between kernels): per launch i <
+ * cap its kernel id, the device times of its start and end events in ms from
+ * the first recorded launch's start (launches on several streams share that
+ * origin), and its algorithmic bytes.  *out_n = launches recorded.  Waits
+ * for the events; does not clear the records (bdl_profile_read does). */
+int bdl_profile_timeline(int32_t *kid_host, double *start_ms_host, double *end_ms_host, double *bytes_host,
+                         int cap, int *out_n_host);
 
 /* Kernel ids are 0 .. bdl_kernel_count()-1; bdl_kernel_name gives each one's
  * name (e.g. "k_knn"). */

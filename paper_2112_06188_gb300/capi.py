@@ -22,7 +22,7 @@ SYMBOLS = [
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
     "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
     "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy", "bdl_next_id",
-    "bdl_knn_count", "bdl_poll_error", "bdl_profile_read_bytes",
+    "bdl_knn_count", "bdl_poll_error", "bdl_profile_read_bytes", "bdl_profile_timeline",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -116,6 +116,7 @@ def load(path=None):
         "bdl_knn_count": (i32, [P, P, i64, i32, P, P, P, P]),
         "bdl_poll_error": (i32, [P, P, P]),
         "bdl_profile_read_bytes": (i32, [P, P, P, i32]),
+        "bdl_profile_timeline": (i32, [P, P, P, P, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -350,6 +351,18 @@ def bdl_profile_read_bytes():
     by = (ctypes.c_double * n)()
     check(load().bdl_profile_read_bytes(ms, cnt, by, n), "bdl_profile_read_bytes")
     return {bdl_kernel_name(i): (ms[i], cnt[i], by[i]) for i in range(n) if cnt[i]}
+
+
+def bdl_profile_timeline(cap=1 << 16):
+    """[(kernel name, start ms, end ms, algorithmic bytes)] of the recorded
+    launches in launch order (does not clear the records)."""
+    kid = (ctypes.c_int32 * cap)()
+    a = (ctypes.c_double * cap)()
+    b = (ctypes.c_double * cap)()
+    by = (ctypes.c_double * cap)()
+    n = ctypes.c_int(0)
+    check(load().bdl_profile_timeline(kid, a, b, by, cap, _ref(n)), "bdl_profile_timeline")
+    return [(bdl_kernel_name(kid[i]), a[i], b[i], by[i]) for i in range(min(cap, n.value))]
 
 
 def bdl_kernel_count():

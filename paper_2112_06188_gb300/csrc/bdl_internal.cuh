@@ -406,6 +406,13 @@ constexpr size_t kPinnedErr = 2044;            // where the error word is read b
 constexpr int kBufOutWords = kMaxLevel + 2;    // per forest: buffer size, root live counts, error word
 int smem_subtree_capacity(int dim);
 
+// Erase_L on one forest for several id lists in order (the server's merged
+// erase requests): an id counts for the first list that names it, so
+// counts[r] is what list r would erase in a call of its own after the lists
+// before it.  One bloom build, descent launch and wait for all of them.
+int erase_lists(bdl_forest *f, const std::vector<const int32_t *> &ids, const std::vector<int64_t> &n,
+                int64_t *counts, cudaStream_t s);
+
 // ---- build.cu ----
 struct ClearedSrc {        // a cleared tree whose live points join a new tree
   const int32_t *pts;      // point records
@@ -472,13 +479,14 @@ struct FillSeg {           // `count` work items of one kind
   const unsigned long long *errw;  // append: the forest's device error word; a set word
                                    // sets bit 1 of *flag
 };
-struct MarkSeg {           // one forest's erase batch
+struct MarkSeg {           // one erase list of one forest
   uint32_t *alive;
   int64_t next_id;
   const int32_t *ids;
   int64_t n;
   int32_t *list;           // out: owned ids
   int64_t *count;          // out: how many
+  int64_t *total;          // out: the forest's count over all its lists (may alias count)
 };
 struct TreeSeg {           // one tree: bloom builds, record packing, live refreshes
   const int32_t *pts;

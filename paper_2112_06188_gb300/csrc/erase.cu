@@ -394,7 +394,10 @@ __global__ void k_erase_mark_many(const MarkSeg *segs, const int64_t *pre_warp, 
   const unsigned m = __ballot_sync(0xffffffffu, own);
   if (!m) return;
   unsigned long long base = 0;
-  if (lane == __ffs(m) - 1) base = atomicAdd((unsigned long long *)g.count, (unsigned long long)__popc(m));
+  if (lane == __ffs(m) - 1) {
+    base = atomicAdd((unsigned long long *)g.count, (unsigned long long)__popc(m));
+    if (g.total != g.count) atomicAdd((unsigned long long *)g.total, (unsigned long long)__popc(m));
+  }
   base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
   if (own) g.list[base + __popc(m & ((1u << lane) - 1))] = id;
 }

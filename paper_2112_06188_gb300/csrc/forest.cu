@@ -849,60 +849,95 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
 }
 
 static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s);
+static int finish(bdl_forest *f, cudaStream_t s, int st);
 
-// Erase_L on nf forests: one marking pass (its counts stay on the device),
-// lazily built blooms, one descent launch, the k-NN records' live counts
-// (refreshed, or kept on the descent paths of small batches), one buffer
-// compaction, one host sync for the counts; reinsertion of trees below half
-// then runs for all forests together (Alg. 4).
-static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, const int64_t *n,
-                      int64_t *out_n, cudaStream_t s) {
-  for (int i = 0; i < nf; ++i) {
-    if (out_n) out_n[i] = 0;
-    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
-    if (n[i] < 0) return set_error(BDL_EINVAL, "n < 0");
-    if (n[i] > 0 && !ids[i]) return set_error(BDL_EINVAL, "ids is NULL");
-  }
-  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
-  if (!distinct(F, nf)) return set_error(BDL_EINVAL, "a forest appears twice");
+// One id list of one forest in an erase call.
+struct EraseList {
+  int forest;              // index into the call's forests
+  const int32_t *ids;
+  int64_t n;
+};
+
+// Erase_L on nf distinct forests, each erasing its lists in the order given
+// (one list per forest for the plain calls; the server's merged requests give
+// several): one marking pass per rank of list -- a forest's list r is marked
+// after its list r - 1, so an id counts for the first list that names it --
+// whose counts stay on the device, lazily built blooms, one descent launch,
+// the k-NN records' live counts (refreshed, or kept on the descent paths of
+// small batches), one buffer compaction, one host sync for the counts;
+// reinsertion of trees below half then runs for all forests together
+// (Alg. 4).  out_list[j] receives list j's count.
+static int erase_core(bdl_forest *const *F, int nf, const std::vector<EraseList> &L, int64_t *out_list,
+                      cudaStream_t s) {
+  const size_t nl = L.size();
+  for (size_t j = 0; j < nl; ++j)
+    if (out_list) out_list[j] = 0;
   Temp tmp(F[0], s);
-  // 1. dedup against the live sets
-  std::vector<MarkSeg> mk;
-  std::vector<int> mk_forest;
-  int64_t total = 0;
+  // 1. dedup against the live sets, list rank by list rank
+  std::vector<int64_t> fsum(nf, 0);
+  for (const auto &e : L) fsum[e.forest] += e.n;
+  std::vector<int> fa(nf, -1), act_forest;   // forest -> active index
   for (int i = 0; i < nf; ++i)
-    if (n[i] > 0 && F[i]->next_id > 0) total += n[i], mk_forest.push_back(i);
-  if (mk_forest.empty()) return BDL_OK;
+    if (fsum[i] > 0 && F[i]->next_id > 0) {
+      fa[i] = (int)act_forest.size();
+      act_forest.push_back(i);
+    }
+  if (act_forest.empty()) return BDL_OK;
+  const size_t na = act_forest.size();
+  std::vector<int> use;                      // lists taking part
+  int64_t total = 0;
+  for (size_t j = 0; j < nl; ++j)
+    if (L[j].n > 0 && fa[L[j].forest] >= 0) use.push_back((int)j), total += L[j].n;
+  // device counts: one per list taking part, then one total per active forest
   void *lists = nullptr, *counts = nullptr, *table = nullptr;
   int st = tmp.get((size_t)total * 4, &lists);
-  if (!st) st = tmp.get(mk_forest.size() * 8, &counts);
-  if (!st) st = tmp.get(table_bytes(mk_forest.size(), sizeof(MarkSeg)), &table);
+  if (!st) st = tmp.get((use.size() + na) * 8, &counts);
+  if (!st) st = tmp.get(table_bytes(use.size(), sizeof(MarkSeg)), &table);
   if (st) return st;
+  int64_t *lcount = (int64_t *)counts;                 // [use.size()]
+  int64_t *ftotal = lcount + use.size();               // [na]
+  std::vector<int32_t *> lptr(use.size());
+  std::vector<int> rank(use.size()), seen(nf, 0);
   int64_t off = 0;
-  for (size_t j = 0; j < mk_forest.size(); ++j) {
-    bdl_forest *f = F[mk_forest[j]];
-    MarkSeg g{f->alive, f->next_id, ids[mk_forest[j]], n[mk_forest[j]], (int32_t *)lists + off,
-              (int64_t *)counts + j};
-    off += g.n;
-    mk.push_back(g);
+  int nrank = 0;
+  for (size_t u = 0; u < use.size(); ++u) {
+    const EraseList &e = L[use[u]];
+    lptr[u] = (int32_t *)lists + off;
+    off += e.n;
+    rank[u] = seen[e.forest]++;
+    nrank = std::max(nrank, rank[u] + 1);
   }
-  cudaMemsetAsync(counts, 0, mk.size() * 8, s);
-  st = launch_erase_mark_many(mk, table, s);
+  cudaMemsetAsync(counts, 0, (use.size() + na) * 8, s);
+  for (int r = 0; r < nrank && !st; ++r) {
+    std::vector<MarkSeg> mk;
+    for (size_t u = 0; u < use.size(); ++u) {
+      if (rank[u] != r) continue;
+      const EraseList &e = L[use[u]];
+      bdl_forest *f = F[e.forest];
+      const bool alone = seen[e.forest] == 1;
+      mk.push_back(MarkSeg{f->alive, f->next_id, e.ids, e.n, lptr[u], lcount + u,
+                           alone ? lcount + u : ftotal + fa[e.forest]});
+    }
+    st = launch_erase_mark_many(mk, table, s);   // stream order: the table is reused after the launch read it
+  }
   if (st) return st;
+  // a forest's count on the device: its list's, or the total over its lists
+  std::vector<const int64_t *> ne_dev(na);
+  for (size_t u = 0; u < use.size(); ++u) {
+    const int i = L[use[u]].forest;
+    ne_dev[fa[i]] = seen[i] == 1 ? lcount + u : ftotal + fa[i];
+  }
   // Every forest with a nonempty batch takes part from here on without a wait
   // for the counts: the launches are sized by the batch lengths and read the
   // counts on the device, and a forest whose batch erased nothing is left as
   // it was (its new blooms are skipped on the device and unmarked after the
   // sync below).
-  const int64_t *ne_dev = (const int64_t *)counts;
-  std::vector<int> act(mk.size());   // indices into mk of the forests taking part
-  for (size_t j = 0; j < mk.size(); ++j) act[j] = (int)j;
   // 2. lazily build the bloom filter of every nonempty tree (Sec. V-A)
   std::vector<TreeSeg> blooms;
   std::vector<FillSeg> zeros;
-  std::vector<std::pair<int, Tree *>> fresh;   // (index into mk, tree) of the blooms built here
-  for (int j : act) {
-    bdl_forest *f = F[mk_forest[j]];
+  std::vector<std::pair<int, Tree *>> fresh;   // (active index, tree) of the blooms built here
+  for (size_t a = 0; a < na; ++a) {
+    bdl_forest *f = F[act_forest[a]];
     for (int i = 0; i < kMaxLevel && !st; ++i) {
       Tree *t = f->trees[i];
       if (!t || t->live == 0 || t->bloom) continue;
@@ -914,7 +949,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       t->bloom = t->bloom_room;
       t->bloom_blocks = blocks;
       t->bloom_bytes = (size_t)blocks * 32;
-      fresh.emplace_back(j, t);
+      fresh.emplace_back((int)a, t);
       FillSeg z;                     // zeroed in one launch with the others
       memset(&z, 0, sizeof(z));
       z.kind = kFillZero;
@@ -929,7 +964,7 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
       g.bloom = t->bloom;
       g.blocks = blocks;
       g.seed = f->cfg.hash_seed;
-      g.gate = ne_dev + j;            // built only if the batch erases something
+      g.gate = ne_dev[a];             // built only if the batch erases something
       blooms.push_back(g);
     }
   }
@@ -947,32 +982,32 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
     if (st) return st;
   }
   // 3. probe, descend, tombstone (Alg. 2 on every tree of every forest, one
-  //    launch); a large batch descends in spatial order
-  std::vector<ForestView> views(act.size());
+  //    launch, one job per list); a large list descends in spatial order
+  std::vector<ForestView> views(na);
   std::vector<EraseCall> calls;
   // The packed k-NN records' live counts: a small batch (under 1/128 of the
   // forest) updates them on its descent paths, a larger one has every record
   // refreshed from the nodes afterwards, whichever touches less.
-  std::vector<int> incremental(act.size());
-  for (size_t a = 0; a < act.size(); ++a) {
-    const bdl_forest *f = F[mk_forest[act[a]]];
-    incremental[a] = mk[act[a]].n * 128 < f->live;
-  }
-  for (size_t a = 0; a < act.size(); ++a) {
-    const int j = act[a];
-    bdl_forest *f = F[mk_forest[j]];
+  std::vector<int> incremental(na);
+  for (size_t a = 0; a < na; ++a) {
+    const bdl_forest *f = F[act_forest[a]];
+    incremental[a] = fsum[act_forest[a]] * 128 < f->live;
     views[a] = forest_view(f);
-    const int32_t *order = mk[j].list;
-    const int64_t nj = mk[j].n;       // the owned ids are the first ne_dev[j] of the list
+  }
+  for (size_t u = 0; u < use.size(); ++u) {
+    const int i = L[use[u]].forest, a = fa[i];
+    bdl_forest *f = F[i];
+    const int32_t *order = lptr[u];
+    const int64_t nj = L[use[u]].n;   // the owned ids are the first lcount[u] of the list
     if (nj >= kSortMinQueries) {
       void *sorted = nullptr;
       if (tmp.get(a256((size_t)nj * 4) + query_sort_bytes(nj, f->dim), &sorted) == BDL_OK) {
-        launch_point_sort(f->idtab, mk[j].list, nj, f->dim, (char *)sorted + a256((size_t)nj * 4),
-                          (int32_t *)sorted, s, ne_dev + j);
+        launch_point_sort(f->idtab, lptr[u], nj, f->dim, (char *)sorted + a256((size_t)nj * 4),
+                          (int32_t *)sorted, s, lcount + u);
         order = (const int32_t *)sorted;
       }
     }
-    calls.push_back(EraseCall{&views[a], order, nj, f->cfg.hash_seed, ne_dev + j, incremental[a]});
+    calls.push_back(EraseCall{&views[a], order, nj, f->cfg.hash_seed, lcount + u, incremental[a]});
   }
   {
     void *et = nullptr;
@@ -985,10 +1020,10 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   std::vector<TreeSeg> lives;
   std::vector<BufSeg> bufs;
   void *outs = nullptr;
-  st = tmp.get(act.size() * kBufOutWords * 8, &outs);
+  st = tmp.get(na * kBufOutWords * 8, &outs);
   if (st) return st;
-  for (size_t a = 0; a < act.size(); ++a) {
-    bdl_forest *f = F[mk_forest[act[a]]];
+  for (size_t a = 0; a < na; ++a) {
+    bdl_forest *f = F[act_forest[a]];
     BufSeg b;
     memset(&b, 0, sizeof(b));
     b.buf = f->buf;
@@ -1021,23 +1056,26 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   }
   st = tmp.get(table_bytes(bufs.size(), sizeof(BufSeg)), &bt2);
   if (!st) st = launch_buffer_compact_many(bufs, bt2, s);
-  std::vector<int64_t> ho(act.size() * kBufOutWords), ne(mk.size());
+  std::vector<int64_t> ho(na * kBufOutWords), hc(use.size() + na);
   if (!st) st = cuda_check(cudaMemcpyAsync(ho.data(), outs, ho.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
-  if (!st) st = cuda_check(cudaMemcpyAsync(ne.data(), counts, ne.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st) st = cuda_check(cudaMemcpyAsync(hc.data(), counts, hc.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
   // 5. new counts; trees below half capacity are emptied and their points
   //    reinserted (Alg. 4), all forests' reinsertions built together
+  std::vector<int64_t> ne(na, 0);
+  for (size_t u = 0; u < use.size(); ++u) {
+    if (out_list) out_list[use[u]] = hc[u];
+    ne[fa[L[use[u]].forest]] += hc[u];
+  }
   std::vector<bdl_forest *> touched;
   int64_t dev_err = 0;
-  for (size_t a = 0; a < act.size(); ++a) {
-    const int j = act[a];
-    bdl_forest *f = F[mk_forest[j]];
-    if (out_n) out_n[mk_forest[j]] = ne[j];
-    f->live -= ne[j];
+  for (size_t a = 0; a < na; ++a) {
+    bdl_forest *f = F[act_forest[a]];
+    f->live -= ne[a];
     const int64_t *o = &ho[a * kBufOutWords];
     dev_err |= o[kMaxLevel + 1];
-    if (ne[j] == 0) continue;   // nothing erased: counts and trees as they were
+    if (ne[a] == 0) continue;   // nothing erased: counts and trees as they were
     f->version++;
     if (o[0] != f->nbuf) f->buf_dirty = true;
     f->nbuf = o[0];
@@ -1061,6 +1099,36 @@ static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, c
   st = reinsert_low(touched, s);
   if (st) return st;
   return cuda_check(cudaGetLastError(), "erase");
+}
+
+// Erase_L on nf distinct forests, one id list each.
+static int erase_many(bdl_forest *const *F, int nf, const int32_t *const *ids, const int64_t *n,
+                      int64_t *out_n, cudaStream_t s) {
+  for (int i = 0; i < nf; ++i) {
+    if (out_n) out_n[i] = 0;
+    if (!F[i]) return set_error(BDL_EINVAL, "forest is NULL");
+    if (n[i] < 0) return set_error(BDL_EINVAL, "n < 0");
+    if (n[i] > 0 && !ids[i]) return set_error(BDL_EINVAL, "ids is NULL");
+  }
+  if (!same_device(F, nf)) return set_error(BDL_EINVAL, "forests on different devices");
+  if (!distinct(F, nf)) return set_error(BDL_EINVAL, "a forest appears twice");
+  std::vector<EraseList> L;
+  for (int i = 0; i < nf; ++i) L.push_back(EraseList{i, ids[i], n[i]});
+  return erase_core(F, nf, L, out_n, s);
+}
+
+int erase_lists(bdl_forest *f, const std::vector<const int32_t *> &ids, const std::vector<int64_t> &n,
+                int64_t *counts, cudaStream_t s) {
+  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
+  std::vector<EraseList> L;
+  for (size_t j = 0; j < ids.size(); ++j) {
+    if (counts) counts[j] = 0;
+    if (n[j] < 0) return set_error(BDL_EINVAL, "n < 0");
+    if (n[j] > 0 && !ids[j]) return set_error(BDL_EINVAL, "ids is NULL");
+    L.push_back(EraseList{0, ids[j], n[j]});
+  }
+  DeviceGuard g(f->device);
+  return finish(f, s, erase_core(&f, 1, L, counts, s));
 }
 
 // Alg. 4's rebuild step for the given forests: every tree with fewer live
@@ -1402,6 +1470,26 @@ int bdl_profile_read_bytes(double *ms, int64_t *launches, double *bytes, int cap
     }
   }
   prof_reset();
+  return BDL_OK;
+}
+
+int bdl_profile_timeline(int32_t *kid, double *start_ms, double *end_ms, double *bytes, int cap, int *out_n) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (out_n) *out_n = (int)g_prof.size();
+  const int n = std::min(cap, (int)g_prof.size());
+  for (int i = 0; i < n; ++i) {
+    const ProfRec &r = g_prof[i];
+    int st = cuda_check(cudaEventSynchronize(r.b), "cudaEventSynchronize");
+    if (st) return st;
+    float a = 0, b = 0;
+    st = cuda_check(cudaEventElapsedTime(&a, g_prof[0].a, r.a), "cudaEventElapsedTime");
+    if (!st) st = cuda_check(cudaEventElapsedTime(&b, g_prof[0].a, r.b), "cudaEventElapsedTime");
+    if (st) return st;
+    if (kid) kid[i] = r.kid;
+    if (start_ms) start_ms[i] = a;
+    if (end_ms) end_ms[i] = b;
+    if (bytes) bytes[i] = r.bytes;
+  }
   return BDL_OK;
 }
 

@@ -6,14 +6,22 @@
 // Semantics: requests take effect in submission order, exactly as if each
 // had been issued alone by the plain calls (bdl_insert / bdl_erase /
 // bdl_knn) in that order.  Batching only changes how they are launched:
-//  * a run of consecutive k-NN requests with the same k reads one state of the
-//    forest, so the run goes to the device as one k-NN launch (one job per
-//    request);
+//  * a run of consecutive k-NN requests reads one state of the forest, so the
+//    run goes to the device as one k-NN launch (one job per request); a run
+//    with one k may be as large as max_group_queries, a run of small requests
+//    may mix k (up to kMixQueries queries in all): it is launched with the
+//    largest k and each request's rows are cut to its own k on the way out --
+//    the k nearest by (d2, id) are the first k of the kmax nearest, padding
+//    included;
 //  * a run of consecutive inserts is one Insert_L of the concatenated points:
 //    the ids are the same consecutive ids and the live set afterwards is the
 //    same, so every later answer is the same (k-NN results are exact and
 //    unique under (d2, id));
-//  * erases run one by one (each reports its own count).
+//  * a run of consecutive erases is one Erase_L of all their ids, whose
+//    marking pass takes the requests' lists in order, so that an id counts for
+//    the first request that names it: each request's count is the one it gets
+//    when the erases run one after another, and the live set afterwards is
+//    the same.
 //
 // Three host threads move requests through three CUDA streams:
 //   admission  -- takes submitted requests in order while the number in flight
@@ -32,6 +40,7 @@
 // one-request-at-a-time path, for comparison.
 #include "bdl_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -58,9 +67,11 @@ struct Req {
 struct Group {
   std::vector<Req *> reqs;
   cudaEvent_t ev_out = nullptr;     // outputs copied back
-  void *merged = nullptr;           // merged insert input
+  void *merged = nullptr;           // merged insert input, or a mixed-k k-NN run's outputs
   size_t merged_bytes = 0;
 };
+
+constexpr int64_t kMixQueries = 1 << 15;   // a k-NN run that mixes k stays this small
 
 }  // namespace
 }  // namespace bdl
@@ -165,14 +176,18 @@ Group *form_group(bdl_server *S) {
   g->reqs.push_back(first);
   if (S->cfg.serial || first->res.status) return g;
   const int kind = first->r.kind;
-  if (kind == BDL_REQ_ERASE) return g;
   int64_t total = first->r.n;
   const int64_t cap = kind == BDL_REQ_KNN ? S->cfg.max_group_queries : S->cfg.max_group_points;
+  bool mixed = false;
   while (!S->admitted.empty()) {
     Req *q = S->admitted.front();
     if (q->res.status || q->r.kind != kind) break;
-    if (kind == BDL_REQ_KNN && q->r.k != first->r.k) break;
     if (total + q->r.n > cap) break;
+    if (kind == BDL_REQ_KNN) {
+      const bool mx = mixed || q->r.k != first->r.k;
+      if (mx && total + q->r.n > kMixQueries) break;
+      mixed = mx;
+    }
     total += q->r.n;
     g->reqs.push_back(q);
     S->admitted.pop_front();
@@ -227,6 +242,94 @@ int run_insert(bdl_server *S, Group *g) {
   return BDL_OK;
 }
 
+// A run of erases: one Erase_L over the requests' lists in order.
+void run_erase(bdl_server *S, Group *g) {
+  std::vector<const int32_t *> ids;
+  std::vector<int64_t> n, cnt(g->reqs.size(), 0);
+  for (Req *q : g->reqs) {
+    ids.push_back((const int32_t *)q->d_in);
+    n.push_back(q->r.n);
+  }
+  const int st = erase_lists(S->f, ids, n, cnt.data(), S->s_exec);
+  for (size_t j = 0; j < g->reqs.size(); ++j) {
+    g->reqs[j]->res.status = st;
+    g->reqs[j]->res.n_done = cnt[j];
+  }
+}
+
+// A run of k-NN requests: one launch.  Same k: each request's rows go to its
+// own device buffer.  Mixed k: one launch with the largest k into a group
+// buffer, each request's rows cut to its k by 2-D copies; without room for
+// that buffer, each request runs by itself (same rows).
+void run_knn(bdl_server *S, Group *g) {
+  const size_t nr = g->reqs.size();
+  int kmax = 0;
+  int64_t rows = 0;
+  bool mixed = false;
+  for (Req *q : g->reqs) {
+    kmax = std::max(kmax, (int)q->r.k);
+    mixed = mixed || q->r.k != g->reqs[0]->r.k;
+    rows += q->r.n;
+  }
+  std::vector<bdl_forest *> F(nr, S->f);
+  std::vector<const int32_t *> qv(nr);
+  std::vector<int64_t> mv(nr);
+  std::vector<int32_t *> oi(nr);
+  std::vector<int64_t *> od(nr);
+  if (mixed && rows > 0) {
+    g->merged_bytes = (size_t)rows * kmax * 12;
+    if (cudaMallocFromPoolAsync(&g->merged, g->merged_bytes, S->pool, S->s_exec) != cudaSuccess) {
+      cudaGetLastError();
+      g->merged = nullptr;
+    }
+  }
+  int64_t row = 0;
+  for (size_t j = 0; j < nr; ++j) {
+    Req *q = g->reqs[j];
+    qv[j] = (const int32_t *)q->d_in;
+    mv[j] = q->r.n;
+    if (g->merged) {     // [rows][kmax] d2, then [rows][kmax] ids
+      od[j] = (int64_t *)g->merged + row * kmax;
+      oi[j] = (int32_t *)((int64_t *)g->merged + rows * kmax) + row * kmax;
+    } else {
+      od[j] = (int64_t *)q->d_out;
+      oi[j] = (int32_t *)((char *)q->d_out + (size_t)q->r.n * q->r.k * 8);
+    }
+    row += q->r.n;
+  }
+  std::vector<int> st(nr, BDL_OK);
+  if (!mixed || g->merged) {
+    const int s1 = bdl_knn_batch(F.data(), (int)nr, qv.data(), mv.data(), kmax, oi.data(), od.data(), S->s_exec);
+    std::fill(st.begin(), st.end(), s1);
+  } else {
+    for (size_t j = 0; j < nr; ++j)
+      st[j] = bdl_knn(S->f, qv[j], mv[j], g->reqs[j]->r.k, oi[j], od[j], S->s_exec);
+  }
+  cudaEvent_t ev = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    ev = get_event(S);
+  }
+  cudaEventRecord(ev, S->s_exec);
+  cudaStreamWaitEvent(S->s_out, ev, 0);
+  for (size_t j = 0; j < nr; ++j) {
+    Req *q = g->reqs[j];
+    q->res.status = st[j];
+    q->res.n_done = st[j] ? 0 : q->r.n;
+    if (st[j] || q->r.n == 0) continue;
+    const int k = q->r.k;
+    const int w = g->merged ? kmax : k;     // row width on the device
+    if (q->r.out_d2_host)
+      cudaMemcpy2DAsync(q->r.out_d2_host, (size_t)k * 8, od[j], (size_t)w * 8, (size_t)k * 8, (size_t)q->r.n,
+                        cudaMemcpyDeviceToHost, S->s_out);
+    if (q->r.out_ids_host)
+      cudaMemcpy2DAsync(q->r.out_ids_host, (size_t)k * 4, oi[j], (size_t)w * 4, (size_t)k * 4, (size_t)q->r.n,
+                        cudaMemcpyDeviceToHost, S->s_out);
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->spare_events.push_back(ev);   // recorded already; reuse after the group completes is safe
+}
+
 void run_group(bdl_server *S, Group *g) {
   for (Req *q : g->reqs) cudaStreamWaitEvent(S->s_exec, q->ev_in, 0);
   const double t = ms_since(S);
@@ -241,46 +344,9 @@ void run_group(bdl_server *S, Group *g) {
   } else if (first->r.kind == BDL_REQ_INSERT) {
     run_insert(S, g);
   } else if (first->r.kind == BDL_REQ_ERASE) {
-    int64_t ne = 0;
-    first->res.status = bdl_erase(S->f, (const int32_t *)first->d_in, first->r.n, &ne, S->s_exec);
-    first->res.n_done = ne;
+    run_erase(S, g);
   } else {
-    const size_t nf = g->reqs.size();
-    const int k = first->r.k;
-    std::vector<bdl_forest *> F(nf, S->f);
-    std::vector<const int32_t *> qv(nf);
-    std::vector<int64_t> mv(nf);
-    std::vector<int32_t *> oi(nf);
-    std::vector<int64_t *> od(nf);
-    for (size_t j = 0; j < nf; ++j) {
-      Req *q = g->reqs[j];
-      qv[j] = (const int32_t *)q->d_in;
-      mv[j] = q->r.n;
-      od[j] = (int64_t *)q->d_out;
-      oi[j] = (int32_t *)((char *)q->d_out + (size_t)q->r.n * k * 8);
-    }
-    const int st = bdl_knn_batch(F.data(), (int)nf, qv.data(), mv.data(), k, oi.data(), od.data(),
-                                 S->s_exec);
-    cudaEvent_t ev = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      ev = get_event(S);
-    }
-    cudaEventRecord(ev, S->s_exec);
-    cudaStreamWaitEvent(S->s_out, ev, 0);
-    for (Req *q : g->reqs) {
-      q->res.status = st;
-      q->res.n_done = st ? 0 : q->r.n;
-      if (st || q->r.n == 0) continue;
-      const size_t nk = (size_t)q->r.n * k;
-      if (q->r.out_d2_host)
-        cudaMemcpyAsync(q->r.out_d2_host, q->d_out, nk * 8, cudaMemcpyDeviceToHost, S->s_out);
-      if (q->r.out_ids_host)
-        cudaMemcpyAsync(q->r.out_ids_host, (char *)q->d_out + nk * 8, nk * 4, cudaMemcpyDeviceToHost,
-                        S->s_out);
-    }
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->spare_events.push_back(ev);   // recorded already; reuse after the group completes is safe
+    run_knn(S, g);
   }
   // buffers are released on the copy-out stream after everything that reads them
   cudaEvent_t ev = nullptr;

@@ -127,11 +127,53 @@ def test_burst_is_batched_and_equal():
     ref = alone(dim, initial, reqs)
     res, groups, _ = in_mix(dim, initial, reqs, paced=False)
     compare(reqs, ref, res)
-    # at least one device group per run of same-kind requests (erases: one each),
-    # and fewer groups than requests once runs merge
+    # at least one device group per run of same-kind requests, and fewer groups
+    # than requests once runs merge
     kinds = [k for _, k, _, _ in reqs]
-    runs = 1 + sum(1 for a, b in zip(kinds, kinds[1:]) if a != b or a == "erase")
+    runs = 1 + sum(1 for a, b in zip(kinds, kinds[1:]) if a != b)
     assert runs <= groups < len(reqs)
+
+
+def test_erase_runs_merge_with_exact_counts():
+    """A burst of erases that overlap (the same id in several requests,
+    repeated inside one request, dead, negative and never-inserted ids) runs
+    as merged Erase_L calls; every request's count is the one it gets when
+    the erases run one after another, and the forest ends the same."""
+    dim = 3
+    n0 = 40_000
+    initial = inputs.uniform_points(n0, dim, seed=11)
+    rng = np.random.default_rng(12)
+    reqs = []
+    for j in range(12):
+        ids = rng.integers(0, n0, size=int(rng.integers(100, 3_000))).astype(np.int32)
+        if j % 3 == 0 and reqs:
+            ids = np.concatenate([ids, reqs[-1][2][:50]])          # overlaps the previous request
+        ids = np.concatenate([ids, ids[:10], np.array([-1, n0 + 5, 2**31 - 1], np.int32)])
+        reqs.append((0.0, "erase", ids.astype(np.int32), 0))
+    q = inputs.uniform_points(2_000, dim, seed=13)
+    reqs.append((0.0, "knn", q, 9))
+    ref = alone(dim, initial, reqs)
+    res, groups, _ = in_mix(dim, initial, reqs, paced=False)
+    compare(reqs, ref, res)
+    assert groups < len(reqs)
+    counts = [r["n_done"] for r in res[:-1]]
+    live = inputs.LiveSet(dim)
+    live.insert(initial)
+    assert counts == [live.erase(p) for _, _, p, _ in reqs[:-1]]
+
+
+def test_knn_runs_mix_k():
+    """Small k-NN requests with k in {1, 5, 10, 32} submitted together share
+    launches; each request's rows are its own k's rows."""
+    dim = 2
+    initial = inputs.uniform_points(30_000, dim, seed=21)
+    rng = np.random.default_rng(22)
+    reqs = [(0.0, "knn", inputs.uniform_points(int(rng.integers(1, 2_000)), dim, seed=30 + j),
+             int(rng.choice([1, 5, 10, 32]))) for j in range(40)]
+    ref = alone(dim, initial, reqs)
+    res, groups, _ = in_mix(dim, initial, reqs, paced=False)
+    compare(reqs, ref, res)
+    assert groups < len(reqs) // 2
 
 
 def test_serial_mode_and_small_budget():
