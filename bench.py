@@ -978,7 +978,7 @@ def recorded_traffic(kernel, leaf):
     return int(fields["dram_bytes_per_launch"])
 
 
-ROOFLINE_KERNELS = ("k_knn", "k_subtree", "k_level_partition", "k_erase_locate", "k_bloom_build")
+ROOFLINE_KERNELS = ("k_knn", "k_subtree", "k_build_levels", "k_erase_locate", "k_bloom_build")
 
 
 def rec_bytes(dim):

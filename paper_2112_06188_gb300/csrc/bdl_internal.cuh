@@ -31,15 +31,9 @@ extern std::atomic<uint64_t> g_launches;
 // implies, computed from the sizes the host knows at launch; 0 where not
 // stated).
 enum KernelId : int {
-  kK_gather_cleared,
-  kK_gather_pool,
-  kK_level_hist,
-  kK_level_bucket,
-  kK_level_collect,
-  kK_level_select,
-  kK_level_partition,
+  kK_build_levels,
   kK_subtree,
-  kK_box_up,
+  kK_build_finish,
   kK_sort_small,
   kK_erase_mark,
   kK_bloom_build,
@@ -299,7 +293,42 @@ enum : unsigned long long {
   kErrPartition = 8,   // partition destination outside its segment
   kErrGather = 16,     // gather destination outside its tree
   kErrLiveCount = 32,  // a packed record's live count differs from its node's (debug check)
+  kErrBarrier = 64,    // a grid barrier of a cooperative kernel waited too long and gave up
 };
+
+// Grid-wide barrier of a cooperative launch (every block resident at once):
+// bar[0] counts the blocks that arrived, bar[1] is the generation the last
+// arrival advances.  Writes before the barrier are visible after it (block
+// barrier, then a device-scope fence by the arriving thread, cumulative over
+// the block's writes, and another after the wait).  The wait is bounded:
+// after kBarrierPolls polls (about a second) the block sets kErrBarrier in
+// *err and goes on, so a lost block never hangs the GPU; the call then fails
+// with BDL_EINTERNAL.
+constexpr unsigned kBarrierPolls = 1u << 24;
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned long long *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned polls = 0;
+      while (*gen == g) {
+        if (++polls > kBarrierPolls) {
+          atomicOr(err, kErrBarrier);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
 
 // ---------------------------------------------------------------------------
 // host-side state

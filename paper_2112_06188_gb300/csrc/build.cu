@@ -23,6 +23,7 @@
 #include "bdl_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace bdl {
 
@@ -105,11 +106,13 @@ struct LvParams {              // one global level
   const int64_t *act_tile;     // [nact + 1] tile prefix
 };
 
-__device__ __forceinline__ LvTree tree_by_tile(const LvParams &P, int64_t b) {
+// The level's tree that owns tile b / segment g (a reference into the
+// level's descriptor in device memory: fields are loaded where used).
+__device__ __forceinline__ const LvTree &tree_by_tile(const LvParams &P, int64_t b) {
   return P.nact == 1 ? P.one : P.lt[find_le(P.act_tile, P.nact, b)];
 }
 
-__device__ __forceinline__ LvTree tree_by_seg(const LvParams &P, int64_t g) {
+__device__ __forceinline__ const LvTree &tree_by_seg(const LvParams &P, int64_t g) {
   return P.nact == 1 ? P.one : P.lt[find_le(P.act_seg, P.nact, g)];
 }
 
@@ -134,10 +137,12 @@ __device__ __forceinline__ int32_t pool_id(const int32_t *buf, int64_t nbuf, con
   return arr ? arr[k - nbuf] : (int32_t)(first + (k - nbuf));
 }
 
-__global__ void k_gather_cleared(const GatherParams P) {
+// Records [b * blockDim.x, (b + 1) * blockDim.x) of the cleared sources: the
+// live ones are appended to their new tree's staging range (one atomic per
+// block and tree).
+__device__ void gather_cleared(const GatherParams &P, int64_t b) {
   __shared__ int wsum[32];
   __shared__ unsigned long long sbase;
-  int b = blockIdx.x;
   const int src = find_le(P.cl_blk, P.nsrc, b);
   const DCleared C = P.cl[src];
   int64_t p = (int64_t)(b - P.cl_blk[src]) * blockDim.x + threadIdx.x;
@@ -169,9 +174,8 @@ __global__ void k_gather_cleared(const GatherParams P) {
   P.stg[P.dim * P.S + dst] = id;
 }
 
-__global__ void k_gather_pool(const GatherParams P, int64_t total) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= total) return;
+// Pool entry k of the new trees (the batch's points, by id).
+__device__ void gather_pool(const GatherParams &P, int64_t k) {
   const int j = find_le(P.pool_off, P.ntrees, k);
   const DTree &T = P.tree[j];
   const int64_t i = k - P.pool_off[j];
@@ -203,10 +207,9 @@ __device__ __forceinline__ TileSegs tile_segs(const LvParams &P, const LvTree &T
   return g;
 }
 
-__global__ void k_level_hist(const LvParams P) {
-  __shared__ uint32_t h[2][kHistBins];
-  int b = blockIdx.x;
-  const LvTree T = tree_by_tile(P, b);
+// Tile b of the level: 11-bit histogram of the split coordinate, per segment.
+__device__ void level_hist(const LvParams &P, int64_t b, uint32_t (*h)[kHistBins]) {
+  const LvTree &T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -230,18 +233,15 @@ __global__ void k_level_hist(const LvParams P) {
 // One warp per segment: the bucket holding the median (rank ceil(m/2)).
 // Each lane sums a contiguous run of 64 bins (independent loads), a warp scan
 // of the run sums finds the run holding the rank, and that lane walks it.
-__global__ void k_level_bucket(const LvParams P, int64_t nseg) {
-  int64_t gs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gs >= nseg) return;
-  const int lane = threadIdx.x & 31;
+__device__ void level_bucket(const LvParams &P, int64_t gs, int lane) {
   constexpr int kRun = kHistBins / 32;
-  const LvTree T = tree_by_seg(P, gs);
+  const LvTree &T = tree_by_seg(P, gs);
   int64_t st, sz;
   seg_range(T.s, T.t, gs - T.seg_off, st, sz);
   const uint32_t r = (uint32_t)((sz + 1) >> 1);
   const uint4 *run = reinterpret_cast<const uint4 *>(P.hist + gs * kHistBins + lane * kRun);
   uint32_t sum = 0;
-#pragma unroll
+#pragma unroll 4
   for (int j = 0; j < kRun / 4; ++j) {
     const uint4 v = run[j];
     sum += v.x + v.y + v.z + v.w;
@@ -279,11 +279,10 @@ __global__ void k_level_bucket(const LvParams P, int64_t nseg) {
 
 // Gather the (low coordinate bits, id) keys of every record in its segment's
 // median bucket, at the segment's own range of the candidate array.
-__global__ void k_level_collect(const LvParams P) {
+__device__ void level_collect(const LvParams &P, int64_t b) {
   __shared__ unsigned cnt[2];
   __shared__ unsigned long long basev[2];
-  int b = blockIdx.x;
-  const LvTree T = tree_by_tile(P, b);
+  const LvTree &T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -317,17 +316,14 @@ __global__ void k_level_collect(const LvParams P) {
 
 // One CTA per segment: exact select of the median among its bucket's keys
 // (8-bit digits over the 40-bit candidate key), then the node is written.
-__global__ void k_level_select(const LvParams P, int64_t nseg) {
+__device__ void level_select(const LvParams &P, int64_t gs, uint64_t *keys) {
   __shared__ uint32_t hist[256];
   __shared__ uint64_t s_pre;
   __shared__ int64_t s_rank;
   __shared__ uint32_t s_cnt;
   __shared__ uint64_t s_found;
-  __shared__ uint32_t s_wsum[8];
-  __shared__ uint64_t keys[2048];
-  int64_t gs = blockIdx.x;
-  if (gs >= nseg) return;
-  const LvTree T = tree_by_seg(P, gs);
+  __shared__ uint32_t s_wsum[32];
+  const LvTree &T = tree_by_seg(P, gs);
   int64_t idx = gs - T.seg_off;
   int64_t st, sz;
   seg_range(T.s, T.t, idx, st, sz);
@@ -420,15 +416,13 @@ __device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, 
 // K2: partition every tile's records around their segment's median into the
 // other staging buffer.  Left records of a segment go to [st, st+ceil(m/2)),
 // right ones after; each CTA reserves its ranges with one atomic per class.
-__global__ void k_level_partition(const LvParams P) {
+__device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long cbase[4];
-  __shared__ int32_t stage[4096];          // one array of the tile, in output order
   __shared__ int64_t gdst[4];              // global start of each class's run
   __shared__ int coff[5];                  // start of each class's run in `stage`
   __shared__ int cok[4];
-  int b = blockIdx.x;
-  const LvTree T = tree_by_tile(P, b);
+  const LvTree &T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   const SegState *s0 = &P.seg[T.seg_off + g.idx0];
   uint64_t med0 = s0[0].median, med1 = g.sz1 ? s0[1].median : 0;
@@ -511,6 +505,71 @@ __global__ void k_level_partition(const LvParams P) {
       if (cok[k]) y[gdst[k] + (i - coff[k])] = stage[i];
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The gather and every global level of a build in one cooperative launch:
+// each phase is a grid-stride loop over its work items (cleared-record
+// blocks, pool entries, tiles, segments), and a grid barrier separates the
+// phases, instead of one launch per phase and level.
+// ---------------------------------------------------------------------------
+
+constexpr int kCoopThreads = 512;   // = tile / kItems for 4096-record tiles
+
+struct LevelWork {                  // one global level, in device memory
+  LvParams P;
+  int64_t ntile, nseg;
+};
+
+struct LevelsParams {
+  GatherParams G;
+  int64_t cl_blocks;                // cleared sources, in blocks of kCoopThreads records
+  int64_t pool_total;               // pool entries
+  const LevelWork *lv;              // [nlev]
+  int nlev;
+  unsigned *bar;                    // grid barrier state (2 words, zeroed)
+  unsigned long long *err;          // where a barrier that gave up is recorded
+};
+
+__global__ void __launch_bounds__(kCoopThreads, 2) k_build_levels(const LevelsParams B) {
+  // one shared buffer for the phases' big arrays (histograms, candidate keys,
+  // the partition's staging), 16 KB
+  __shared__ __align__(16) uint32_t s_big[2 * kHistBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t b = blockIdx.x; b < B.cl_blocks; b += gridDim.x) {
+    gather_cleared(B.G, b);
+    __syncthreads();
+  }
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < B.pool_total;
+       k += (int64_t)gridDim.x * blockDim.x)
+    gather_pool(B.G, k);
+  for (int it = 0; it < B.nlev; ++it) {
+    const LevelWork &W = B.lv[it];
+    const LvParams &P = W.P;
+    grid_barrier(B.bar, B.err);
+    for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
+      level_hist(P, b, reinterpret_cast<uint32_t (*)[kHistBins]>(s_big));
+      __syncthreads();
+    }
+    grid_barrier(B.bar, B.err);
+    for (int64_t gs = (int64_t)blockIdx.x * nwarps + warp; gs < W.nseg; gs += (int64_t)gridDim.x * nwarps)
+      level_bucket(P, gs, lane);
+    grid_barrier(B.bar, B.err);
+    for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
+      level_collect(P, b);
+      __syncthreads();
+    }
+    grid_barrier(B.bar, B.err);
+    for (int64_t gs = blockIdx.x; gs < W.nseg; gs += gridDim.x) {
+      level_select(P, gs, reinterpret_cast<uint64_t *>(s_big));
+      __syncthreads();
+    }
+    grid_barrier(B.bar, B.err);
+    for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
+      level_partition(P, b, reinterpret_cast<int32_t *>(s_big));
+      __syncthreads();
+    }
   }
 }
 
@@ -861,29 +920,46 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// K4: boxes and live counts of the global-level nodes, one depth per launch
+// K4: boxes and live counts of the global-level nodes, deepest level first,
+// in one cooperative launch (a grid barrier between depths)
 // ---------------------------------------------------------------------------
 
-struct BoxParams {
-  int nact, dim, t;
-  const DTree *tree;
-  const int32_t *act;          // [nact] trees with global levels below depth t
+struct BoxWork {               // the nodes of one depth t of the trees with global levels below t
+  int nact, t;
+  const int32_t *act;          // [nact] trees
   const int64_t *node;         // [nact + 1] prefix of 2^t nodes per tree
+  int64_t total;
 };
 
-__global__ void k_box_up(const BoxParams P) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.node[P.nact]) return;
-  const int j = find_le(P.node, P.nact, g);
-  const DTree &D = P.tree[P.act[j]];
+struct FinishParams {
+  int dim, nlev;
+  const DTree *tree;
+  const BoxWork *bw;           // [nlev], by depth
+  unsigned *bar;
+  unsigned long long *err;
+};
+
+__device__ void box_up(const FinishParams &F, const BoxWork &W, int64_t g) {
+  const int j = find_le(W.node, W.nact, g);
+  const DTree &D = F.tree[W.act[j]];
   const NodeOut o = D.out;
-  int l = D.h + 1, t = P.t, dim = P.dim;
-  int64_t i = g - P.node[j];
-  int64_t v = veb_slot(l, t, i), vl = veb_slot(l, t + 1, 2 * i), vr = veb_slot(l, t + 1, 2 * i + 1);
+  const int l = D.h + 1, t = W.t, dim = F.dim;
+  const int64_t i = g - W.node[j];
+  const int64_t v = veb_slot(l, t, i), vl = veb_slot(l, t + 1, 2 * i), vr = veb_slot(l, t + 1, 2 * i + 1);
   o.live[v] = o.live[vl] + o.live[vr];
   for (int c = 0; c < dim; ++c) {
     o.box[v * 2 * dim + c] = min(o.box[vl * 2 * dim + c], o.box[vr * 2 * dim + c]);
     o.box[v * 2 * dim + dim + c] = max(o.box[vl * 2 * dim + dim + c], o.box[vr * 2 * dim + dim + c]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_build_finish(const FinishParams F) {
+  for (int t = F.nlev - 1; t >= 0; --t) {
+    const BoxWork &W = F.bw[t];
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < W.total;
+         g += (int64_t)gridDim.x * blockDim.x)
+      box_up(F, W, g);
+    if (t > 0) grid_barrier(F.bar, F.err);
   }
 }
 
@@ -913,6 +989,31 @@ __global__ void k_sort_small(int32_t *ids, int n, int np2) {
 }
 
 constexpr size_t kSubtreeSmemMax = 212 * 1024;   // dynamic part; static part ~6 KB
+
+// Blocks of a cooperative launch of `fn` with `threads` threads: every block
+// that fits on the device at once (SMs x resident blocks per SM), cached per
+// kernel and device.
+int coop_grid(const void *fn, int threads, int *out) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void *, int>, int>> cache;
+  int dev = 0;
+  int st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto &c : cache)
+    if (c.first.first == fn && c.first.second == dev) {
+      *out = c.second;
+      return BDL_OK;
+    }
+  int sms = 0, per = 0;
+  st = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+  if (!st) st = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0), "occupancy");
+  if (st) return st;
+  if (per < 1) return set_error(BDL_EINTERNAL, "cooperative kernel does not fit on an SM");
+  *out = sms * per;
+  cache.push_back({{fn, dev}, *out});
+  return BDL_OK;
+}
 
 size_t subtree_smem_bytes(int dim, int cap) {
   return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap;
@@ -1004,7 +1105,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     pool_off[j + 1] = pool_off[j] + (b.s - b.from_cleared);
     sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << b.g);
   }
-  const int TB = 256;
+  const int TB = kCoopThreads;   // cleared records per gather work item
   std::vector<DCleared> dc(cl.size());
   std::vector<int64_t> cl_blk(cl.size() + 1, 0);
   for (size_t i = 0; i < cl.size(); ++i) {
@@ -1071,13 +1172,18 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     pack_nodes_entries(trees, dim, pk_segs, pk_pre);
   }
   const size_t o_pk = img.put(pk_segs), o_pkpre = img.put(pk_pre);
+  // per-level descriptors of the fused kernels: placeholders here, filled in
+  // once the device addresses they hold are known
+  const size_t o_lw = img.put(std::vector<LevelWork>(gmax)), o_bw = img.put(std::vector<BoxWork>(gmax));
 
   // ---- one device block: scratch + plan ----
   const size_t stg_bytes = align256((size_t)(dim + 1) * S * 4);
   const size_t cand_bytes = gmax ? align256((size_t)S * 8) : 0;
   const size_t hist_bytes = align256((size_t)nseg_max * kHistBins * 4);
   const size_t seg_bytes = align256((size_t)nseg_max * sizeof(SegState));
-  const size_t cursor_bytes = align256((size_t)ntree * 8);
+  // per-tree gather cursors, then (at the next 256-byte boundary) the two
+  // fused kernels' grid-barrier words
+  const size_t cursor_bytes = align256((size_t)ntree * 8) + 256;
   const size_t plan_bytes = align256(img.bytes.size());
   const size_t total = 2 * stg_bytes + cand_bytes + hist_bytes + seg_bytes + cursor_bytes + plan_bytes;
   void *block = nullptr;
@@ -1092,80 +1198,96 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   uint32_t *hist = (uint32_t *)p; p += hist_bytes;   // zeroed here, then by each level's
   unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;   // bucket pass
   unsigned char *plan = p;
+  unsigned *bar = (unsigned *)((unsigned char *)cursor + align256((size_t)ntree * 8));   // [0..1] levels, [2..3] boxes
+  const DTree *d_tree = (const DTree *)(plan + o_dt);
+  const int32_t *d_act = (const int32_t *)(plan + o_act);
+  const int64_t *d_pre = (const int64_t *)(plan + o_pre);
+
+  // ---- the fused kernels' per-level descriptors, with device addresses ----
+  GatherParams G;
+  G.nsrc = (int)cl.size();
+  G.ntrees = ntree;
+  G.dim = dim;
+  G.S = S;
+  G.stg = stg[0];
+  G.cursor = cursor;
+  G.tree = d_tree;
+  G.cl = (const DCleared *)(plan + o_dc);
+  G.cl_blk = (const int64_t *)(plan + o_clb);
+  G.pool_off = (const int64_t *)(plan + o_pool);
+  double lv_bytes = 0;
+  {
+    LevelWork *lw = (LevelWork *)(img.bytes.data() + o_lw);
+    BoxWork *bw = (BoxWork *)(img.bytes.data() + o_bw);
+    for (int it = 0; it < gmax; ++it) {
+      const LevelHost &L = lv[it];
+      LevelWork W;
+      memset(&W, 0, sizeof(W));
+      LvParams &P = W.P;
+      P.nact = L.nact;
+      P.dim = dim;
+      P.tile = tile;
+      P.it = it;
+      P.S = S;
+      P.src = stg[it & 1];
+      P.dst = stg[(it & 1) ^ 1];
+      P.hist = hist;
+      P.seg = seg;
+      P.cand = cand;
+      P.one = lt_all[L.lt];
+      P.lt = (const LvTree *)(plan + o_lt) + L.lt;
+      P.act_seg = d_pre + L.seg;
+      P.act_tile = d_pre + L.tile;
+      W.ntile = L.ntile;
+      W.nseg = L.nseg;
+      memcpy(lw + it, &W, sizeof(W));
+      BoxWork B{L.nact, it, d_act + L.act, d_pre + L.node, L.nseg};
+      memcpy(bw + it, &B, sizeof(B));
+      // algorithmic bytes per record of the level: the split coordinate (4)
+      // for the histogram and for the candidate gather, the record (d + 1
+      // words) read and written by the partition
+      lv_bytes += (double)L.recs * (8.0 + 8.0 * (dim + 1));
+    }
+  }
   st = h2d(plan, img.bytes.data(), img.bytes.size(), s);
   if (!st) st = cuda_check(cudaMemsetAsync(hist, 0, hist_bytes + cursor_bytes, s), "memset");
   if (st) {
     dev_free(af, block, total, s);
     return st;
   }
-  const DTree *d_tree = (const DTree *)(plan + o_dt);
-  const int32_t *d_act = (const int32_t *)(plan + o_act);
-  const int64_t *d_pre = (const int64_t *)(plan + o_pre);
+  auto coop = [&](const void *fn, int threads, void **args, int kid, double bytes) {
+    int g = 0;
+    int e = coop_grid(fn, threads, &g);
+    if (e) return e;
+    KScope ks_(kid, s, bytes);
+    return cuda_check(cudaLaunchCooperativeKernel(fn, dim3((unsigned)g), dim3((unsigned)threads), args, 0, s),
+                      "cooperative build kernel");
+  };
 
-  // ---- K5 gather ----
-  {
-    GatherParams G;
-    G.nsrc = (int)cl.size();
-    G.ntrees = ntree;
-    G.dim = dim;
-    G.S = S;
-    G.stg = stg[0];
-    G.cursor = cursor;
-    G.tree = d_tree;
-    G.cl = (const DCleared *)(plan + o_dc);
-    G.cl_blk = (const int64_t *)(plan + o_clb);
-    G.pool_off = (const int64_t *)(plan + o_pool);
-    // algorithmic bytes: every cleared record read, every live one written
-    // to staging (d + 1 words); a pool entry's coordinates gathered from the
-    // id table and written
+  // ---- gather (K5) and the global levels (K1/K2), one cooperative launch ----
+  if (cl_blk.back() || pool_off.back() || gmax) {
+    // algorithmic bytes of the gather: every cleared record read, every live
+    // one written to staging (d + 1 words); a pool entry's coordinates
+    // gathered from the id table and written
     double cl_read = 0, cl_live = 0;
     for (auto &c : cl) cl_read += (double)c.size;
     for (auto &b : bt) cl_live += (double)b.from_cleared;
     const double rin = 4.0 * rec_ints(dim), rst = 4.0 * (dim + 1);
-    if (cl_blk.back()) {
-      KScope ks_(kK_gather_cleared, s, cl_read * rin + cl_live * rst);
-      k_gather_cleared<<<(unsigned)cl_blk.back(), TB, 0, s>>>(G);
-    }
-    if (pool_off.back()) {
-      KScope ks_(kK_gather_pool, s, (double)pool_off.back() * (4.0 * dim + rst));
-      k_gather_pool<<<(unsigned)ceil_div(pool_off.back(), 256), 256, 0, s>>>(G, pool_off.back());
-    }
-  }
-
-  // ---- global levels ----
-  for (int it = 0; it < gmax; ++it) {
-    const LevelHost &L = lv[it];
-    LvParams P;
-    P.nact = L.nact;
-    P.dim = dim;
-    P.tile = tile;
-    P.it = it;
-    P.S = S;
-    P.src = stg[it & 1];
-    P.dst = stg[(it & 1) ^ 1];
-    P.hist = hist;
-    P.seg = seg;
-    P.cand = cand;
-    P.one = lt_all[L.lt];
-    P.lt = (const LvTree *)(plan + o_lt) + L.lt;
-    P.act_seg = d_pre + L.seg;
-    P.act_tile = d_pre + L.tile;
-    // algorithmic bytes per record of the level: the split coordinate (4)
-    // for the histogram and the candidate gather; the record (d + 1 words)
-    // read and written by the partition
-    const double recs = (double)L.recs;
-    { KScope ks_(kK_level_hist, s, recs * 4); k_level_hist<<<(unsigned)L.ntile, 512, 0, s>>>(P); }
-    { KScope ks_(kK_level_bucket, s);
-      k_level_bucket<<<(unsigned)ceil_div(L.nseg, 8), 256, 0, s>>>(P, L.nseg); }
-    { KScope ks_(kK_level_collect, s, recs * 4);
-      k_level_collect<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
-    { KScope ks_(kK_level_select, s); k_level_select<<<(unsigned)L.nseg, 256, 0, s>>>(P, L.nseg); }
-    { KScope ks_(kK_level_partition, s, recs * 8.0 * (dim + 1));
-      k_level_partition<<<(unsigned)L.ntile, tile / kItems, 0, s>>>(P); }
+    const double gbytes = cl_read * rin + cl_live * rst + (double)pool_off.back() * (4.0 * dim + rst);
+    LevelsParams B;
+    B.G = G;
+    B.cl_blocks = cl_blk.back();
+    B.pool_total = pool_off.back();
+    B.lv = (const LevelWork *)(plan + o_lw);
+    B.nlev = gmax;
+    B.bar = bar;
+    B.err = bt[0].err;
+    void *args[] = {(void *)&B};
+    st = coop((const void *)k_build_levels, kCoopThreads, args, kK_build_levels, gbytes + lv_bytes);
   }
 
   // ---- subtrees on chip ----
-  {
+  if (!st) {
     SubParams P;
     P.ntrees = ntree;
     P.dim = dim;
@@ -1179,37 +1301,37 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     cudaError_t e = cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSubtreeSmemMax);
     if (e != cudaSuccess) {
-      dev_free(af, block, total, s);
-      return cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
+      st = cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
+    } else {
+      // algorithmic bytes: every record read from staging (d + 1 words) and
+      // written in leaf order (rec_ints words); every node below the global
+      // levels written (16-byte node, box, live count); the leaf offsets
+      double sub_bytes = 0;
+      for (auto &b : bt)
+        sub_bytes += (double)b.s * 4.0 * ((dim + 1) + rec_ints(dim)) +
+                     (double)(((int64_t)2 << b.h) - ((int64_t)1 << b.g)) * (16.0 + 8.0 * dim + 4.0) +
+                     4.0 * (double)(((int64_t)1 << b.h) + 1);
+      KScope ks_(kK_subtree, s, sub_bytes);
+      k_subtree<<<(unsigned)sub_blk.back(), kSubThreads, smem, s>>>(P);
     }
-    // algorithmic bytes: every record read from staging (d + 1 words) and
-    // written in leaf order (rec_ints words); every node below the global
-    // levels written (16-byte node, box, live count); the leaf offsets
-    double sub_bytes = 0;
-    for (auto &b : bt)
-      sub_bytes += (double)b.s * 4.0 * ((dim + 1) + rec_ints(dim)) +
-                   (double)(((int64_t)2 << b.h) - ((int64_t)1 << b.g)) * (16.0 + 8.0 * dim + 4.0) +
-                   4.0 * (double)(((int64_t)1 << b.h) + 1);
-    KScope ks_(kK_subtree, s, sub_bytes);
-    k_subtree<<<(unsigned)sub_blk.back(), kSubThreads, smem, s>>>(P);
   }
 
   // ---- boxes and live counts of the global-level nodes, deepest first ----
-  for (int t = gmax - 1; t >= 0; --t) {
-    const LevelHost &L = lv[t];
-    BoxParams B;
-    B.nact = L.nact;
-    B.dim = dim;
-    B.t = t;
-    B.tree = d_tree;
-    B.act = d_act + L.act;
-    B.node = d_pre + L.node;
-    KScope ks_(kK_box_up, s);
-    k_box_up<<<(unsigned)ceil_div(L.nseg, 256), 256, 0, s>>>(B);
+  if (!st && gmax) {
+    FinishParams F;
+    F.dim = dim;
+    F.nlev = gmax;
+    F.tree = d_tree;
+    F.bw = (const BoxWork *)(plan + o_bw);
+    F.bar = bar + 2;
+    F.err = bt[0].err;
+    void *args[] = {(void *)&F};
+    st = coop((const void *)k_build_finish, 256, args, kK_build_finish, 0);
   }
-  launch_pack_nodes((const TreeSeg *)(plan + o_pk), (const int64_t *)(plan + o_pkpre), (int)pk_segs.size(),
-                    pk_pre.back(), s);
-  int err = cuda_check(cudaGetLastError(), "build kernels");
+  if (!st)
+    launch_pack_nodes((const TreeSeg *)(plan + o_pk), (const int64_t *)(plan + o_pkpre), (int)pk_segs.size(),
+                      pk_pre.back(), s);
+  int err = st ? st : cuda_check(cudaGetLastError(), "build kernels");
   dev_free(af, block, total, s);
   return err;
 }

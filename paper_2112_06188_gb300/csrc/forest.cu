@@ -24,15 +24,9 @@ std::atomic<uint64_t> g_launches{0};
 static thread_local std::string g_err;
 
 const char *const kKernelNames[kKernelCount] = {
-    "k_gather_cleared",
-    "k_gather_pool",
-    "k_level_hist",
-    "k_level_bucket",
-    "k_level_collect",
-    "k_level_select",
-    "k_level_partition",
+    "k_build_levels",
     "k_subtree",
-    "k_box_up",
+    "k_build_finish",
     "k_sort_small",
     "k_erase_mark",
     "k_bloom_build",
