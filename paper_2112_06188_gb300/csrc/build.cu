@@ -87,6 +87,7 @@ __device__ __forceinline__ int find_le(const int64_t *pre, int n, int64_t x) {
 
 struct LvTree {                // one tree at one global level
   int64_t base, s, seg_off, tile_off;
+  int64_t next_seg;            // its first segment at the next global level, or -1 if it has none
   int32_t t, c, h;
   NodeOut out;
   unsigned long long *err;
@@ -97,8 +98,11 @@ struct LvParams {              // one global level
   int64_t S;
   const int32_t *src;
   int32_t *dst;
-  uint32_t *hist;
-  SegState *seg;
+  uint32_t *hist;              // this level's per-segment histograms (filled by the level before)
+  SegState *seg;               // this level's segment states
+  uint32_t *hist_next;         // the next level's (accumulated by this level's partition)
+  SegState *seg_next;          // the next level's (cleared by this level's partition)
+  int64_t nseg_next;
   uint64_t *cand;
   LvTree one;                  // the level's tree when nact == 1 (no memory lookups)
   const LvTree *lt;            // [nact] the level's trees
@@ -230,51 +234,43 @@ __device__ void level_hist(const LvParams &P, int64_t b, uint32_t (*h)[kHistBins
   }
 }
 
-// One warp per segment: the bucket holding the median (rank ceil(m/2)).
-// Each lane sums a contiguous run of 64 bins (independent loads), a warp scan
-// of the run sums finds the run holding the rank, and that lane walks it.
-__device__ void level_bucket(const LvParams &P, int64_t gs, int lane) {
-  constexpr int kRun = kHistBins / 32;
-  const LvTree &T = tree_by_seg(P, gs);
-  int64_t st, sz;
-  seg_range(T.s, T.t, gs - T.seg_off, st, sz);
-  const uint32_t r = (uint32_t)((sz + 1) >> 1);
-  const uint4 *run = reinterpret_cast<const uint4 *>(P.hist + gs * kHistBins + lane * kRun);
-  uint32_t sum = 0;
-#pragma unroll 4
-  for (int j = 0; j < kRun / 4; ++j) {
-    const uint4 v = run[j];
-    sum += v.x + v.y + v.z + v.w;
+// The bin of a kHistBins-bin histogram h that holds the r-th smallest entry
+// (1-based), and how many entries lie in the bins before it; block-wide,
+// kCoopThreads threads, 4 bins each.
+__device__ void hist_rank_bin(const uint32_t *h, uint32_t r, int *out_bin, uint32_t *out_below,
+                              uint32_t *out_cnt) {
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int per = kHistBins / blockDim.x;   // 4
+  uint32_t v[4] = {0, 0, 0, 0}, sum = 0;
+  if (per == 4) {
+    const uint4 q = reinterpret_cast<const uint4 *>(h)[threadIdx.x];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    sum = q.x + q.y + q.z + q.w;
   }
   uint32_t inc = sum;
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += y;
   }
-  const bool hit = inc >= r && inc - sum < r;
-  const unsigned m = __ballot_sync(0xffffffffu, hit);
-  uint32_t *bins = P.hist + gs * kHistBins + lane * kRun;
-  if (hit && lane == __ffs(m) - 1) {
-    uint32_t below = inc - sum;
-    for (int j = 0; j < kRun; ++j) {
-      const uint32_t v = bins[j];
-      if (below + v >= r) {
-        SegState &S = P.seg[gs];
-        S.bucket = lane * kRun + j;
-        S.nbucket = (int32_t)v;
-        S.rank = (int64_t)(r - below);
-        S.cand_n = 0;
-        S.lcur = 0;
-        S.rcur = 0;
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t base = 0;
+  for (int w = 0; w < warp; ++w) base += wsum[w];
+  (void)nwarps;
+  uint32_t below = base + inc - sum;
+  if (below < r && r <= below + sum) {
+    for (int j = 0; j < 4; ++j) {
+      if (r <= below + v[j]) {
+        *out_bin = threadIdx.x * 4 + j;
+        *out_below = below;
+        *out_cnt = v[j];
         break;
       }
-      below += v;
+      below += v[j];
     }
   }
-  // leave the bins zeroed for the next level's histogram
-  uint4 *zrun = reinterpret_cast<uint4 *>(bins);
-#pragma unroll
-  for (int j = 0; j < kRun / 4; ++j) zrun[j] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
 }
 
 // Gather the (low coordinate bits, id) keys of every record in its segment's
@@ -282,12 +278,28 @@ __device__ void level_bucket(const LvParams &P, int64_t gs, int lane) {
 __device__ void level_collect(const LvParams &P, int64_t b) {
   __shared__ unsigned cnt[2];
   __shared__ unsigned long long basev[2];
+  __shared__ int s_bin[2];
+  __shared__ uint32_t s_below[2], s_cnt[2];
   const LvTree &T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  // the bucket holding each segment's median (rank ceil(m/2)), from the
+  // segment's histogram; the block whose tile holds the segment's first
+  // record records it for the select
+  for (int w = 0; w < (g.sz1 ? 2 : 1); ++w) {
+    const int64_t gs = T.seg_off + g.idx0 + w;
+    const int64_t sz = w ? g.sz1 : g.sz0;
+    hist_rank_bin(P.hist + gs * kHistBins, (uint32_t)((sz + 1) >> 1), &s_bin[w], &s_below[w], &s_cnt[w]);
+    const int64_t st = w ? g.st1 : g.st0;
+    if (threadIdx.x == 0 && st >= g.p0) {
+      SegState &S = P.seg[gs];
+      S.bucket = s_bin[w];
+      S.nbucket = (int32_t)s_cnt[w];
+      S.rank = (int64_t)(((sz + 1) >> 1) - s_below[w]);
+    }
+  }
   __syncthreads();
-  const SegState *s0 = &P.seg[T.seg_off + g.idx0];
-  int32_t bk0 = s0[0].bucket, bk1 = g.sz1 ? s0[1].bucket : -1;
+  int32_t bk0 = s_bin[0], bk1 = g.sz1 ? s_bin[1] : -1;
   const int32_t *x = P.src + T.c * P.S + T.base;
   const int32_t *xi = P.src + P.dim * P.S + T.base;
   uint64_t key[kItems];
@@ -387,6 +399,9 @@ __device__ void level_select(const LvParams &P, int64_t gs, uint64_t *keys) {
     shift = ns;
     __syncthreads();
   }
+  // the segment's histogram is done with: cleared for the level after next
+  for (int i = threadIdx.x; i < kHistBins / 4; i += blockDim.x)
+    reinterpret_cast<uint4 *>(P.hist + gs * kHistBins)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     uint64_t k40 = s_found;
     uint32_t coord = ((uint32_t)S.bucket << kHistShift) | (uint32_t)(k40 >> 31);
@@ -416,7 +431,10 @@ __device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, 
 // K2: partition every tile's records around their segment's median into the
 // other staging buffer.  Left records of a segment go to [st, st+ceil(m/2)),
 // right ones after; each CTA reserves its ranges with one atomic per class.
-__device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage) {
+// hnext: shared memory for the next level's histograms of the tile's (up to
+// four) child segments, 16-bit counts packed in pairs (a tile has at most
+// 4096 records).
+__device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage, uint32_t *hnext) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long cbase[4];
   __shared__ int64_t gdst[4];              // global start of each class's run
@@ -424,6 +442,11 @@ __device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage) {
   __shared__ int cok[4];
   const LvTree &T = tree_by_tile(P, b);
   TileSegs g = tile_segs(P, T, b);
+  const int64_t nxt = T.next_seg;
+  const int cn = (T.t + 1) % P.dim;
+  if (nxt >= 0)   // cleared before the block barriers below, filled after them
+    for (int i = threadIdx.x; i < 4 * kHistBins / 8; i += blockDim.x)
+      reinterpret_cast<uint4 *>(hnext)[i] = make_uint4(0, 0, 0, 0);
   const SegState *s0 = &P.seg[T.seg_off + g.idx0];
   uint64_t med0 = s0[0].median, med1 = g.sz1 ? s0[1].median : 0;
   const int32_t *xc = P.src + T.c * P.S + T.base;
@@ -490,14 +513,21 @@ __device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage) {
     run[c]++;
   }
   // each array: scatter into shared memory, then write every class's run
-  // with consecutive threads on consecutive addresses
+  // with consecutive threads on consecutive addresses; the next level's
+  // split coordinate also goes into its child segment's histogram
   const int ntile = coff[4];
   for (int c = 0; c <= P.dim; ++c) {
     int32_t v[kItems];
     load8(P.src + c * P.S + T.base, pb, g.p1, v);
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
-      if (spos[j] >= 0) stage[spos[j]] = v[j];
+      if (spos[j] >= 0) {
+        stage[spos[j]] = v[j];
+        if (c == cn && nxt >= 0) {
+          const int bin = v[j] >> kHistShift;
+          atomicAdd(&hnext[cls[j] * (kHistBins / 2) + (bin >> 1)], 1u << (16 * (bin & 1)));
+        }
+      }
     __syncthreads();
     int32_t *y = P.dst + c * P.S + T.base;
     for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
@@ -506,6 +536,16 @@ __device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage) {
     }
     __syncthreads();
   }
+  if (nxt >= 0)   // child (segment w, side) of level index idx0 + w is 2 (idx0 + w) + side
+    for (int i = threadIdx.x; i < 4 * kHistBins / 2; i += blockDim.x) {
+      const int k = i / (kHistBins / 2), wd = i % (kHistBins / 2);
+      if ((k >> 1) && !g.sz1) continue;
+      const uint32_t x = hnext[i];
+      if (!x) continue;
+      uint32_t *h = P.hist_next + (nxt + 2 * (g.idx0 + (k >> 1)) + (k & 1)) * kHistBins + 2 * wd;
+      if (x & 0xffffu) atomicAdd(h, x & 0xffffu);
+      if (x >> 16) atomicAdd(h + 1, x >> 16);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -533,10 +573,10 @@ struct LevelsParams {
 };
 
 __global__ void __launch_bounds__(kCoopThreads, 2) k_build_levels(const LevelsParams B) {
-  // one shared buffer for the phases' big arrays (histograms, candidate keys,
-  // the partition's staging), 16 KB
+  // shared buffers for the phases' big arrays (histograms, candidate keys,
+  // the partition's staging; the next level's histograms), 16 KB each
   __shared__ __align__(16) uint32_t s_big[2 * kHistBins];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  __shared__ __align__(16) uint32_t s_next[2 * kHistBins];
   for (int64_t b = blockIdx.x; b < B.cl_blocks; b += gridDim.x) {
     gather_cleared(B.G, b);
     __syncthreads();
@@ -544,17 +584,17 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_build_levels(const LevelsPa
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < B.pool_total;
        k += (int64_t)gridDim.x * blockDim.x)
     gather_pool(B.G, k);
+  if (B.nlev == 0) return;
+  // the first level's histograms; every later level's come from the
+  // partition of the level before
+  grid_barrier(B.bar, B.err);
+  for (int64_t b = blockIdx.x; b < B.lv[0].ntile; b += gridDim.x) {
+    level_hist(B.lv[0].P, b, reinterpret_cast<uint32_t (*)[kHistBins]>(s_big));
+    __syncthreads();
+  }
   for (int it = 0; it < B.nlev; ++it) {
     const LevelWork &W = B.lv[it];
     const LvParams &P = W.P;
-    grid_barrier(B.bar, B.err);
-    for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
-      level_hist(P, b, reinterpret_cast<uint32_t (*)[kHistBins]>(s_big));
-      __syncthreads();
-    }
-    grid_barrier(B.bar, B.err);
-    for (int64_t gs = (int64_t)blockIdx.x * nwarps + warp; gs < W.nseg; gs += (int64_t)gridDim.x * nwarps)
-      level_bucket(P, gs, lane);
     grid_barrier(B.bar, B.err);
     for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
       level_collect(P, b);
@@ -566,8 +606,14 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_build_levels(const LevelsPa
       __syncthreads();
     }
     grid_barrier(B.bar, B.err);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nseg_next;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      P.seg_next[i].cand_n = 0;
+      P.seg_next[i].lcur = 0;
+      P.seg_next[i].rcur = 0;
+    }
     for (int64_t b = blockIdx.x; b < W.ntile; b += gridDim.x) {
-      level_partition(P, b, reinterpret_cast<int32_t *>(s_big));
+      level_partition(P, b, reinterpret_cast<int32_t *>(s_big), s_next);
       __syncthreads();
     }
   }
@@ -1124,6 +1170,17 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   std::vector<int64_t> pre_all;
   std::vector<std::pair<size_t, size_t>> act_pos(gmax), seg_pos(gmax), tile_pos(gmax), node_pos(gmax);
   int64_t nseg_max = 0;
+  // each tree's first segment at each global level (for the histograms the
+  // partition of the level before accumulates)
+  std::vector<std::vector<int64_t>> segoff(gmax + 1, std::vector<int64_t>(ntree, -1));
+  for (int it = 0; it < gmax; ++it) {
+    int64_t segs = 0;
+    for (int j = 0; j < ntree; ++j)
+      if (bt[j].g > it) {
+        segoff[it][j] = segs;
+        segs += (int64_t)1 << it;
+      }
+  }
   for (int it = 0; it < gmax; ++it) {
     LevelHost &L = lv[it];
     L.act = act_all.size();
@@ -1142,6 +1199,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
       T.t = it;
       T.c = it % dim;
       T.seg_off = segs;
+      T.next_seg = segoff[it + 1][j];
       T.tile_off = tiles;
       T.out = dt[j].out;
       T.err = dt[j].err;
@@ -1179,8 +1237,10 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   // ---- one device block: scratch + plan ----
   const size_t stg_bytes = align256((size_t)(dim + 1) * S * 4);
   const size_t cand_bytes = gmax ? align256((size_t)S * 8) : 0;
-  const size_t hist_bytes = align256((size_t)nseg_max * kHistBins * 4);
-  const size_t seg_bytes = align256((size_t)nseg_max * sizeof(SegState));
+  // histograms and segment states alternate between two halves: a level
+  // fills the next level's half while it reads its own
+  const size_t hist_half = align256((size_t)nseg_max * kHistBins * 4), hist_bytes = 2 * hist_half;
+  const size_t seg_half = align256((size_t)nseg_max * sizeof(SegState)), seg_bytes = 2 * seg_half;
   // per-tree gather cursors, then (at the next 256-byte boundary) the two
   // fused kernels' grid-barrier words
   const size_t cursor_bytes = align256((size_t)ntree * 8) + 256;
@@ -1194,9 +1254,9 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   stg[0] = (int32_t *)p; p += stg_bytes;
   stg[1] = (int32_t *)p; p += stg_bytes;
   uint64_t *cand = (uint64_t *)p; p += cand_bytes;
-  SegState *seg = (SegState *)p; p += seg_bytes;
-  uint32_t *hist = (uint32_t *)p; p += hist_bytes;   // zeroed here, then by each level's
-  unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;   // bucket pass
+  SegState *seg = (SegState *)p; p += seg_bytes;     // zeroed here, then each level clears
+  uint32_t *hist = (uint32_t *)p; p += hist_bytes;   // the next one's states and its own
+  unsigned long long *cursor = (unsigned long long *)p; p += cursor_bytes;   // histograms
   unsigned char *plan = p;
   unsigned *bar = (unsigned *)((unsigned char *)cursor + align256((size_t)ntree * 8));   // [0..1] levels, [2..3] boxes
   const DTree *d_tree = (const DTree *)(plan + o_dt);
@@ -1231,8 +1291,11 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
       P.S = S;
       P.src = stg[it & 1];
       P.dst = stg[(it & 1) ^ 1];
-      P.hist = hist;
-      P.seg = seg;
+      P.hist = (uint32_t *)((unsigned char *)hist + (it & 1) * hist_half);
+      P.seg = (SegState *)((unsigned char *)seg + (it & 1) * seg_half);
+      P.hist_next = (uint32_t *)((unsigned char *)hist + ((it + 1) & 1) * hist_half);
+      P.seg_next = (SegState *)((unsigned char *)seg + ((it + 1) & 1) * seg_half);
+      P.nseg_next = it + 1 < gmax ? lv[it + 1].nseg : 0;
       P.cand = cand;
       P.one = lt_all[L.lt];
       P.lt = (const LvTree *)(plan + o_lt) + L.lt;
@@ -1250,7 +1313,8 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     }
   }
   st = h2d(plan, img.bytes.data(), img.bytes.size(), s);
-  if (!st) st = cuda_check(cudaMemsetAsync(hist, 0, hist_bytes + cursor_bytes, s), "memset");
+  // segment states, histograms and cursors (contiguous) start at zero
+  if (!st) st = cuda_check(cudaMemsetAsync(seg, 0, seg_bytes + hist_bytes + cursor_bytes, s), "memset");
   if (st) {
     dev_free(af, block, total, s);
     return st;
