@@ -428,7 +428,9 @@ ForestView forest_view(const bdl_forest *f);
 ForestView knn_view(bdl_forest *f, bool build, cudaStream_t s);
 // BDL_DEBUG_CHECK: wait for the call's kernels and report a bounds-check hit.
 int finish_call(bdl_forest *f, cudaStream_t s, int status);
-constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input order
+constexpr int64_t kSortMinQueries = 1 << 15;   // smaller batches run in input order ...
+constexpr int64_t kBatchSortMinQueries = 1 << 12;   // ... unless a batched call's small jobs
+                                                   // hold this many queries together
 constexpr size_t kPinnedWords = 2048;          // a forest's pinned scratch, in int64 words
 constexpr size_t kPinnedFlags = 2040;          // insert-validation flags that fit in it
 constexpr size_t kPinnedErr = 2044;            // where the error word is read back
@@ -460,7 +462,14 @@ int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
                         const std::vector<ClearedSrc> &cl, cudaStream_t s);
 int build_trees(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
                 const std::vector<ClearedSrc> &cl, cudaStream_t s);
-void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s);
+// Sort each list (ids[n], n <= 16384) ascending, one CTA per list, in one
+// launch; the list table goes to `table` (sort_small_table_bytes of device memory).
+struct SortList {
+  int32_t *ids;
+  int32_t n, np2;
+};
+size_t sort_small_table_bytes(size_t nlists);
+int launch_sort_small_many(const std::vector<SortList> &lists, void *table, cudaStream_t s);
 
 // ---- erase.cu ----
 // One forest's deduplicated erase list in an erase launch.
@@ -488,8 +497,15 @@ size_t erase_table_bytes(const std::vector<EraseCall> &calls);
 // table goes to `table` (erase_table_bytes of device memory).
 int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
                       cudaStream_t s);
-int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n,
-                        int32_t *out, cudaStream_t s);
+// The live ids of trees `trees` of forest f in increasing order, n of them,
+// into out -- for many forests in shared launches.
+struct LiveCollect {
+  bdl_forest *f;
+  std::vector<Tree *> trees;
+  int64_t n;
+  int32_t *out;
+};
+int collect_sorted_live(const std::vector<LiveCollect> &jobs, cudaStream_t s);
 
 // Table-driven helpers (one launch for many forests or trees).
 enum FillKind : int32_t { kFillAppend = 0, kFillPoolTail = 1, kFillIota = 2, kFillAlive = 3, kFillZero = 4 };
@@ -593,6 +609,12 @@ void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<T
                         std::vector<int64_t> &pre);
 // ... and one launch over a device copy of them (pre[nseg] = total).
 void launch_pack_nodes(const TreeSeg *segs, const int64_t *pre, int nseg, int64_t total, cudaStream_t s);
+// Spatial order for the small jobs of a batched call (all of one dimension,
+// perm unset): one counting sort over all their queries keyed by (job rank,
+// Morton prefix), which sets each call's perm; scratch of
+// batch_query_sort_bytes().  Does nothing for fewer than two jobs.
+size_t batch_query_sort_bytes(const std::vector<KnnCall> &calls);
+int batch_query_sort(std::vector<KnnCall> &calls, void *scratch, size_t bytes, cudaStream_t s);
 // Spatial order of the queries (counting sort on a Morton prefix of their
 // coordinates): perm[m] gets query indices; scratch of query_sort_bytes().
 size_t query_sort_bytes(int64_t m, int dim);

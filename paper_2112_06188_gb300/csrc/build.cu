@@ -1013,9 +1013,13 @@ __global__ void __launch_bounds__(256) k_build_finish(const FinishParams F) {
 // buffer helpers
 // ---------------------------------------------------------------------------
 
-// Single-CTA bitonic sort of n <= 16384 ids.
-__global__ void k_sort_small(int32_t *ids, int n, int np2) {
+// One CTA per list: bitonic sort of its n <= 16384 ids (np2 = n rounded up to
+// a power of two, padded with INT32_MAX).
+__global__ void k_sort_small_many(const SortList *lists) {
   extern __shared__ int32_t a[];
+  const SortList L = lists[blockIdx.x];
+  int32_t *ids = L.ids;
+  const int n = L.n, np2 = L.np2;
   for (int i = threadIdx.x; i < np2; i += blockDim.x) a[i] = i < n ? ids[i] : INT32_MAX;
   __syncthreads();
   for (int k = 2; k <= np2; k <<= 1) {
@@ -1400,13 +1404,18 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   return err;
 }
 
-void launch_sort_small(int32_t *ids, int64_t n, cudaStream_t s) {
-  if (n <= 1) return;
-  int np2 = 1;
-  while (np2 < n) np2 <<= 1;
-  cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
-  { KScope ks_(kK_sort_small, s);
-  k_sort_small<<<1, 1024, (size_t)np2 * 4, s>>>(ids, (int)n, np2); }
+size_t sort_small_table_bytes(size_t nlists) { return align256(std::max<size_t>(nlists, 1) * sizeof(SortList)); }
+
+int launch_sort_small_many(const std::vector<SortList> &lists, void *table, cudaStream_t s) {
+  int np2max = 0;
+  for (const auto &L : lists) np2max = std::max(np2max, L.np2);
+  if (lists.empty() || np2max <= 1) return BDL_OK;
+  int st = h2d(table, lists.data(), lists.size() * sizeof(SortList), s);
+  if (st) return st;
+  cudaFuncSetAttribute(k_sort_small_many, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
+  KScope ks_(kK_sort_small, s);
+  k_sort_small_many<<<(unsigned)lists.size(), 1024, (size_t)np2max * 4, s>>>((const SortList *)table);
+  return cuda_check(cudaGetLastError(), "sort kernel");
 }
 
 }  // namespace bdl

@@ -135,13 +135,47 @@ __global__ void k_erase_locate(const EraseJob *jobs, const int64_t *job_warp, in
   }
 }
 
-// Ordered gather: mark the live ids of the given trees in a bitmap, then emit
-// them in increasing order through a prefix sum of per-word popcounts.
-__global__ void k_mark_ids(const int32_t *pts, int64_t size, int dim, uint32_t *bm) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= size) return;
-  int32_t id = pts[j * rec_ints(dim) + dim];
-  if (id >= 0) atomicOr(&bm[id >> 5], 1u << (id & 31));
+// Ordered gather, for many forests at once: mark the live ids of the given
+// trees in their forest's bitmap, then emit each forest's marked ids in
+// increasing order through a prefix sum of per-word popcounts.
+
+// One tree whose live ids are marked in its forest's bitmap.
+struct MarkTree {
+  const int32_t *pts;
+  int64_t size;
+  int32_t dim, pad_;
+  uint32_t *bm;
+};
+
+// One forest's bitmap and output.
+struct BitForest {
+  const uint32_t *bm;
+  int64_t nwords;
+  int64_t *bsum;           // [blocks] popcount of each scan block, then its exclusive prefix
+  int64_t nb;
+  int32_t *out;
+  int64_t nout;
+  unsigned long long *err;
+};
+
+__device__ __forceinline__ int find_pre(const int64_t *pre, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// thread per record of the trees (tree j owns records pre[j] .. pre[j+1]-1)
+__global__ void k_mark_ids_many(const MarkTree *t, const int64_t *pre, int nt) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[nt]) return;
+  const int j = find_pre(pre, nt, x);
+  const MarkTree &T = t[j];
+  const int32_t id = T.pts[(x - pre[j]) * rec_ints(T.dim) + T.dim];
+  if (id >= 0) atomicOr(&T.bm[id >> 5], 1u << (id & 31));
 }
 
 constexpr int kScanBlock = 1024;
@@ -174,49 +208,59 @@ __device__ int block_excl_scan(int v, int *tot) {
   return r;
 }
 
-__global__ void k_popc_blocks(const uint32_t *bm, int64_t nwords, int64_t *bsum) {
-  int64_t w0 = ((int64_t)blockIdx.x * kScanBlock + threadIdx.x) * kScanWords;
+// Scan block bb of all forests' bitmaps (forest j owns blocks pre[j] ..
+// pre[j+1]-1): its popcount.
+__global__ void k_popc_blocks_many(const BitForest *f, const int64_t *pre, int nf) {
+  const int j = find_pre(pre, nf, blockIdx.x);
+  const BitForest &F = f[j];
+  const int64_t b = blockIdx.x - pre[j];
+  const int64_t w0 = (b * kScanBlock + threadIdx.x) * kScanWords;
   int c = 0;
   for (int k = 0; k < kScanWords; ++k)
-    if (w0 + k < nwords) c += __popc(bm[w0 + k]);
+    if (w0 + k < F.nwords) c += __popc(F.bm[w0 + k]);
   int tot;
   block_excl_scan(c, &tot);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  if (threadIdx.x == 0) F.bsum[b] = tot;
 }
 
-__global__ void k_scan_bsum(int64_t *bsum, int64_t nb) {
+// One CTA per forest: exclusive prefix of its blocks' popcounts.
+__global__ void k_scan_bsum_many(const BitForest *f) {
   __shared__ int64_t carry;
+  const BitForest &F = f[blockIdx.x];
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int64_t a = 0; a < nb; a += blockDim.x) {
+  for (int64_t a = 0; a < F.nb; a += blockDim.x) {
     int64_t j = a + threadIdx.x;
-    int v = j < nb ? (int)bsum[j] : 0;
+    int v = j < F.nb ? (int)F.bsum[j] : 0;
     int tot;
     int e = block_excl_scan(v, &tot);
-    if (j < nb) bsum[j] = carry + e;
+    if (j < F.nb) F.bsum[j] = carry + e;
     __syncthreads();
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
 }
 
-__global__ void k_emit_ids(const uint32_t *bm, int64_t nwords, const int64_t *bsum, int32_t *out,
-                           int64_t nout, unsigned long long *err) {
-  int64_t w0 = ((int64_t)blockIdx.x * kScanBlock + threadIdx.x) * kScanWords;
+// Scan block bb of all forests' bitmaps: its ids, in order, to the forest's output.
+__global__ void k_emit_ids_many(const BitForest *f, const int64_t *pre, int nf) {
+  const int j = find_pre(pre, nf, blockIdx.x);
+  const BitForest &F = f[j];
+  const int64_t b = blockIdx.x - pre[j];
+  const int64_t w0 = (b * kScanBlock + threadIdx.x) * kScanWords;
   uint32_t wv[kScanWords];
   int c = 0;
   for (int k = 0; k < kScanWords; ++k) {
-    wv[k] = w0 + k < nwords ? bm[w0 + k] : 0u;
+    wv[k] = w0 + k < F.nwords ? F.bm[w0 + k] : 0u;
     c += __popc(wv[k]);
   }
   int tot;
-  int64_t pos = bsum[blockIdx.x] + block_excl_scan(c, &tot);
+  int64_t pos = F.bsum[b] + block_excl_scan(c, &tot);
   for (int k = 0; k < kScanWords; ++k) {
     uint32_t x = wv[k];
     while (x) {
-      int b = __ffs(x) - 1;
-      if (pos < nout) out[pos] = (int32_t)(((w0 + k) << 5) + b);
-      else atomicOr(err, kErrGather);
+      int bt = __ffs(x) - 1;
+      if (pos < F.nout) F.out[pos] = (int32_t)(((w0 + k) << 5) + bt);
+      else atomicOr(F.err, kErrGather);
       pos++;
       x &= x - 1;
     }
@@ -291,32 +335,90 @@ int launch_erase_jobs(const std::vector<EraseCall> &calls, void *table,
   return cuda_check(cudaGetLastError(), "erase kernel");
 }
 
-int collect_sorted_live(bdl_forest *f, const std::vector<Tree *> &from, int64_t n, int32_t *out,
-                        cudaStream_t s) {
-  if (n <= 0) return BDL_OK;
-  int64_t nwords = (f->next_id + 31) >> 5;
-  int64_t per_block = (int64_t)kScanBlock * kScanWords;
-  int64_t nb = cdiv(nwords, per_block);
-  size_t bytes = (size_t)nwords * 4 + 256 + (size_t)nb * 8;
-  void *blk = nullptr;
-  int st = dev_alloc(f, &blk, bytes, s);
-  if (st) return st;
-  uint32_t *bm = (uint32_t *)blk;
-  int64_t *bsum = (int64_t *)((char *)blk + ((size_t)nwords * 4 + 255) / 256 * 256);
-  cudaMemsetAsync(bm, 0, (size_t)nwords * 4, s);
-  for (Tree *t : from) {
-    { KScope ks_(kK_mark_ids, s);
-    k_mark_ids<<<(unsigned)cdiv(t->size, 256), 256, 0, s>>>(t->pts, t->size, f->dim, bm); }
+int collect_sorted_live(const std::vector<LiveCollect> &jobs, cudaStream_t s) {
+  std::vector<BitForest> bf;
+  std::vector<MarkTree> mt;
+  std::vector<int64_t> fpre{0}, tpre{0};
+  size_t bytes = 0;
+  for (const auto &J : jobs) {
+    if (J.n <= 0) continue;
+    const int64_t nwords = (J.f->next_id + 31) >> 5;
+    const int64_t nb = cdiv(nwords, (int64_t)kScanBlock * kScanWords);
+    bytes += ((size_t)nwords * 4 + 255) / 256 * 256 + ((size_t)nb * 8 + 255) / 256 * 256;
   }
-  { KScope ks_(kK_popc_blocks, s);
-  k_popc_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum); }
-  { KScope ks_(kK_scan_bsum, s);
-  k_scan_bsum<<<1, 1024, 0, s>>>(bsum, nb); }
-  { KScope ks_(kK_emit_ids, s);
-  k_emit_ids<<<(unsigned)nb, kScanBlock, 0, s>>>(bm, nwords, bsum, out, n, f->err); }
-  int err = cuda_check(cudaGetLastError(), "collect_sorted_live");
-  dev_free(f, blk, bytes, s);
-  return err;
+  if (bytes == 0) return BDL_OK;
+  bdl_forest *charge = nullptr;
+  for (const auto &J : jobs)
+    if (J.n > 0) { charge = J.f; break; }
+  void *blk = nullptr;
+  int st = dev_alloc(charge, &blk, bytes, s);
+  if (st) return st;
+  char *p = (char *)blk;
+  size_t bm_bytes = 0;
+  for (const auto &J : jobs) {
+    if (J.n <= 0) continue;
+    const int64_t nwords = (J.f->next_id + 31) >> 5;
+    const int64_t nb = cdiv(nwords, (int64_t)kScanBlock * kScanWords);
+    BitForest F;
+    F.bm = (const uint32_t *)p;
+    p += ((size_t)nwords * 4 + 255) / 256 * 256;
+    bm_bytes = (size_t)(p - (char *)blk);
+    F.nwords = nwords;
+    F.bsum = nullptr;
+    F.nb = nb;
+    F.out = J.out;
+    F.nout = J.n;
+    F.err = J.f->err;
+    for (Tree *t : J.trees) {
+      mt.push_back(MarkTree{t->pts, t->size, J.f->dim, 0, (uint32_t *)F.bm});
+      tpre.push_back(tpre.back() + t->size);
+    }
+    bf.push_back(F);
+    fpre.push_back(fpre.back() + nb);
+  }
+  for (auto &F : bf) {   // the block sums after all bitmaps
+    F.bsum = (int64_t *)p;
+    p += ((size_t)F.nb * 8 + 255) / 256 * 256;
+  }
+  // tables: [MarkTree][tree prefix][BitForest][block prefix]
+  std::vector<unsigned char> img;
+  auto put = [&](const void *src, size_t n) {
+    size_t off = (img.size() + 255) / 256 * 256;
+    img.resize(off + std::max<size_t>(n, 8));
+    memcpy(img.data() + off, src, n);
+    return off;
+  };
+  const size_t o_mt = put(mt.data(), mt.size() * sizeof(MarkTree)), o_tp = put(tpre.data(), tpre.size() * 8),
+               o_bf = put(bf.data(), bf.size() * sizeof(BitForest)), o_fp = put(fpre.data(), fpre.size() * 8);
+  void *tab = nullptr;
+  st = dev_alloc(charge, &tab, img.size(), s);
+  if (st) {
+    dev_free(charge, blk, bytes, s);
+    return st;
+  }
+  st = h2d(tab, img.data(), img.size(), s);
+  if (!st) st = cuda_check(cudaMemsetAsync(blk, 0, bm_bytes, s), "memset");
+  const char *T = (const char *)tab;
+  const int nt = (int)mt.size(), nf = (int)bf.size();
+  if (!st && tpre.back() > 0) {
+    KScope ks_(kK_mark_ids, s);
+    k_mark_ids_many<<<(unsigned)cdiv(tpre.back(), 256), 256, 0, s>>>((const MarkTree *)(T + o_mt),
+                                                                     (const int64_t *)(T + o_tp), nt);
+  }
+  if (!st) {
+    { KScope ks_(kK_popc_blocks, s);
+      k_popc_blocks_many<<<(unsigned)fpre.back(), kScanBlock, 0, s>>>((const BitForest *)(T + o_bf),
+                                                                      (const int64_t *)(T + o_fp), nf); }
+    { KScope ks_(kK_scan_bsum, s);
+      k_scan_bsum_many<<<(unsigned)nf, 1024, 0, s>>>((const BitForest *)(T + o_bf)); }
+    { KScope ks_(kK_emit_ids, s);
+      k_emit_ids_many<<<(unsigned)fpre.back(), kScanBlock, 0, s>>>((const BitForest *)(T + o_bf),
+                                                                   (const int64_t *)(T + o_fp), nf); }
+  }
+  if (!st) st = cuda_check(cudaGetLastError(), "collect_sorted_live");
+  dev_free(charge, tab, img.size(), s);
+  dev_free(charge, blk, bytes, s);
+  return st;
 }
 
 }  // namespace bdl

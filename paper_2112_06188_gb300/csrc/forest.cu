@@ -505,14 +505,22 @@ static FillSeg tail_fill(const InsertPlan &ip) {
   return g;
 }
 
+// A list to sort, given its length.
+static SortList sort_list(int32_t *ids, int64_t n) {
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  return SortList{ids, (int32_t)n, np2};
+}
+
 // After the build and the tail fill: free cleared trees and the old buffer,
-// install the new trees.
-static void commit_insert(InsertPlan &ip, cudaStream_t s) {
+// install the new trees.  A buffer that took reinserted ids is added to
+// `sorts` (it must stay in ascending id order).
+static void commit_insert(InsertPlan &ip, std::vector<SortList> &sorts, cudaStream_t s) {
   bdl_forest *f = ip.f;
   const int64_t X = f->cfg.buffer_size;
   if (ip.pool.arr) {             // reinserted ids: keep the buffer sorted
-    if (ip.q == 0) launch_sort_small(f->buf, ip.t, s);
-    else if (ip.rem > 1) launch_sort_small((int32_t *)ip.newbuf, ip.rem, s);
+    if (ip.q == 0 && ip.t > 1) sorts.push_back(sort_list(f->buf, ip.t));
+    else if (ip.q > 0 && ip.rem > 1) sorts.push_back(sort_list((int32_t *)ip.newbuf, ip.rem));
   }
   if (ip.q == 0) {
     f->nbuf = ip.t;
@@ -611,9 +619,14 @@ static int commit_planned(std::vector<InsertPlan> &plans, std::vector<FillSeg> f
     for (auto &ip : plans) drop_plan(ip, s);
     return st;
   }
+  std::vector<SortList> sorts;
   for (auto &ip : plans)
-    if (ip.f) commit_insert(ip, s);
-  return BDL_OK;
+    if (ip.f) commit_insert(ip, sorts, s);
+  if (sorts.empty()) return BDL_OK;
+  void *st_tab = nullptr;
+  st = tmp.get(sort_small_table_bytes(sorts.size()), &st_tab);
+  if (!st) st = launch_sort_small_many(sorts, st_tab, s);
+  return st;
 }
 
 static int build_and_commit(std::vector<InsertPlan> &plans, std::vector<BuildTree> &bt,
@@ -1156,11 +1169,13 @@ static int reinsert_low(const std::vector<bdl_forest *> &fs, cudaStream_t s) {
   }
   if (lows.empty()) return BDL_OK;
   int st = BDL_OK;
+  std::vector<LiveCollect> jobs;
   for (auto &L : lows) {
     if (st) break;
     st = dev_alloc(L.f, &L.R, (size_t)std::max<int64_t>(L.nr, 1) * 4, s);
-    if (!st) st = collect_sorted_live(L.f, L.trees, L.nr, (int32_t *)L.R, s);
+    jobs.push_back(LiveCollect{L.f, L.trees, L.nr, (int32_t *)L.R});
   }
+  if (!st) st = collect_sorted_live(jobs, s);   // every forest's ids in shared launches
   std::vector<InsertPlan> plans(lows.size());
   std::vector<BuildTree> bt;
   std::vector<ClearedSrc> cl;
@@ -1249,6 +1264,21 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
     for (int i = 0; i < nf; ++i)
       if (F[i]->dim == d && F[i]->knn_stats) stats = F[i]->knn_stats;
     if (counts) stats = counts;
+    // the jobs too small for a sort of their own share one (job, Morton) sort
+    if (!counts) {
+      std::vector<int> small;
+      int64_t msum = 0;
+      for (size_t j = 0; j < g.size(); ++j)
+        if (!g[j].perm && g[j].m > 0) small.push_back((int)j), msum += g[j].m;
+      if (small.size() >= 2 && msum >= kBatchSortMinQueries) {
+        std::vector<KnnCall> sg;
+        for (int j : small) sg.push_back(g[j]);
+        void *scr = nullptr;
+        const size_t bytes = batch_query_sort_bytes(sg);
+        if (tmp.get(bytes, &scr) == BDL_OK && batch_query_sort(sg, scr, bytes, s) == BDL_OK)
+          for (size_t j = 0; j < small.size(); ++j) g[small[j]].perm = sg[j].perm;
+      }
+    }
     void *table = nullptr;
     const size_t tb = knn_table_bytes(g);
     if (tb) st = tmp.get(tb, &table);

@@ -605,7 +605,100 @@ __global__ void k_qscatter(const int32_t *coords, const int32_t *ids, int64_t m,
   if (pos < m) out[pos] = ids ? ids[i] : (int32_t)i;
 }
 
+// Many small query batches (one per job of a batched call) in one counting
+// sort: the key is the job's rank, then a Morton prefix of B bits per
+// coordinate, so that each job's queries come out together and in spatial
+// order.  perm[off_j + t] = the t-th query of job j, as an index into job j's
+// queries.
+struct BatchSortJobs {
+  const int32_t *const *q;   // [njobs] query arrays
+  const int64_t *pre;        // [njobs + 1] query prefix
+  int njobs, dim, B;
+};
+
+__device__ __forceinline__ uint32_t batch_key(const BatchSortJobs &S, int64_t x, int32_t &local) {
+  const int j = knn_find(S.pre, S.njobs, x);
+  local = (int32_t)(x - S.pre[j]);
+  return ((uint32_t)j << (S.B * S.dim)) | morton_key(S.q[j] + (int64_t)local * S.dim, S.dim, S.B);
+}
+
+__global__ void k_bkey_hist(const BatchSortJobs S, uint32_t *hist) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= S.pre[S.njobs]) return;
+  int32_t local;
+  atomicAdd(&hist[batch_key(S, x, local)], 1u);
+}
+
+__global__ void k_bkey_scatter(const BatchSortJobs S, uint32_t *offs, const uint32_t *bsum, int32_t *perm) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t M = S.pre[S.njobs];
+  if (x >= M) return;
+  int32_t local;
+  const uint32_t key = batch_key(S, x, local);
+  const uint32_t pos = bsum[key / kScanPer] + atomicAdd(&offs[key], 1u);
+  if (pos < M) perm[pos] = local;
+}
+
 }  // namespace
+
+int batch_query_sort(std::vector<KnnCall> &calls, void *scratch, size_t bytes, cudaStream_t s) {
+  const int n = (int)calls.size();
+  if (n < 2) return BDL_OK;
+  const int dim = calls[0].fv->dim;
+  // bits per coordinate: the most with n * 2^(B*dim) <= 2^22 bins, at most 10
+  int B = 0;
+  while (B < 10 && ((int64_t)n << ((B + 1) * dim)) <= ((int64_t)1 << 22)) ++B;
+  if (B == 0) return BDL_OK;
+  const int64_t nbins = (int64_t)n << (B * dim);
+  const int64_t nb = (nbins + kScanPer - 1) / kScanPer;
+  int64_t M = 0;
+  for (auto &c : calls) M += c.m;
+  if (bytes < batch_query_sort_bytes(calls)) return set_error(BDL_EINTERNAL, "batch sort scratch too small");
+  // scratch: perm [M], hist [nbins], block sums [nb], job table (q pointers, prefix)
+  char *p = (char *)scratch;
+  int32_t *perm = (int32_t *)p; p += ((size_t)M * 4 + 255) / 256 * 256;
+  uint32_t *hist = (uint32_t *)p; p += ((size_t)nbins * 4 + 255) / 256 * 256;
+  uint32_t *bsum = (uint32_t *)p; p += ((size_t)nb * 4 + 255) / 256 * 256;
+  std::vector<unsigned char> img(((size_t)n * 8 + 255) / 256 * 256 + (size_t)(n + 1) * 8);
+  const int32_t **qv = (const int32_t **)img.data();
+  int64_t *pre = (int64_t *)(img.data() + ((size_t)n * 8 + 255) / 256 * 256);
+  pre[0] = 0;
+  for (int j = 0; j < n; ++j) {
+    qv[j] = calls[j].q;
+    pre[j + 1] = pre[j] + calls[j].m;
+  }
+  int st = h2d(p, img.data(), img.size(), s);
+  if (st) return st;
+  BatchSortJobs S;
+  S.q = (const int32_t *const *)p;
+  S.pre = (const int64_t *)(p + ((size_t)n * 8 + 255) / 256 * 256);
+  S.njobs = n;
+  S.dim = dim;
+  S.B = B;
+  st = cuda_check(cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s), "memset");
+  if (st) return st;
+  const unsigned g = (unsigned)((M + 255) / 256);
+  { KScope ks_(kK_qsort, s); k_bkey_hist<<<g, 256, 0, s>>>(S, hist); }
+  { KScope ks_(kK_qsort, s); k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum); }
+  { KScope ks_(kK_qsort, s); k_scan_top<<<1, 1024, 0, s>>>(bsum, nb); }
+  { KScope ks_(kK_qsort, s); k_bkey_scatter<<<g, 256, 0, s>>>(S, hist, bsum, perm); }
+  for (int j = 0; j < n; ++j) calls[j].perm = perm + pre[j];
+  return cuda_check(cudaGetLastError(), "batch query sort");
+}
+
+size_t batch_query_sort_bytes(const std::vector<KnnCall> &calls) {
+  const int n = (int)calls.size();
+  if (n < 2) return 0;
+  const int dim = calls[0].fv->dim;
+  int B = 0;
+  while (B < 10 && ((int64_t)n << ((B + 1) * dim)) <= ((int64_t)1 << 22)) ++B;
+  const int64_t nbins = (int64_t)n << (B * dim);
+  const int64_t nb = (nbins + kScanPer - 1) / kScanPer;
+  int64_t M = 0;
+  for (auto &c : calls) M += c.m;
+  return ((size_t)M * 4 + 255) / 256 * 256 + ((size_t)nbins * 4 + 255) / 256 * 256 +
+         ((size_t)nb * 4 + 255) / 256 * 256 + ((size_t)n * 8 + 255) / 256 * 256 + (size_t)(n + 1) * 8 + 256;
+}
 
 size_t knn_table_bytes(const std::vector<KnnCall> &calls) {
   if (calls.size() == 1) return 0;   // one forest: no table (kernel parameters)
