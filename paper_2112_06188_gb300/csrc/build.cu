@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       s_bel[kMaxRadixSegs];
   __shared__ unsigned char s_done[kMaxRadixSegs], s_fnd[kMaxRadixSegs];
   __shared__ uint32_t s_w[32];
+  __shared__ int s_ncand;
 
   const int cap = P.cap, dim = P.dim;
   int b = blockIdx.x;
@@ -711,6 +712,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   __syncthreads();
 
   const int U = T.h - t0;
+  bool hist_ready = false;   // `hist` holds this level's first-pass histogram already
   uint16_t *cur = perm0, *nxt = perm1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
@@ -736,21 +738,33 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         s_cnt[s] = 0;
       }
       __syncthreads();
+      // The first pass's histogram (the top w bits of every key) was filled by
+      // the previous level's partition, except at the subtree's first level.
+      // After the first pass, the records that can still hold their
+      // segment's median (key prefix = the chosen digits) are listed once in
+      // `nxt` (free until this level's partition), and the later passes read
+      // only them.
+      uint16_t *cand = nxt;
       int shift = kKeyBits;
+      bool first = true;
       while (true) {
         const int ns = max(0, shift - w);
         const int ww = shift - ns;
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        for (int q = threadIdx.x; q < m0; q += blockDim.x) {
-          int s = segid[q];
-          if (s_done[s]) continue;
-          uint64_t k = skey(sc, sid, cap, c, cur[q]);
-          if ((k >> shift) != (s_pre[s] >> shift)) continue;
-          if (s_cnt[s] == 1) { s_res[s] = k; s_fnd[s] = 1; continue; }
-          atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << ww) - 1))], 1u);
+        if (!(first && hist_ready)) {
+          for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;
+          __syncthreads();
+          const int nq = first ? m0 : s_ncand;
+          for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const int q = first ? i : cand[i];
+            int s = segid[q];
+            if (s_done[s]) continue;
+            uint64_t k = skey(sc, sid, cap, c, cur[q]);
+            if ((k >> shift) != (s_pre[s] >> shift)) continue;
+            if (s_cnt[s] == 1) { s_res[s] = k; s_fnd[s] = 1; continue; }
+            atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << ww) - 1))], 1u);
+          }
+          __syncthreads();
         }
-        __syncthreads();
         // block exclusive scan of hist -> ex (2048 bins, 2 per thread)
         {
           int i2 = 2 * threadIdx.x;
@@ -802,14 +816,37 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         }
         shift = ns;
         if (!__syncthreads_or(pending)) break;
+        if (first) {   // list the records whose key still matches their segment's prefix
+          if (threadIdx.x == 0) s_ncand = 0;
+          __syncthreads();
+          for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+            const int s = segid[q];
+            if (s_done[s]) continue;
+            const uint64_t k = skey(sc, sid, cap, c, cur[q]);
+            if ((k >> shift) == (s_pre[s] >> shift)) cand[atomicAdd(&s_ncand, 1)] = (uint16_t)q;
+          }
+          __syncthreads();
+          first = false;
+        }
       }
+      hist_ready = false;
       // node keys
       for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
         int64_t bfs = (i0 << u) + s;
         int64_t v = veb_slot(l, t, bfs);
         o.node[v] = Node{s_res[s], (int32_t)veb_slot(l, t + 1, 2 * bfs), (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
       }
-      // stable partition by a block scan of the left flags (positions blocked per thread)
+      // stable partition by a block scan of the left flags (positions blocked
+      // per thread); when the next level also selects by radix, its first
+      // pass's histogram (the top bits of the next split coordinate, per
+      // child segment) is counted on the way
+      int64_t nst_, nsz_;
+      seg_range(m0, u + 1, 0, nst_, nsz_);
+      const bool next_radix = u + 1 < U && nsz_ > kWarpMode;
+      const int wn = 10 - u;                 // the next level's digit width, 11 - (u + 1)
+      const int cn = (t + 1) % dim;
+      if (next_radix)
+        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;   // ordered by the barriers below
       const int ipt = (cap + blockDim.x - 1) / blockDim.x;
       const int q0 = threadIdx.x * ipt;
       uint32_t flags = 0;
@@ -869,12 +906,17 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             } else {
               nxt[dst] = cur[q];
               segid_n[dst] = (unsigned char)(2 * s + (left ? 0 : 1));   // child segment
+              if (next_radix) {
+                const int32_t x = sc[cn * cap + cur[q]];
+                atomicAdd(&hist[((2 * s + (left ? 0 : 1)) << wn) + (x >> (kCoordBits - wn))], 1u);
+              }
             }
             run += (flags >> j) & 1;
           }
         }
       }
       __syncthreads();
+      hist_ready = next_radix;
       unsigned char *ts = segid; segid = segid_n; segid_n = ts;
     } else {
       // ---------------- warp mode: one warp sorts each segment -------------
@@ -903,10 +945,12 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
           if (e1 < z) nxt[a + e1] = (uint16_t)(x1 & 8191u);
           med = __shfl_sync(0xffffffffu, (mr & 1) ? x1 : x0, mr >> 1);
         }
-        if (lane == 0) {
+        {
+          // the node's vEB slot and its children's, three lanes at once
           const int64_t bfs = (i0 << u) + s;
-          o.node[veb_slot(l, t, bfs)] = Node{med >> 13, (int32_t)veb_slot(l, t + 1, 2 * bfs),
-                                             (int32_t)veb_slot(l, t + 1, 2 * bfs + 1)};
+          const int64_t sl = lane < 3 ? veb_slot(l, lane ? t + 1 : t, lane ? 2 * bfs + lane - 1 : bfs) : 0;
+          const int64_t vl = __shfl_sync(0xffffffffu, sl, 1), vr = __shfl_sync(0xffffffffu, sl, 2);
+          if (lane == 0) o.node[sl] = Node{med >> 13, (int32_t)vl, (int32_t)vr};
         }
       }
       __syncthreads();
@@ -914,43 +958,129 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     uint16_t *tmp = cur; cur = nxt; nxt = tmp;
   }
 
-  // leaves: slot, leaf range, box, live count
+  // leaves: slot, leaf range, box, live count; then the subtree's internal
+  // nodes bottom-up
   const int nleaf = 1 << U;
   const int64_t nleaves_tree = (int64_t)1 << T.h;
-  for (int lf = threadIdx.x; lf < nleaf; lf += blockDim.x) {
-    int64_t a64, z64;
-    seg_range(m0, U, lf, a64, z64);
-    int a = (int)a64, z = (int)z64;
-    int64_t leaf = (i0 << U) + lf;
-    int64_t v = veb_slot(l, T.h, leaf);
-    o.node[v] = Node{0, (int32_t)(-1 - leaf), 0};
-    o.live[v] = z;
-    o.leaf_off[leaf] = (int32_t)(start0 + a);
-    if (leaf == nleaves_tree - 1) o.leaf_off[nleaves_tree] = (int32_t)T.s;
-    for (int cc = 0; cc < dim; ++cc) {
-      int32_t lo = INT32_MAX, hi = INT32_MIN;
-      for (int q = a; q < a + z; ++q) {
-        int32_t x = sc[cc * cap + cur[q]];
-        lo = min(lo, x);
-        hi = max(hi, x);
-      }
-      o.box[v * 2 * dim + cc] = lo;
-      o.box[v * 2 * dim + dim + cc] = hi;
+  if (nleaf <= (int)blockDim.x) {
+    // Every node's vEB slot once, in heap order in shared memory (node (u, s)
+    // at (1 << u) + s; the histogram space is free now), then per channel --
+    // the live counts, then each coordinate's low and high bounds -- a value
+    // per leaf in a thread, pairs combined by warp shuffles up to the warp's
+    // subtree, the warps' results by warp 0: no barrier and no read-back of
+    // global memory per level.
+    int32_t *nslot = (int32_t *)hist;                  // [2 * nleaf]
+    int32_t *wlo = nslot + 2 * nleaf, *whi = wlo + 32; // [32] each: the warps' results
+    for (int x = threadIdx.x + 1; x < 2 * nleaf; x += blockDim.x) {
+      const int u = 31 - __clz(x);
+      nslot[x] = (int32_t)veb_slot(l, t0 + u, (i0 << u) + (x - (1 << u)));
     }
-  }
-  // internal nodes of the subtree, bottom-up (children are in global memory)
-  for (int u = U - 1; u >= 0; --u) {
     __syncthreads();
-    for (int s = threadIdx.x; s < (1 << u); s += blockDim.x) {
-      int64_t bfs = (i0 << u) + s;
-      int t = t0 + u;
-      int64_t v = veb_slot(l, t, bfs);
-      int64_t vl = veb_slot(l, t + 1, 2 * bfs), vr = veb_slot(l, t + 1, 2 * bfs + 1);
-      o.live[v] = o.live[vl] + o.live[vr];
+    const int lf = threadIdx.x;
+    const bool has = lf < nleaf;
+    int a = 0, z = 0;
+    if (has) {
+      int64_t a64, z64;
+      seg_range(m0, U, lf, a64, z64);
+      a = (int)a64;
+      z = (int)z64;
+      const int64_t leaf = (i0 << U) + lf;
+      o.node[nslot[nleaf + lf]] = Node{0, (int32_t)(-1 - leaf), 0};
+      o.leaf_off[leaf] = (int32_t)(start0 + a);
+      if (leaf == nleaves_tree - 1) o.leaf_off[nleaves_tree] = (int32_t)T.s;
+    }
+    const int kw = U < 5 ? U : 5;        // levels combined inside a warp
+    for (int ch = -1; ch < dim; ++ch) {  // ch = -1: live counts
+      int32_t lo = ch < 0 ? 0 : INT32_MAX, hi = INT32_MIN;
+      if (has) {
+        if (ch < 0) {
+          lo = z;
+        } else {
+          for (int q = a; q < a + z; ++q) {
+            const int32_t x = sc[ch * cap + cur[q]];
+            lo = min(lo, x);
+            hi = max(hi, x);
+          }
+        }
+      }
+      auto put = [&](int x, int32_t vlo, int32_t vhi) {   // node at heap index x
+        const int64_t v = nslot[x];
+        if (ch < 0) {
+          o.live[v] = vlo;
+        } else {
+          o.box[v * 2 * dim + ch] = vlo;
+          o.box[v * 2 * dim + dim + ch] = vhi;
+        }
+      };
+      if (has) put(nleaf + lf, lo, hi);
+      for (int k = 1; k <= kw; ++k) {
+        const int32_t plo = __shfl_xor_sync(0xffffffffu, lo, 1 << (k - 1));
+        const int32_t phi = __shfl_xor_sync(0xffffffffu, hi, 1 << (k - 1));
+        lo = ch < 0 ? lo + plo : min(lo, plo);
+        hi = max(hi, phi);
+        const int idx = lf >> k;         // parent's index at level U - k
+        if ((lane & ((1 << k) - 1)) == 0 && idx < (nleaf >> k)) put((1 << (U - k)) + idx, lo, hi);
+      }
+      if (U > 5) {                       // the warps' subtrees: combined by warp 0
+        if (lane == 0) {
+          wlo[warp] = lo;
+          whi[warp] = hi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          const int nw = nleaf >> 5;     // <= 32
+          lo = lane < nw ? wlo[lane] : (ch < 0 ? 0 : INT32_MAX);
+          hi = lane < nw ? whi[lane] : INT32_MIN;
+          for (int k = 1; k <= U - 5; ++k) {
+            const int32_t plo = __shfl_xor_sync(0xffffffffu, lo, 1 << (k - 1));
+            const int32_t phi = __shfl_xor_sync(0xffffffffu, hi, 1 << (k - 1));
+            lo = ch < 0 ? lo + plo : min(lo, plo);
+            hi = max(hi, phi);
+            const int idx = lane >> k;
+            if ((lane & ((1 << k) - 1)) == 0 && idx < (nw >> k)) put((1 << (U - 5 - k)) + idx, lo, hi);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  } else {
+    // more leaves than threads: leaves first, then each level from its
+    // children in global memory
+    for (int lf = threadIdx.x; lf < nleaf; lf += blockDim.x) {
+      int64_t a64, z64;
+      seg_range(m0, U, lf, a64, z64);
+      int a = (int)a64, z = (int)z64;
+      int64_t leaf = (i0 << U) + lf;
+      int64_t v = veb_slot(l, T.h, leaf);
+      o.node[v] = Node{0, (int32_t)(-1 - leaf), 0};
+      o.live[v] = z;
+      o.leaf_off[leaf] = (int32_t)(start0 + a);
+      if (leaf == nleaves_tree - 1) o.leaf_off[nleaves_tree] = (int32_t)T.s;
       for (int cc = 0; cc < dim; ++cc) {
-        o.box[v * 2 * dim + cc] = min(o.box[vl * 2 * dim + cc], o.box[vr * 2 * dim + cc]);
-        o.box[v * 2 * dim + dim + cc] =
-            max(o.box[vl * 2 * dim + dim + cc], o.box[vr * 2 * dim + dim + cc]);
+        int32_t lo = INT32_MAX, hi = INT32_MIN;
+        for (int q = a; q < a + z; ++q) {
+          int32_t x = sc[cc * cap + cur[q]];
+          lo = min(lo, x);
+          hi = max(hi, x);
+        }
+        o.box[v * 2 * dim + cc] = lo;
+        o.box[v * 2 * dim + dim + cc] = hi;
+      }
+    }
+    // internal nodes of the subtree, bottom-up (children are in global memory)
+    for (int u = U - 1; u >= 0; --u) {
+      __syncthreads();
+      for (int s = threadIdx.x; s < (1 << u); s += blockDim.x) {
+        int64_t bfs = (i0 << u) + s;
+        int t = t0 + u;
+        int64_t v = veb_slot(l, t, bfs);
+        int64_t vl = veb_slot(l, t + 1, 2 * bfs), vr = veb_slot(l, t + 1, 2 * bfs + 1);
+        o.live[v] = o.live[vl] + o.live[vr];
+        for (int cc = 0; cc < dim; ++cc) {
+          o.box[v * 2 * dim + cc] = min(o.box[vl * 2 * dim + cc], o.box[vr * 2 * dim + cc]);
+          o.box[v * 2 * dim + dim + cc] =
+              max(o.box[vl * 2 * dim + dim + cc], o.box[vr * 2 * dim + dim + cc]);
+        }
       }
     }
   }
