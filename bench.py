@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--dim", type=int, default=3)
     ap.add_argument("--leaf", default="auto",
                     help="leaf size, or 'auto': autotuned in {8, 12, 16, 24, 32} on this workload before timing")
+    ap.add_argument("--knn-shape", default="128x32",
+                    help="k-NN launch shape BLOCKxQUERIES_PER_WARP (64/128/256 x 32/64/128) when --leaf "
+                         "is given; with --leaf auto the autotuner picks it after the leaf size")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end steps after the timed ones (default: as many as --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -84,11 +87,25 @@ def parse():
     return a
 
 
+def parse_shape(text):
+    """'BLOCKxQPW' -> (block threads, queries per warp)."""
+    b, q = text.lower().split("x")
+    return int(b), int(q)
+
+
+def shape_record(shape, ms_by_shape, seconds, inputs_text):
+    """The autotune record of the k-NN launch shape."""
+    return {"candidates_ms_per_knn": {"%dx%d" % sh: round(v, 3) for sh, v in ms_by_shape.items()},
+            "chosen": {"block_threads": shape[0], "queries_per_warp": shape[1]},
+            "tuning_s": round(seconds, 2), "inputs": inputs_text}
+
+
 def workload_config(a, n_gpus):
     return {"workload": "3-D uniform int32 forest of %d points; per step insert %d, erase %d "
                         "live ids, k=%d NN for %d live-set queries" % (a.n0, a.batch, a.batch, a.k, a.queries),
             "dim": a.dim, "n0": a.n0, "insert_batch": a.batch, "erase_batch": a.batch,
-            "queries": a.queries, "k": a.k, "leaf_size": a.leaf, "buffer_size": 1024, "split": a.split,
+            "queries": a.queries, "k": a.k, "leaf_size": a.leaf, "knn_shape": a.knn_shape,
+            "buffer_size": 1024, "split": a.split,
             "l2": "flushed between steps (256 MB write), inputs resident in HBM",
             "parallelism": "one independent forest per GPU" if n_gpus > 1 else "single GPU"}
 
@@ -228,7 +245,8 @@ def run_ours(a, rank, world, dist):
     capi.load()
     stream = torch.cuda.Stream(dev)
     # warm-up, timed (profiled), timed again without profiling, end to end
-    nsteps = a.warmup + 2 * a.steps + a.e2e_steps + 1
+    e2e_warm = min(a.warmup, 3) if a.e2e_steps > 0 else 0
+    nsteps = a.warmup + 2 * a.steps + e2e_warm + a.e2e_steps + 1
     W = StepInputs(a.n0, a.batch, a.queries, a.dim, nsteps, seed=2 + 17 * rank)
 
     def H2D(x):
@@ -236,7 +254,7 @@ def run_ours(a, rank, world, dist):
 
     autotune = None
     if a.leaf == "auto":
-        from paper_2112_06188_gb300.autotune import CONFIG_CANDIDATES, choose, tune_leaf_size
+        from paper_2112_06188_gb300.autotune import CONFIG_CANDIDATES, choose, tune_knn_shape, tune_leaf_size
         t0 = time.perf_counter()
         # the tuning forest and steps come from a seed of their own: the
         # timed steps are never seen before they are timed
@@ -245,18 +263,33 @@ def run_ours(a, rank, world, dist):
             tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in TW.steps]
             best, ms_by_leaf = tune_leaf_size(a.dim, H2D(TW.initial), tsteps, a.k, device=dev, stream=stream,
                                               split=a.split)
-        del tsteps, TW
+        del tsteps
         if dist:
             best = rank0_choice(best, dist, dev)
         a.leaf = best
+        t1 = time.perf_counter()
+        with torch.cuda.stream(stream):   # then the k-NN launch shape on a forest of that leaf size
+            tsteps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in TW.steps[:4]]
+            shape, ms_by_shape = tune_knn_shape(a.dim, best, H2D(TW.initial), tsteps, a.k, device=dev,
+                                                stream=stream, split=a.split)
+        del tsteps, TW
+        if dist:
+            code = rank0_choice(shape[0] * 1000 + shape[1], dist, dev)
+            shape = (code // 1000, code % 1000)
+        a.knn_shape = "%dx%d" % shape
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
-                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2),
+                    "chosen": best, "tuning_s": round(t1 - t0, 2),
                     "inputs": "own seed (7919), 8 timed steps after one warm-up; not the timed steps",
                     "config_set": {"candidates": list(CONFIG_CANDIDATES),
-                                   "chosen": choose({L: ms_by_leaf[L] for L in CONFIG_CANDIDATES})}}
+                                   "chosen": choose({L: ms_by_leaf[L] for L in CONFIG_CANDIDATES})},
+                    "knn_shape": shape_record(shape, ms_by_shape, time.perf_counter() - t1,
+                                              "the tuning seed's first 4 steps applied, then their "
+                                              "4 query batches per shape, 2 rounds after one warm-up round")}
     a.leaf = int(a.leaf)
+    shape = parse_shape(a.knn_shape)
     with torch.cuda.stream(stream):
         f = Forest(a.dim, leaf_size=a.leaf, buffer_size=1024, stream=stream, device=dev, split=a.split)
+        f.set_knn_shape(*shape)
         f.insert(H2D(W.initial))
         dev_steps = [(H2D(i), H2D(e), H2D(q)) for (i, e, q) in W.steps]
         out_ids = torch.empty((a.queries, a.k), dtype=torch.int32, device=dev)
@@ -343,7 +376,9 @@ def run_ours(a, rank, world, dist):
     if K > 0:
         import torch as _t
         first = a.warmup + 2 * a.steps
-        idx = list(range(first, first + K))
+        # e2e_warm untimed steps through the same loop and buffers first (each
+        # with its own inputs): the loop's one-time costs stay out of the timing
+        idx = list(range(first, first + e2e_warm + K))
         hin = [tuple(_t.from_numpy(x).pin_memory() for x in W.steps[i]) for i in idx]
         hout = [(_t.empty((a.queries, a.k), dtype=_t.int32).pin_memory(),
                  _t.empty((a.queries, a.k), dtype=_t.int64).pin_memory()) for _ in range(2)]
@@ -363,29 +398,34 @@ def run_ours(a, rank, world, dist):
                     xd.copy_(xh, non_blocking=True)
             ev_in[b].record(h2s)
 
-        _t.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        load(0)
-        for j in range(K):
-            b = j & 1
-            if j + 1 < K:
-                load(j + 1)
-            stream.wait_event(ev_in[b])
-            with _t.cuda.stream(stream):
-                flush.zero_()
-            f.insert(din[b][0])
-            f.erase(din[b][1])
-            stream.wait_event(ev_out[b])                # set b's previous rows are out
-            f.knn(din[b][2], a.k, out=dout[b])
-            ev_used[b].record(stream)
-            d2s.wait_event(ev_used[b])
-            with _t.cuda.stream(d2s):
-                hout[b][0].copy_(dout[b][0], non_blocking=True)
-                hout[b][1].copy_(dout[b][1], non_blocking=True)
-            ev_out[b].record(d2s)
-        d2s.synchronize()
-        stream.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3 / K)
+        def e2e_pass(j0, n):
+            _t.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            load(j0)
+            for j in range(j0, j0 + n):
+                b = j & 1
+                if j + 1 < j0 + n:
+                    load(j + 1)
+                stream.wait_event(ev_in[b])
+                with _t.cuda.stream(stream):
+                    flush.zero_()
+                f.insert(din[b][0])
+                f.erase(din[b][1])
+                stream.wait_event(ev_out[b])            # set b's previous rows are out
+                f.knn(din[b][2], a.k, out=dout[b])
+                ev_used[b].record(stream)
+                d2s.wait_event(ev_used[b])
+                with _t.cuda.stream(d2s):
+                    hout[b][0].copy_(dout[b][0], non_blocking=True)
+                    hout[b][1].copy_(dout[b][1], non_blocking=True)
+                ev_out[b].record(d2s)
+            d2s.synchronize()
+            stream.synchronize()
+            return (time.perf_counter() - t0) * 1e3 / n
+
+        if e2e_warm:
+            e2e_pass(0, e2e_warm)
+        e2e_ms.append(e2e_pass(e2e_warm, K))
         if dist:   # the slowest rank's time, as for the device-timed steps
             e2e_ms[-1] = slowest(e2e_ms[-1], dist, dev)
         h2d = sum(x.numel() * x.element_size() for x in hin[0])
@@ -410,7 +450,7 @@ def forests_config(a, n_gpus):
     return {"workload": "%d independent forests, dim 2 or 3, sizes log-uniform in [1000, 200000], "
                         "uniform int32 points; per step per forest insert 5-20%% of its size, erase "
                         "2-10%% of its live ids, k=%d NN for 1000-5000 live-set queries" % (a.forests, a.k),
-            "forests": a.forests, "k": a.k, "leaf_size": a.leaf, "buffer_size": 1024,
+            "forests": a.forests, "k": a.k, "leaf_size": a.leaf, "knn_shape": a.knn_shape, "buffer_size": 1024,
             "l2": "flushed between steps (256 MB write), inputs resident in HBM",
             "parallelism": "one independent set of forests per GPU" if n_gpus > 1 else "single GPU"}
 
@@ -474,23 +514,42 @@ def run_forests(a, rank, world, dist):
     if a.leaf == "auto" and nsteps < 2:
         a.leaf = 16                      # too few steps to time a candidate: the default
     if a.leaf == "auto":
-        from paper_2112_06188_gb300.autotune import tune_leaf_size_forests
+        from paper_2112_06188_gb300.autotune import tune_knn_shape_forests, tune_leaf_size_forests
         t0 = time.perf_counter()
         T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        # forests and steps of a seed of their own: the timed steps are never
+        # seen before they are timed
+        TW = inputs.ForestsWorkload(nf=a.forests, seed=7919 + 17 * rank)
+        tw_steps = [TW.step() for _ in range(4)]
         with torch.cuda.stream(stream):
-            tinit = [T(p) for p in W.initial]
-            tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in steps[:4]]
-            best, ms_by_leaf = tune_leaf_size_forests(W.dims, tinit, tsteps, a.k, device=dev, stream=stream)
-        del tinit, tsteps
+            tinit = [T(p) for p in TW.initial]
+            tsteps = [[(T(i), T(e), T(q)) for i, e, q in st] for st in tw_steps]
+            best, ms_by_leaf = tune_leaf_size_forests(TW.dims, tinit, tsteps, a.k, device=dev, stream=stream)
         if dist:
             best = rank0_choice(best, dist, dev)
+        t1 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            shape, ms_by_shape = tune_knn_shape_forests(TW.dims, best, tinit, tsteps, a.k, device=dev,
+                                                        stream=stream)
+        del tinit, tsteps, tw_steps
+        if dist:
+            code = rank0_choice(shape[0] * 1000 + shape[1], dist, dev)
+            shape = (code // 1000, code % 1000)
         a.leaf = best
+        a.knn_shape = "%dx%d" % shape
         autotune = {"candidates_ms_per_step": {str(L): round(v, 3) for L, v in ms_by_leaf.items()},
-                    "chosen": best, "tuning_s": round(time.perf_counter() - t0, 2)}
+                    "chosen": best, "tuning_s": round(t1 - t0, 2),
+                    "inputs": "forests and steps of their own seed (7919); not the timed steps",
+                    "knn_shape": shape_record(shape, ms_by_shape, time.perf_counter() - t1,
+                                              "the tuning forests after 4 batched steps, then the 4 steps' "
+                                              "query sets per shape, 2 rounds after one warm-up round")}
     a.leaf = int(a.leaf)
+    shape = parse_shape(a.knn_shape)
     with torch.cuda.stream(stream):
         A = [Forest(d, leaf_size=a.leaf, stream=stream, device=dev) for d in W.dims]
         B = [Forest(d, leaf_size=a.leaf, stream=stream, device=dev) for d in W.dims]
+        for f in A + B:
+            f.set_knn_shape(*shape)
         hA = (ctypes.c_void_p * nf)(*[f._h for f in A])
         hB = [f._h for f in B]
         init = FlatInputs([(p, np.zeros(0, np.int32), np.zeros((0, p.shape[1]), np.int32))
@@ -954,10 +1013,10 @@ def run_sweep(a):
             "sweep": out, "clocks": clk}
 
 
-def recorded_traffic(kernel, leaf):
+def recorded_traffic(kernel, leaf, knn_shape):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
-    when the summary is missing, was captured at another leaf size, or the
-    kernel source changed since the capture."""
+    when the summary is missing, was captured at another leaf size or k-NN
+    launch shape, or the kernel source changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "%s_3d_10M.md" % kernel)
     try:
@@ -966,8 +1025,10 @@ def recorded_traffic(kernel, leaf):
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines()
                   if line.startswith(("kernel_source:", "source_sha256_16:", "dram_bytes_per_launch:",
-                                      "leaf_size:")))
+                                      "leaf_size:", "knn_shape:")))
     if fields.get("leaf_size", "").strip() != str(leaf):
+        return None
+    if fields.get("knn_shape", "128x32").strip() != knn_shape:
         return None
     try:
         src = open(os.path.join(ROOT, fields["kernel_source"].strip()), "rb").read()
@@ -1014,7 +1075,7 @@ def rooflines(a, res, peaks):
         if not algo or not tot_ms or not peak:
             continue
         achieved = algo / (tot_ms * 1e-3) / 1e9
-        traffic = recorded_traffic(name, a.leaf) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
+        traffic = recorded_traffic(name, a.leaf, a.knn_shape) if a.n0 == 10_000_000 and a.queries == 1_000_000 else None
         e = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
              "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
              "ms_per_launch": round(tot_ms / nl, 4), "launches_per_step": round(nl / a.steps, 2),
@@ -1209,6 +1270,7 @@ def main():
         out["e2e"] = {"value": round(ops / (res["e2e_ms"] * 1e-3), 1), "unit": "ops/s",
                       "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"],
                       "ms_per_step": round(res["e2e_ms"], 3), "steps": a.e2e_steps,
+                      "warmup": min(a.warmup, 3),
                       "pipelined": "next inputs in and previous rows out on copy streams during each step"}
     if world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_line(a)

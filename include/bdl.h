@@ -142,6 +142,18 @@ int bdl_knn(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_
 int bdl_knn_noalloc(bdl_forest *f, const int32_t *q_dev, int64_t m, int k, int32_t *out_ids_dev,
                     int64_t *out_d2_dev, bdl_stream_t stream);
 
+/* Launch shape of f's k-NN kernel (a tuning knob of this library; the paper's
+ * kNN_L, Alg. 5, has none): block_threads in {64, 128, 256} (0 = the default
+ * 128; a block is halved while its k top-k slots per thread, 12 bytes each,
+ * would pass 48 KB of shared memory) and queries_per_warp in {32, 64, 128}
+ * (0 = the default 32): each warp answers that many consecutive queries in
+ * the order the call processes them, 32 at a time.  Used by bdl_knn,
+ * bdl_knn_noalloc, bdl_knn_count, and by the batched calls and plans whose
+ * forests[0] is f (a plan keeps the shape it was made with).  Results do not
+ * depend on the shape.  Other values: BDL_EINVAL, shape unchanged.  Host
+ * only; no device work. */
+int bdl_set_knn_shape(bdl_forest *f, int block_threads, int queries_per_warp);
+
 /* ---------------------------------------------------------------------
  * Batched forests: one call runs the same operation on nf independent
  * forests (nf >= 0) of possibly different sizes, sharing kernel launches and

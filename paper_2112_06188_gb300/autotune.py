@@ -1,4 +1,4 @@
-"""Leaf-size autotuner.
+"""Autotuner: leaf size, and the k-NN kernel's block size and queries per warp.
 
 The leaf size L (points per leaf, Sec. V-D) trades tree height -- node
 visits per query and levels per build -- against points scanned per leaf.
@@ -9,8 +9,15 @@ workload's own initial points and time a few steps of it (one insert batch,
 one erase batch, one k-NN batch) with CUDA events; the fastest mean step
 wins, except that the default leaf size is kept unless another candidate is
 faster by more than TIE (step times of neighbouring leaf sizes are often
-within the noise of a few steps).  Every step runs in the CUDA library; this
-module only times calls.
+within the noise of a few steps).
+
+The k-NN launch shape (threads per block, queries per warp) changes neither
+the trees nor the answers, only the k-NN kernel's speed, so it is tuned
+after L on one forest of the chosen L: the tuning steps' updates are applied,
+then every shape answers the same query batches, in round-robin order over
+the shapes so that drift hits them alike; the fastest mean k-NN time wins,
+with the same tie rule towards the default shape.  Every step runs in the
+CUDA library; this module only times calls.
 """
 import numpy as np
 import torch
@@ -22,14 +29,65 @@ CANDIDATES = (8, 12, 16, 24, 32)
 CONFIG_CANDIDATES = (8, 16, 32)   # the leaf sizes the 10M-point 3-D workload names
 DEFAULT = 16
 TIE = 0.01
+# k-NN launch shapes (threads per block, queries per warp)
+SHAPES = tuple((b, q) for b in (64, 128, 256) for q in (32, 64, 128))
+DEFAULT_SHAPE = (128, 32)
 
 
-def choose(ms):
-    """The leaf size to use given {candidate: mean step ms}."""
+def choose(ms, default=DEFAULT):
+    """The candidate to use given {candidate: mean ms}: the fastest, unless
+    the default is within TIE of it."""
     best = min(ms, key=ms.get)
-    if DEFAULT in ms and ms[best] > ms[DEFAULT] * (1.0 - TIE):
-        return DEFAULT
+    if default in ms and ms[best] > ms[default] * (1.0 - TIE):
+        return default
     return best
+
+
+def _time_shapes(forests, run_knn, queries, shapes, reps, stream):
+    """{shape: mean ms of one k-NN call}: every shape answers every query
+    batch `reps` times, shapes interleaved; run_knn(q) issues one call."""
+    L2 = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
+    times = {sh: [] for sh in shapes}
+    for f in forests:                        # one untimed call per shape
+        f.set_knn_shape(*shapes[0])
+    run_knn(queries[0])
+    for r in range(reps + 1):
+        for q in queries:
+            for sh in shapes:
+                for f in forests:
+                    f.set_knn_shape(*sh)
+                with torch.cuda.stream(stream):
+                    L2.zero_()               # no query batch starts with a warm L2
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                run_knn(q)
+                b.record(stream)
+                b.synchronize()
+                if r:                        # the first round warms every shape up
+                    times[sh].append(a.elapsed_time(b))
+    for f in forests:
+        f.set_knn_shape(*DEFAULT_SHAPE)
+    return {sh: float(np.mean(v)) for sh, v in times.items()}
+
+
+def tune_knn_shape(dim, leaf, initial, steps, k, shapes=SHAPES, reps=2, device=None, stream=None,
+                   split="object"):
+    """The fastest k-NN launch shape (block threads, queries per warp) for a
+    forest of leaf size `leaf` after the updates of `steps` (device-tensor
+    triples as in tune_leaf_size), timed on the steps' query batches; and the
+    mean k-NN ms of each shape."""
+    stream = stream or torch.cuda.current_stream(device)
+    f = Forest(dim, leaf_size=leaf, stream=stream, device=device, split=split)
+    try:
+        f.insert(initial)
+        for ins, era, _ in steps:
+            f.insert(ins)
+            f.erase(era)
+        ms = _time_shapes([f], lambda q: f.knn(q, k), [q for _, _, q in steps], list(shapes), reps, stream)
+        return choose(ms, DEFAULT_SHAPE), ms
+    finally:
+        f.close()
 
 
 def time_steps(dim, leaf, initial, steps, k, device=None, stream=None, split="object"):
@@ -114,6 +172,28 @@ def time_forests_step(dims, leaf, initial, steps, k, device=None, stream=None, s
             if i:
                 times.append(a.elapsed_time(b))
         return float(np.mean(times))
+    finally:
+        for f in forests:
+            f.close()
+
+
+def tune_knn_shape_forests(dims, leaf, initial, steps, k, shapes=SHAPES, reps=2, device=None, stream=None,
+                           split="object"):
+    """tune_knn_shape for a batched many-forest workload: the forests take
+    the steps' updates in batched calls, then every shape answers the steps'
+    batched query sets (the batched call launches with the first forest's
+    shape; every forest gets the same)."""
+    from .forest import erase_batch, insert_batch, knn_batch
+    stream = stream or torch.cuda.current_stream(device)
+    forests = [Forest(d, leaf_size=leaf, stream=stream, device=device, split=split) for d in dims]
+    try:
+        insert_batch(forests, initial, stream=stream)
+        for st in steps:
+            insert_batch(forests, [x for x, _, _ in st], stream=stream)
+            erase_batch(forests, [e for _, e, _ in st], stream=stream)
+        ms = _time_shapes(forests, lambda qs: knn_batch(forests, qs, k, stream=stream),
+                          [[q for _, _, q in st] for st in steps], list(shapes), reps, stream)
+        return choose(ms, DEFAULT_SHAPE), ms
     finally:
         for f in forests:
             f.close()

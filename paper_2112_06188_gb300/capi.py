@@ -22,7 +22,7 @@ SYMBOLS = [
     "bdl_server_default_config", "bdl_server_create", "bdl_server_submit", "bdl_server_wait",
     "bdl_server_drain", "bdl_server_stats", "bdl_server_destroy", "bdl_server_now_ms",
     "bdl_knn_plan_create", "bdl_knn_plan_launch", "bdl_knn_plan_destroy", "bdl_next_id",
-    "bdl_knn_count", "bdl_poll_error", "bdl_profile_read_bytes", "bdl_profile_timeline",
+    "bdl_knn_count", "bdl_poll_error", "bdl_profile_read_bytes", "bdl_profile_timeline", "bdl_set_knn_shape",
 ]
 
 BDL_REQ_INSERT, BDL_REQ_ERASE, BDL_REQ_KNN = 0, 1, 2
@@ -115,6 +115,7 @@ def load(path=None):
         "bdl_next_id": (i32, [P, P]),
         "bdl_knn_count": (i32, [P, P, i64, i32, P, P, P, P]),
         "bdl_poll_error": (i32, [P, P, P]),
+        "bdl_set_knn_shape": (i32, [P, i32, i32]),
         "bdl_profile_read_bytes": (i32, [P, P, P, i32]),
         "bdl_profile_timeline": (i32, [P, P, P, P, i32, P]),
     }
@@ -186,6 +187,11 @@ def bdl_poll_error(f, stream):
     bits = ctypes.c_uint64(0)
     st = load().bdl_poll_error(f, _ref(bits), stream)
     return st, bits.value
+
+
+def bdl_set_knn_shape(f, block_threads, queries_per_warp):
+    """Launch shape of the forest's k-NN kernel (block size, queries per warp)."""
+    return load().bdl_set_knn_shape(f, block_threads, queries_per_warp)
 
 
 def bdl_knn_noalloc(f, q_dev, m, k, out_ids_dev, out_d2_dev, stream):

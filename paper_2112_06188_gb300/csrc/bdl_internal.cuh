@@ -55,6 +55,7 @@ enum KernelId : int {
   kK_sp_split,
   kK_sp_box,
   kK_knn_count,
+  kK_small_copy,
   kKernelCount
 };
 extern const char *const kKernelNames[kKernelCount];
@@ -381,6 +382,14 @@ struct BuildTree {
 
 struct Scratch;            // allocation helper (forest.cu)
 
+// Launch shape of the k-NN kernels (results do not depend on it): threads
+// per block (64, 128 or 256; halved while k slots per thread would pass 48 KB
+// of shared memory) and queries per warp (32, 64 or 128: a warp answers that
+// many consecutive queries of its job, 32 at a time).
+struct KnnShape {
+  int block = 128;
+  int qpw = 32;
+};
 }  // namespace bdl
 
 struct bdl_forest {
@@ -402,12 +411,14 @@ struct bdl_forest {
   int64_t bytes_in_use = 0;
   int64_t *pinned = nullptr;     // pinned host scratch [kPinnedWords]: [0, kPinnedFlags) insert
                                  // flags, [kPinnedErr] the error word
+  int64_t *pinned_dev = nullptr; // its device address (mapped page-locked memory)
   int64_t *dev_small = nullptr;  // small device scratch for counts / flags
   unsigned long long *err = nullptr;  // device error word (inside dev_small)
   bool debug_check = false;      // BDL_DEBUG_CHECK=1: sync and check err after each call
   unsigned long long *knn_stats = nullptr;  // [3] device counters, or nullptr
   uint64_t version = 0;          // bumped by every change of the trees or the buffer
   cudaEvent_t ev_flags = nullptr;  // recorded behind the insert flags' copy
+  bdl::KnnShape knn_shape;         // launch shape of its k-NN calls
 };
 
 namespace bdl {
@@ -421,6 +432,20 @@ void dev_free(bdl_forest *f, void *p, size_t bytes, cudaStream_t s);
 // memory, ordered on `s`, without making the host wait for the stream; the
 // source may be reused when this returns.  Legal while `s` is capturing.
 int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// A small copy between device memory and page-locked host memory (which the
+// device reaches directly, unified addressing), done by a kernel on `s`
+// instead of a copy engine: the caller's own large transfers queued on the
+// copy engines cannot delay it.
+int small_copy(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// Zero a device buffer with a kernel (not a copy-engine memset), for the
+// same reason.
+int small_zero(void *dst, size_t bytes, cudaStream_t s);
+// Page-locked host scratch for readbacks, from a pool (returned by
+// pinned_put); nullptr if none can be had.
+void *pinned_get(size_t bytes);
+void pinned_put(void *p);
+// The device address of mapped page-locked host memory (nullptr if none).
+void *mapped(void *host);
 ForestView forest_view(const bdl_forest *f);
 // The view k-NN uses: the static trees plus the buffer's kd-tree.  With
 // build = true a stale buffer tree is rebuilt first (this allocates); with
@@ -596,12 +621,13 @@ size_t knn_table_bytes(const std::vector<KnnCall> &calls);
 // `calls` (knn_table_bytes_always bytes at `table`; *warps = warps to launch),
 // then launch it as often as wanted.
 size_t knn_table_bytes_always(const std::vector<KnnCall> &calls);
-int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, cudaStream_t s);
-int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, unsigned long long *stats,
+int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, int qpw,
                      cudaStream_t s);
+int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, const KnnShape &sh,
+                     unsigned long long *stats, cudaStream_t s);
 // k-NN for every call (all of dimension `dim`) in one launch; the job table
 // is uploaded to `table` (knn_table_bytes of device memory) on stream s.
-int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,
+int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, const KnnShape &sh, void *table,
                     unsigned long long *stats, cudaStream_t s);
 // The packed k-NN records of many trees (Sec. V-B's per-node data, laid out
 // for the query kernel): table entries and their work prefix ...

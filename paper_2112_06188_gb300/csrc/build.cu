@@ -1448,7 +1448,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   }
   st = h2d(plan, img.bytes.data(), img.bytes.size(), s);
   // segment states, histograms and cursors (contiguous) start at zero
-  if (!st) st = cuda_check(cudaMemsetAsync(seg, 0, seg_bytes + hist_bytes + cursor_bytes, s), "memset");
+  if (!st) st = small_zero(seg, seg_bytes + hist_bytes + cursor_bytes, s);
   if (st) {
     dev_free(af, block, total, s);
     return st;

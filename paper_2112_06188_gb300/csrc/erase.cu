@@ -397,7 +397,7 @@ int collect_sorted_live(const std::vector<LiveCollect> &jobs, cudaStream_t s) {
     return st;
   }
   st = h2d(tab, img.data(), img.size(), s);
-  if (!st) st = cuda_check(cudaMemsetAsync(blk, 0, bm_bytes, s), "memset");
+  if (!st) st = small_zero(blk, bm_bytes, s);
   const char *T = (const char *)tab;
   const int nt = (int)mt.size(), nf = (int)bf.size();
   if (!st && tpre.back() > 0) {

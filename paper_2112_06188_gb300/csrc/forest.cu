@@ -48,6 +48,7 @@ const char *const kKernelNames[kKernelCount] = {
     "k_sp_split",
     "k_sp_box",
     "k_knn_count",
+    "k_small_copy",
 };
 
 // ---- live per-kernel timing (CUDA events on the launching stream) ----
@@ -186,6 +187,7 @@ __global__ void k_put_blob(const Blob b, unsigned char *dst, int bytes) {
 
 struct Ring {
   unsigned char *base = nullptr;
+  unsigned char *dbase = nullptr;   // its device address
   size_t head = 0;
   struct Use {
     size_t off, len;
@@ -198,6 +200,102 @@ std::mutex g_ring_mu;
 Ring g_ring[128];
 
 }  // namespace
+
+namespace {
+
+// Word-wise copy between device-accessible buffers (8-byte words when both
+// ends are 8-byte aligned, bytes otherwise).
+__global__ void k_small_copy(const unsigned char *src, unsigned char *dst, size_t bytes) {
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+  if ((((uintptr_t)src | (uintptr_t)dst) & 7) == 0) {
+    const size_t nw = bytes / 8;
+    const uint64_t *s8 = (const uint64_t *)src;
+    uint64_t *d8 = (uint64_t *)dst;
+    for (size_t i = i0; i < nw; i += step) d8[i] = s8[i];
+    for (size_t i = nw * 8 + i0; i < bytes; i += step) dst[i] = src[i];
+  } else {
+    for (size_t i = i0; i < bytes; i += step) dst[i] = src[i];
+  }
+}
+
+// Zero fill of a device buffer (8-byte words when aligned).
+__global__ void k_zero(unsigned char *dst, size_t bytes) {
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+  if (((uintptr_t)dst & 7) == 0) {
+    const size_t nw = bytes / 8;
+    uint64_t *d8 = (uint64_t *)dst;
+    for (size_t i = i0; i < nw; i += step) d8[i] = 0;
+    for (size_t i = nw * 8 + i0; i < bytes; i += step) dst[i] = 0;
+  } else {
+    for (size_t i = i0; i < bytes; i += step) dst[i] = 0;
+  }
+}
+
+std::mutex g_pin_mu;
+std::vector<std::pair<void *, size_t>> g_pin_free;   // page-locked buffers not in use
+std::vector<std::pair<void *, size_t>> g_pin_used;
+
+}  // namespace
+
+// Page-locked, device-mapped host memory, and the address kernels use for it.
+static int host_alloc_mapped(void **p, size_t bytes) {
+  return cuda_check(cudaHostAlloc(p, bytes, cudaHostAllocMapped | cudaHostAllocPortable), "cudaHostAlloc");
+}
+
+void *mapped(void *host) {
+  void *d = nullptr;
+  if (cudaHostGetDevicePointer(&d, host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return d;
+}
+
+int small_copy(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BDL_OK;
+  const size_t words = (bytes + 7) / 8;
+  const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 64);
+  KScope ks_(kK_small_copy, s);
+  k_small_copy<<<blocks, 256, 0, s>>>((const unsigned char *)src, (unsigned char *)dst, bytes);
+  return cuda_check(cudaGetLastError(), "small copy");
+}
+
+int small_zero(void *dst, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BDL_OK;
+  const size_t words = (bytes + 7) / 8;
+  const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 2048);
+  KScope ks_(kK_small_copy, s);
+  k_zero<<<blocks, 256, 0, s>>>((unsigned char *)dst, bytes);
+  return cuda_check(cudaGetLastError(), "zero fill");
+}
+
+void *pinned_get(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  for (size_t i = 0; i < g_pin_free.size(); ++i)
+    if (g_pin_free[i].second >= bytes) {
+      auto b = g_pin_free[i];
+      g_pin_free.erase(g_pin_free.begin() + (long)i);
+      g_pin_used.push_back(b);
+      return b.first;
+    }
+  size_t sz = 4096;
+  while (sz < bytes) sz *= 2;
+  void *p = nullptr;
+  if (host_alloc_mapped(&p, sz) != BDL_OK) return nullptr;
+  g_pin_used.push_back({p, sz});
+  return p;
+}
+
+void pinned_put(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  for (size_t i = 0; i < g_pin_used.size(); ++i)
+    if (g_pin_used[i].first == p) {
+      g_pin_free.push_back(g_pin_used[i]);
+      g_pin_used.erase(g_pin_used.begin() + (long)i);
+      return;
+    }
+}
 
 int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return BDL_OK;
@@ -224,8 +322,14 @@ int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_ring_mu);
   Ring &R = g_ring[dev];
   if (!R.base) {
-    st = cuda_check(cudaMallocHost((void **)&R.base, kRingBytes), "cudaMallocHost(table ring)");
+    st = host_alloc_mapped((void **)&R.base, kRingBytes);
     if (st) return st;
+    R.dbase = (unsigned char *)mapped(R.base);
+    if (!R.dbase) {
+      cudaFreeHost(R.base);
+      R.base = nullptr;
+      return set_error(BDL_ECUDA, "table ring is not device-mapped");
+    }
   }
   if (R.head + len > kRingBytes) R.head = 0;
   const size_t lo = R.head, hi = R.head + len;
@@ -241,7 +345,7 @@ int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     }
   }
   memcpy(R.base + lo, src, bytes);
-  st = cuda_check(cudaMemcpyAsync(dst, R.base + lo, bytes, cudaMemcpyHostToDevice, s), "table upload");
+  st = small_copy(dst, R.dbase + lo, bytes, s);   // not behind the caller's transfers on a copy engine
   if (st) return st;
   cudaEvent_t ev = nullptr;
   if (!R.spare.empty()) {
@@ -763,7 +867,7 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   if (!st) st = tmp.get(table_bytes(app.size(), sizeof(FillSeg)), &table);
   if (st) return st;
   for (size_t j = 0; j < app.size(); ++j) app[j].flag = (unsigned long long *)flags + j;
-  cudaMemsetAsync(flags, 0, app.size() * 8, s);
+  small_zero(flags, app.size() * 8, s);
   st = launch_fill_many(app, table, s);
   // The append stores off-grid coordinates clamped onto the grid and flags
   // them.  With room for the flags in the forest's pinned scratch, the build
@@ -777,7 +881,8 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
     hf_big.resize(app.size());
     hf = hf_big.data();
   }
-  if (!st) st = cuda_check(cudaMemcpyAsync(hf, flags, app.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  if (!st && ahead) st = small_copy(F[0]->pinned_dev, flags, app.size() * 8, s);   // the forest's mapped scratch
+  if (!st && !ahead) st = cuda_check(cudaMemcpyAsync(hf, flags, app.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
   if (!st && ahead) {
     if (!F[0]->ev_flags) st = cuda_check(cudaEventCreateWithFlags(&F[0]->ev_flags, cudaEventDisableTiming),
                                          "cudaEventCreate");
@@ -914,7 +1019,7 @@ static int erase_core(bdl_forest *const *F, int nf, const std::vector<EraseList>
     rank[u] = seen[e.forest]++;
     nrank = std::max(nrank, rank[u] + 1);
   }
-  cudaMemsetAsync(counts, 0, (use.size() + na) * 8, s);
+  small_zero(counts, (use.size() + na) * 8, s);
   for (int r = 0; r < nrank && !st; ++r) {
     std::vector<MarkSeg> mk;
     for (size_t u = 0; u < use.size(); ++u) {
@@ -1063,9 +1168,29 @@ static int erase_core(bdl_forest *const *F, int nf, const std::vector<EraseList>
   }
   st = tmp.get(table_bytes(bufs.size(), sizeof(BufSeg)), &bt2);
   if (!st) st = launch_buffer_compact_many(bufs, bt2, s);
-  std::vector<int64_t> ho(na * kBufOutWords), hc(use.size() + na);
-  if (!st) st = cuda_check(cudaMemcpyAsync(ho.data(), outs, ho.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
-  if (!st) st = cuda_check(cudaMemcpyAsync(hc.data(), counts, hc.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+  // counts back through page-locked scratch written by a kernel (not behind
+  // the caller's transfers on a copy engine)
+  const size_t nho = na * kBufOutWords, nhc = use.size() + na;
+  struct PinGuard {
+    void *p;
+    ~PinGuard() { pinned_put(p); }
+  } pin{pinned_get((nho + nhc) * 8)};
+  std::vector<int64_t> ho_v, hc_v;
+  int64_t *ho, *hc;
+  int64_t *pin_dev = pin.p ? (int64_t *)mapped(pin.p) : nullptr;
+  if (pin_dev) {
+    ho = (int64_t *)pin.p;
+    hc = ho + nho;
+    if (!st) st = small_copy(pin_dev, outs, nho * 8, s);
+    if (!st) st = small_copy(pin_dev + nho, counts, nhc * 8, s);
+  } else {
+    ho_v.resize(nho);
+    hc_v.resize(nhc);
+    ho = ho_v.data();
+    hc = hc_v.data();
+    if (!st) st = cuda_check(cudaMemcpyAsync(ho, outs, nho * 8, cudaMemcpyDeviceToHost, s), "copy");
+    if (!st) st = cuda_check(cudaMemcpyAsync(hc, counts, nhc * 8, cudaMemcpyDeviceToHost, s), "copy");
+  }
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
   // 5. new counts; trees below half capacity are emptied and their points
@@ -1282,7 +1407,7 @@ static int knn_many(bdl_forest *const *F, int nf, const int32_t *const *q, const
     void *table = nullptr;
     const size_t tb = knn_table_bytes(g);
     if (tb) st = tmp.get(tb, &table);
-    if (!st) st = launch_knn_jobs(g, d, k, table, stats, s);
+    if (!st) st = launch_knn_jobs(g, d, k, F[0]->knn_shape, table, stats, s);
     if (st) return st;
   }
   return BDL_OK;
@@ -1301,6 +1426,7 @@ struct bdl_knn_plan {
     int64_t warps;
     void *table;
     unsigned long long *stats;
+    bdl::KnnShape shape;
   };
   struct Sort {
     const int32_t *q;
@@ -1371,8 +1497,8 @@ static int knn_plan_make(bdl_forest *const *F, int nf, const int32_t *const *q, 
     unsigned long long *stats = nullptr;
     for (int i = 0; i < nf; ++i)
       if (F[i]->dim == d && F[i]->knn_stats) stats = F[i]->knn_stats;
-    bdl_knn_plan::Part part{d, (int)groups[gi].size(), 0, p, stats};
-    st = upload_knn_table(groups[gi], p, &part.warps, s);
+    bdl_knn_plan::Part part{d, (int)groups[gi].size(), 0, p, stats, F[0]->knn_shape};
+    st = upload_knn_table(groups[gi], p, &part.warps, part.shape.qpw, s);
     if (st) return st;
     p += a256(knn_table_bytes_always(groups[gi]));
     P->parts.push_back(part);
@@ -1390,7 +1516,7 @@ static int knn_plan_launch(bdl_knn_plan *P, cudaStream_t s) {
       return set_error(BDL_EINVAL, "a forest changed since the k-NN plan was made");
   for (auto &so : P->sorts) launch_query_sort(so.q, so.m, so.dim, so.scratch, so.perm, s);
   for (auto &part : P->parts) {
-    const int st = launch_knn_table(part.table, part.njobs, part.warps, part.dim, P->k, part.stats, s);
+    const int st = launch_knn_table(part.table, part.njobs, part.warps, part.dim, P->k, part.shape, part.stats, s);
     if (st) return st;
   }
   return BDL_OK;
@@ -1400,7 +1526,7 @@ static int knn_plan_launch(bdl_knn_plan *P, cudaStream_t s) {
 // BDL_EINTERNAL if one of them recorded an out-of-range index.
 static int finish(bdl_forest *f, cudaStream_t s, int st) {
   if (st || !f->debug_check) return st;
-  st = cuda_check(cudaMemcpyAsync(f->pinned + kPinnedErr, f->err, 8, cudaMemcpyDeviceToHost, s), "copy");
+  st = small_copy(f->pinned_dev + kPinnedErr, f->err, 8, s);
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "sync");
   if (st) return st;
   if (f->pinned[kPinnedErr])
@@ -1551,7 +1677,11 @@ int bdl_create(int dim, const bdl_config *cfg, const int32_t *pts, int64_t n, in
   cudaStream_t s = (cudaStream_t)stream;
   st = cuda_check(cudaGetDevice(&f->device), "cudaGetDevice");
   if (!st) st = get_pool(f->device, &f->pool);
-  if (!st) st = cuda_check(cudaMallocHost((void **)&f->pinned, kPinnedWords * 8), "cudaMallocHost");
+  if (!st) st = host_alloc_mapped((void **)&f->pinned, kPinnedWords * 8);
+  if (!st) {
+    f->pinned_dev = (int64_t *)mapped(f->pinned);
+    if (!f->pinned_dev) st = set_error(BDL_ECUDA, "page-locked scratch is not device-mapped");
+  }
   void *small = nullptr;
   if (!st) st = dev_alloc(f, &small, 4096, s);
   f->dev_small = (int64_t *)small;
@@ -1623,7 +1753,7 @@ int bdl_poll_error(const bdl_forest *f, uint64_t *out_bits, bdl_stream_t stream)
   if (!f) return set_error(BDL_EINVAL, "forest is NULL");
   DeviceGuard g(f->device);
   cudaStream_t s = (cudaStream_t)stream;
-  int st = cuda_check(cudaMemcpyAsync(f->pinned + kPinnedErr, f->err, 8, cudaMemcpyDeviceToHost, s), "copy");
+  int st = small_copy(f->pinned_dev + kPinnedErr, f->err, 8, s);
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "sync");
   if (st) return st;
   const uint64_t bits = (uint64_t)f->pinned[kPinnedErr];
@@ -1782,6 +1912,16 @@ int bdl_bloom_export(const bdl_forest *f, int level, uint32_t *words, bdl_stream
   int st = cuda_check(cudaMemcpyAsync(words, t->bloom, t->bloom_bytes, cudaMemcpyDeviceToHost, s), "copy");
   if (st) return st;
   return cuda_check(cudaStreamSynchronize(s), "sync");
+}
+
+int bdl_set_knn_shape(bdl_forest *f, int block_threads, int queries_per_warp) {
+  if (!f) return set_error(BDL_EINVAL, "forest is NULL");
+  const int b = block_threads ? block_threads : 128, q = queries_per_warp ? queries_per_warp : 32;
+  if (b != 64 && b != 128 && b != 256) return set_error(BDL_EINVAL, "block_threads must be 64, 128 or 256");
+  if (q != 32 && q != 64 && q != 128) return set_error(BDL_EINVAL, "queries_per_warp must be 32, 64 or 128");
+  f->knn_shape.block = b;
+  f->knn_shape.qpw = q;
+  return BDL_OK;
 }
 
 int bdl_knn_stats(bdl_forest *f, int enable, int64_t *out) {

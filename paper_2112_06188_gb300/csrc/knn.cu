@@ -32,13 +32,23 @@ namespace {
 constexpr int kStack = 2 * kMaxLevel + 4;
 constexpr uint64_t kNone = ~0ull;
 
+// k-NN blocks: the default shape (128 threads, 32 queries per warp) runs an
+// instance compiled for exactly that launch; every other shape (KnnShape:
+// 64, 128 or 256 threads, 32, 64 or 128 queries per warp) runs the general
+// instance, compiled for blocks of up to 256 threads with the same register
+// budget (256 x 6 = 128 x 12 threads per SM).
 constexpr int kKnnThreads = 128;
+constexpr int kKnnMaxThreads = 256;
 
 // The k best candidates of one query, sorted by (d2, id), live in shared
-// memory ([slot][thread], so a warp's accesses hit 32 different banks); only
-// the current k-th pair stays in registers for the pruning tests.
+// memory with a warp's 32 lanes in consecutive words, so that its accesses
+// hit 32 different banks: [slot][thread] (slot stride S = the block size)
+// in the default-shape instance, [warp][slot][lane] (S = 32) in the general
+// one, whose block size is a launch parameter.  Only the current k-th pair
+// stays in registers for the pruning tests.
+template <int S>
 struct TopK {
-  uint64_t *d;     // d[j * kKnnThreads]
+  uint64_t *d;     // d[j * S]
   int32_t *id;
   int n;           // entries held (<= k)
   uint64_t kd;     // current k-th distance (kNone while fewer than k held)
@@ -46,9 +56,10 @@ struct TopK {
 
   float kdf;       // kd rounded up to float (pruning bound)
 
-  __device__ __forceinline__ void init(uint64_t *sd, int32_t *sid) {
-    d = sd + threadIdx.x;
-    id = sid + threadIdx.x;
+  __device__ __forceinline__ void init(uint64_t *sd, int32_t *sid, int k) {
+    const int at = S == 32 ? (threadIdx.x >> 5) * k * 32 + (threadIdx.x & 31) : threadIdx.x;
+    d = sd + at;
+    id = sid + at;
     n = 0;
     kd = kNone;
     kid = INT32_MAX;
@@ -61,19 +72,19 @@ struct TopK {
   __device__ __forceinline__ void insert(uint64_t x, int32_t i, int k) {
     int j = n < k ? n : k - 1;
     while (j > 0) {
-      uint64_t pd = d[(j - 1) * kKnnThreads];
-      int32_t pi = id[(j - 1) * kKnnThreads];
+      uint64_t pd = d[(j - 1) * S];
+      int32_t pi = id[(j - 1) * S];
       if (!(x < pd || (x == pd && i < pi))) break;
-      d[j * kKnnThreads] = pd;
-      id[j * kKnnThreads] = pi;
+      d[j * S] = pd;
+      id[j * S] = pi;
       --j;
     }
-    d[j * kKnnThreads] = x;
-    id[j * kKnnThreads] = i;
+    d[j * S] = x;
+    id[j * S] = i;
     if (n < k) n++;
     if (n == k) {
-      kd = d[(k - 1) * kKnnThreads];
-      kid = id[(k - 1) * kKnnThreads];
+      kd = d[(k - 1) * S];
+      kid = id[(k - 1) * S];
       kdf = __ull2float_ru(kd);
     }
   }
@@ -136,9 +147,9 @@ __device__ __forceinline__ void cmp_swap(float &a, int &ca, float &b, int &cb) {
 // rounded-up k-th distance only for a point whose exact distance exceeds the
 // k-th), then the exact int64 distance for the points that pass.  Erased
 // points (negative ids) are skipped.
-template <int D, bool STATS>
+template <int D, bool STATS, class TK>
 __device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, const int32_t *q, int dim,
-                                          int rs, int k, TopK &best, unsigned long long &npts) {
+                                          int rs, int k, TK &best, unsigned long long &npts) {
   for (int j = pa; j < pz; ++j) {
     const int32_t *src = T.pts + (int64_t)j * rs;
     int32_t id;
@@ -185,9 +196,9 @@ __device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, con
 // to visit held in a register, the rest on a stack), and the leaves that come
 // due wait until half of the working lanes have one, so that the warp
 // scans them together.  A record gives the bounds of four entries at once.
-template <int D>
+template <int D, class TK>
 __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, bool active,
-                                            const int32_t *q, int dim, int k, TopK &best,
+                                            const int32_t *q, int dim, int k, TK &best,
                                             uint64_t *stk) {
   const int rec = packed_node_ints(dim);
   const int rs = rec_ints(dim);
@@ -296,9 +307,9 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
 // the nodes it visits (a node or leaf taken from the stack and not pruned, or
 // a nearer child that is a leaf) and the live leaf points it examines: the
 // counting instance of the kernel, for measurement runs.
-template <int D>
+template <int D, class TK>
 __device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, const int32_t *q,
-                                           int dim, int k, TopK &best, uint64_t *stk,
+                                           int dim, int k, TK &best, uint64_t *stk,
                                            unsigned long long &nvisit, unsigned long long &npts) {
   const int rs = rec_ints(dim);
   const float kInf = __int_as_float(0x7f800000);
@@ -353,13 +364,13 @@ __device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, c
 // J.ntrees), then the buffer.  The timed instance (STATS false) is called by
 // whole warps of one job, which stay resident and converged until each of
 // their lanes is done; the counting instance walks each lane on its own.
-template <int D, bool STATS>
+template <int D, bool STATS, int S>
 __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees, int64_t t, int k,
                                           unsigned long long *stats) {
-  // k (d2, id) slots per thread: [slot][thread]
+  // k (d2, id) slots per thread (TopK<S>'s layout)
   extern __shared__ __align__(8) unsigned char knn_sm[];
   uint64_t *s_d = reinterpret_cast<uint64_t *>(knn_sm);
-  int32_t *s_id = reinterpret_cast<int32_t *>(s_d + (size_t)k * kKnnThreads);
+  int32_t *s_id = reinterpret_cast<int32_t *>(s_d + (size_t)k * blockDim.x);
   const int64_t m = J.m;
   const int32_t *qs = J.q, *perm = J.perm;
   int32_t *out_ids = J.oi;
@@ -372,8 +383,8 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
 #pragma unroll
   for (int c = 0; c < (D ? D : kMaxDim); ++c)
     if (c < dim) q[c] = active ? qs[qi * dim + c] : 0;
-  TopK best;
-  best.init(s_d, s_id);
+  TopK<S> best;
+  best.init(s_d, s_id, k);
   unsigned long long nvisit = 0, npts = 0;
   uint64_t stk[kStack];   // (distance bits << 32) | code
 
@@ -403,8 +414,8 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
   int64_t *od = out_d2 + qi * k;
   for (int j = 0; j < k; ++j) {
     const bool ok = j < best.n;
-    oi[j] = ok ? best.id[j * kKnnThreads] : -1;
-    od[j] = ok ? (int64_t)best.d[j * kKnnThreads] : INT64_MAX;
+    oi[j] = ok ? best.id[j * S] : -1;
+    od[j] = ok ? (int64_t)best.d[j * S] : INT64_MAX;
   }
   if (STATS) {
     atomicAdd(&stats[0], nvisit);
@@ -413,15 +424,26 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
   }
 }
 
-// Many forests: every warp finds its job in the table (jobs are warp-aligned).
-template <int D, bool STATS>
-__global__ void __launch_bounds__(kKnnThreads, 12) k_knn(const KnnJob *jobs, const int64_t *job_warp,
-                                                         int njobs, int k,
-                                                         unsigned long long *stats) {
+// Many forests: every warp finds its job in the table (jobs are warp-aligned:
+// job j owns ceil(m_j / qpw) warps).  A warp answers qpw consecutive queries
+// of its job (in the job's processing order), 32 at a time; every round ends
+// with the warp converged.  GEN false: the default shape (qpw = 32).
+template <int D, bool STATS, bool GEN>
+__global__ void __launch_bounds__(GEN ? kKnnMaxThreads : kKnnThreads, GEN ? 6 : 12)
+    k_knn(const KnnJob *jobs, const int64_t *job_warp, int njobs, int k, int qpw, unsigned long long *stats) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= job_warp[njobs]) return;
   const int jb = knn_find(job_warp, njobs, w);
-  knn_query<D, STATS>(jobs[jb], jobs[jb].trees, (w - job_warp[jb]) * 32 + (threadIdx.x & 31), k, stats);
+  if (!GEN) {
+    knn_query<D, STATS, kKnnThreads>(jobs[jb], jobs[jb].trees, (w - job_warp[jb]) * 32 + (threadIdx.x & 31), k,
+                                     stats);
+    return;
+  }
+  const int64_t t0 = (w - job_warp[jb]) * qpw, m = jobs[jb].m;
+  for (int r = 0; r < qpw && t0 + r < m; r += 32) {   // warp-uniform bounds
+    knn_query<D, STATS, 32>(jobs[jb], jobs[jb].trees, t0 + r + (threadIdx.x & 31), k, stats);
+    __syncwarp();
+  }
 }
 
 // One forest: its job and tree views travel as kernel parameters, read
@@ -431,35 +453,64 @@ struct KnnOne {
   TreeView trees[kMaxLevel];
 };
 
-template <int D, bool STATS>
-__global__ void __launch_bounds__(kKnnThreads, 12) k_knn_one(const __grid_constant__ KnnOne P, int k,
-                                                             unsigned long long *stats) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((t & ~(int64_t)31) >= P.job.m) return;     // whole warp past the end
-  knn_query<D, STATS>(P.job, P.trees, t, k, stats);
+template <int D, bool STATS, bool GEN>
+__global__ void __launch_bounds__(GEN ? kKnnMaxThreads : kKnnThreads, GEN ? 6 : 12)
+    k_knn_one(const __grid_constant__ KnnOne P, int k, int qpw, unsigned long long *stats) {
+  if (!GEN) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((t & ~(int64_t)31) >= P.job.m) return;     // whole warp past the end
+    knn_query<D, STATS, kKnnThreads>(P.job, P.trees, t, k, stats);
+    return;
+  }
+  const int64_t t0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * qpw;
+  for (int r = 0; r < qpw && t0 + r < P.job.m; r += 32) {   // warp-uniform bounds
+    knn_query<D, STATS, 32>(P.job, P.trees, t0 + r + (threadIdx.x & 31), k, stats);
+    __syncwarp();
+  }
+}
+
+// The block size actually launched for shape sh and k: the requested one,
+// halved while k slots per thread would pass 48 KB of shared memory.
+int knn_block_for(const KnnShape &sh, int k) {
+  int b = sh.block;
+  while (b > 32 && (size_t)k * b * 12 > 48 * 1024) b >>= 1;
+  return b;
 }
 
 template <int D>
 void launch_d(const KnnJob *jobs, const int64_t *job_warp, int njobs, int64_t warps, int k,
-              unsigned long long *stats, cudaStream_t s) {
-  const size_t smem = (size_t)k * kKnnThreads * 12;   // <= 48 KB for k <= 32
+              const KnnShape &sh, unsigned long long *stats, cudaStream_t s) {
+  const int bt = knn_block_for(sh, k);
+  const size_t smem = (size_t)k * bt * 12;   // <= 48 KB
   KScope ks_(stats ? kK_knn_count : kK_knn, s);
-  const unsigned grid = (unsigned)((warps * 32 + kKnnThreads - 1) / kKnnThreads);
-  if (stats)
-    k_knn<D, true><<<grid, kKnnThreads, smem, s>>>(jobs, job_warp, njobs, k, stats);
+  const unsigned grid = (unsigned)((warps * 32 + bt - 1) / bt);
+  const bool gen = bt != kKnnThreads || sh.qpw != 32;
+  if (stats && gen)
+    k_knn<D, true, true><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
+  else if (stats)
+    k_knn<D, true, false><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
+  else if (gen)
+    k_knn<D, false, true><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
   else
-    k_knn<D, false><<<grid, kKnnThreads, smem, s>>>(jobs, job_warp, njobs, k, stats);
+    k_knn<D, false, false><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
 }
 
 template <int D>
-void launch_one(const KnnOne &P, int k, unsigned long long *stats, cudaStream_t s) {
-  const size_t smem = (size_t)k * kKnnThreads * 12;
+void launch_one(const KnnOne &P, int k, const KnnShape &sh, unsigned long long *stats, cudaStream_t s) {
+  const int bt = knn_block_for(sh, k);
+  const size_t smem = (size_t)k * bt * 12;
   KScope ks_(stats ? kK_knn_count : kK_knn, s);
-  const unsigned grid = (unsigned)((P.job.m + kKnnThreads - 1) / kKnnThreads);
-  if (stats)
-    k_knn_one<D, true><<<grid, kKnnThreads, smem, s>>>(P, k, stats);
+  const int64_t warps = (P.job.m + sh.qpw - 1) / sh.qpw;
+  const unsigned grid = (unsigned)((warps * 32 + bt - 1) / bt);
+  const bool gen = bt != kKnnThreads || sh.qpw != 32;
+  if (stats && gen)
+    k_knn_one<D, true, true><<<grid, bt, smem, s>>>(P, k, sh.qpw, stats);
+  else if (stats)
+    k_knn_one<D, true, false><<<grid, bt, smem, s>>>(P, k, sh.qpw, stats);
+  else if (gen)
+    k_knn_one<D, false, true><<<grid, bt, smem, s>>>(P, k, sh.qpw, stats);
   else
-    k_knn_one<D, false><<<grid, kKnnThreads, smem, s>>>(P, k, stats);
+    k_knn_one<D, false, false><<<grid, bt, smem, s>>>(P, k, sh.qpw, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,7 +726,7 @@ int batch_query_sort(std::vector<KnnCall> &calls, void *scratch, size_t bytes, c
   S.njobs = n;
   S.dim = dim;
   S.B = B;
-  st = cuda_check(cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s), "memset");
+  st = small_zero(hist, (size_t)nbins * 4, s);
   if (st) return st;
   const unsigned g = (unsigned)((M + 255) / 256);
   { KScope ks_(kK_qsort, s); k_bkey_hist<<<g, 256, 0, s>>>(S, hist); }
@@ -711,7 +762,8 @@ size_t knn_table_bytes_always(const std::vector<KnnCall> &calls) {
   return n * sizeof(KnnJob) + (n + 1) * 8 + views * sizeof(TreeView) + 64;
 }
 
-int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, cudaStream_t s) {
+int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *warps, int qpw,
+                     cudaStream_t s) {
   const size_t n = calls.size();
   std::vector<unsigned char> img(knn_table_bytes_always(calls));
   KnnJob *jobs = (KnnJob *)img.data();
@@ -737,29 +789,29 @@ int upload_knn_table(const std::vector<KnnCall> &calls, void *table, int64_t *wa
     J.oi = c.oi;
     J.od = c.od;
     for (int t = 0; t < c.fv->ntrees; ++t) views[v++] = c.fv->tree[t];
-    warp[j + 1] = warp[j] + (c.m + 31) / 32;
+    warp[j + 1] = warp[j] + (c.m + qpw - 1) / qpw;
   }
   *warps = warp[n];
   if (warp[n] == 0) return BDL_OK;
   return h2d(table, img.data(), img.size(), s);
 }
 
-int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, unsigned long long *stats,
-                     cudaStream_t s) {
+int launch_knn_table(const void *table, int njobs, int64_t warps, int dim, int k, const KnnShape &sh,
+                     unsigned long long *stats, cudaStream_t s) {
   if (warps == 0) return BDL_OK;
   const KnnJob *dj = (const KnnJob *)table;
   const int64_t *dw = (const int64_t *)((const char *)table + njobs * sizeof(KnnJob));
   switch (dim) {
-    case 2: launch_d<2>(dj, dw, njobs, warps, k, stats, s); break;
-    case 3: launch_d<3>(dj, dw, njobs, warps, k, stats, s); break;
-    case 5: launch_d<5>(dj, dw, njobs, warps, k, stats, s); break;
-    case 7: launch_d<7>(dj, dw, njobs, warps, k, stats, s); break;
-    default: launch_d<0>(dj, dw, njobs, warps, k, stats, s); break;
+    case 2: launch_d<2>(dj, dw, njobs, warps, k, sh, stats, s); break;
+    case 3: launch_d<3>(dj, dw, njobs, warps, k, sh, stats, s); break;
+    case 5: launch_d<5>(dj, dw, njobs, warps, k, sh, stats, s); break;
+    case 7: launch_d<7>(dj, dw, njobs, warps, k, sh, stats, s); break;
+    default: launch_d<0>(dj, dw, njobs, warps, k, sh, stats, s); break;
   }
   return cuda_check(cudaGetLastError(), "knn kernel");
 }
 
-int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *table,
+int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, const KnnShape &sh, void *table,
                     unsigned long long *stats, cudaStream_t s) {
   const size_t n = calls.size();
   if (n == 1) {
@@ -780,18 +832,18 @@ int launch_knn_jobs(const std::vector<KnnCall> &calls, int dim, int k, void *tab
     P.job.od = c.od;
     for (int t = 0; t < c.fv->ntrees; ++t) P.trees[t] = c.fv->tree[t];
     switch (dim) {
-      case 2: launch_one<2>(P, k, stats, s); break;
-      case 3: launch_one<3>(P, k, stats, s); break;
-      case 5: launch_one<5>(P, k, stats, s); break;
-      case 7: launch_one<7>(P, k, stats, s); break;
-      default: launch_one<0>(P, k, stats, s); break;
+      case 2: launch_one<2>(P, k, sh, stats, s); break;
+      case 3: launch_one<3>(P, k, sh, stats, s); break;
+      case 5: launch_one<5>(P, k, sh, stats, s); break;
+      case 7: launch_one<7>(P, k, sh, stats, s); break;
+      default: launch_one<0>(P, k, sh, stats, s); break;
     }
     return cuda_check(cudaGetLastError(), "knn kernel");
   }
   int64_t warps = 0;
-  int st = upload_knn_table(calls, table, &warps, s);
+  int st = upload_knn_table(calls, table, &warps, sh.qpw, s);
   if (st) return st;
-  return launch_knn_table(table, (int)n, warps, dim, k, stats, s);
+  return launch_knn_table(table, (int)n, warps, dim, k, sh, stats, s);
 }
 
 void pack_nodes_entries(const std::vector<Tree *> &trees, int dim, std::vector<TreeSeg> &segs,
@@ -830,7 +882,7 @@ void launch_point_sort(const int32_t *coords, const int32_t *ids, int64_t m, int
   const int64_t nb = (nbins + kScanPer - 1) / kScanPer;   // <= 256
   uint32_t *hist = (uint32_t *)scratch;
   uint32_t *bsum = (uint32_t *)((char *)scratch + ((size_t)nbins * 4 + 255) / 256 * 256);
-  cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s);
+  small_zero(hist, (size_t)nbins * 4, s);
   const unsigned g = (unsigned)((m + 255) / 256);
   { KScope ks_(kK_qsort, s); k_qkey_hist<<<g, 256, 0, s>>>(coords, ids, m, m_dev, dim, B, hist); }
   { KScope ks_(kK_qsort, s); k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum); }
@@ -913,7 +965,7 @@ extern "C" int bdl_knn_noalloc(bdl_forest *f, const int32_t *q, int64_t m, int k
     }
     // a single forest's job goes by kernel parameters: no table to place
     std::vector<KnnCall> calls{KnnCall{&fv, q, perm, m, out_ids, out_d2}};
-    st = finish_call(f, s, launch_knn_jobs(calls, f->dim, k, nullptr, f->knn_stats, s));
+    st = finish_call(f, s, launch_knn_jobs(calls, f->dim, k, f->knn_shape, nullptr, f->knn_stats, s));
   }
   if (prev >= 0 && prev != f->device) cudaSetDevice(prev);
   return st;

@@ -519,7 +519,7 @@ int build_trees_spatial(bdl_forest *af, int dim, std::vector<BuildTree> &bt, con
   if (!st) st = h2d(d_lpre, leaf_pre.data(), leaf_pre.size() * 8, s);
   if (!st && !pk.empty()) st = h2d(d_pk, pk.data(), pk.size() * sizeof(TreeSeg), s);
   if (!st) st = h2d(d_pkpre, pk_pre.data(), pk_pre.size() * 8, s);
-  if (!st) st = cuda_check(cudaMemsetAsync(cursor, 0, b_cur, s), "memset");
+  if (!st) st = small_zero(cursor, b_cur, s);
   if (st) {
     dev_free(af, block, total, s);
     return st;

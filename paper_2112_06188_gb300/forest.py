@@ -235,6 +235,13 @@ class Forest:
             capi.check(st, "bdl_poll_error")
         return bits
 
+    def set_knn_shape(self, block_threads=128, queries_per_warp=32):
+        """Launch shape of this forest's k-NN kernel: threads per block (64,
+        128, 256) and queries per warp (32, 64, 128).  Results do not depend
+        on it."""
+        capi.check(capi.bdl_set_knn_shape(self._h, int(block_threads), int(queries_per_warp)),
+                   "bdl_set_knn_shape")
+
     def knn_stats(self, enable=None):
         """enable=True/False switches per-query visit counting on/off (and resets);
         enable=None reads (nodes visited, leaf points examined, queries)."""
