@@ -23,7 +23,9 @@
 #include "bdl_internal.cuh"
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
+#include <queue>
 
 namespace bdl {
 
@@ -628,7 +630,8 @@ struct SubParams {
   int64_t S;
   const int32_t *stg[2];
   const DTree *tree;
-  const int64_t *sub_blk;      // [ntrees + 1] prefix of 2^g subtrees per tree
+  const int64_t *sub_blk;      // [ntrees + 1] prefix of 2^g subtrees per tree, in launch order
+  const int32_t *sub_ord;      // [ntrees] the trees in launch order (largest subtrees first)
 };
 
 // Ascending bitonic sort of one 64-bit word per lane across a warp.
@@ -670,6 +673,29 @@ __device__ __forceinline__ uint64_t skey(const int32_t *sc, const int32_t *sid, 
   return comp_key(sc[c * cap + it], sid[it]);
 }
 
+// seg_range for a subtree (m < 2^31 points).
+__device__ __forceinline__ void seg_range32(int m, int u, int idx, int &start, int &size) {
+  start = 0;
+  size = m;
+  for (int j = u - 1; j >= 0; --j) {
+    const int l = (size + 1) >> 1;
+    if ((idx >> j) & 1) {
+      start += l;
+      size -= l;
+    } else {
+      size = l;
+    }
+  }
+}
+
+// Key bits a segment's median search still has to decide, given that every
+// coordinate of the segment (in the split dimension) lies in [lo, hi]: the
+// coordinate bits below their common prefix, and the 31 id bits.
+__device__ __forceinline__ int open_key_bits(int32_t lo, int32_t hi) {
+  if (lo > hi) return kKeyBits;
+  return 31 + (lo == hi ? 0 : 32 - __clz(lo ^ hi));
+}
+
 __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint64_t s_pre[kMaxRadixSegs], s_res[kMaxRadixSegs];
@@ -679,14 +705,19 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   __shared__ unsigned char s_done[kMaxRadixSegs], s_fnd[kMaxRadixSegs];
   __shared__ uint32_t s_w[32];
   __shared__ int s_ncand;
+  __shared__ int s_multi[3];   // a pending segment's median bucket holds more than one record
+  // key bits still open per segment (the digits below them are the next to
+  // decide): this level's, and the next level's set by the partition
+  __shared__ int32_t s_sh[kMaxRadixSegs], s_shn[kMaxRadixSegs];
 
   const int cap = P.cap, dim = P.dim;
   int b = blockIdx.x;
-  const int tj = find_le(P.sub_blk, P.ntrees, b);
+  const int jj = find_le(P.sub_blk, P.ntrees, b);
+  const int tj = P.sub_ord[jj];
   const DTree &T = P.tree[tj];
   const NodeOut o = T.out;
   const int t0 = T.g;
-  int64_t i0 = b - P.sub_blk[tj];
+  int64_t i0 = b - P.sub_blk[jj];
   int64_t start0, m64;
   seg_range(T.s, t0, i0, start0, m64);
   const int m0 = (int)m64;
@@ -695,13 +726,22 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
   int32_t *sc = (int32_t *)sm;                          // [dim][cap]
   int32_t *sid = sc + (size_t)dim * cap;                // [cap]
   uint32_t *hist = (uint32_t *)(sid + cap);             // [2048]
-  uint32_t *ex = hist + kHistBins;                      // [2048]
+  uint32_t *ex = hist + kHistBins;                      // [2048] exclusive prefix of hist
   uint16_t *perm0 = (uint16_t *)(ex + kHistBins);       // [cap]
   uint16_t *perm1 = perm0 + cap;                        // [cap]
   unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap] segment of each position
   unsigned char *segid_n = segid + cap;                   // [cap] the same for the next level
+  // per-segment coordinate bounds [lo, hi] in every dimension, of this
+  // level's segments and of the next level's: [kMaxRadixSegs][dim][2] each
+  int32_t *bcur = (int32_t *)(segid_n + cap);
+  int32_t *bnxt = bcur + kMaxRadixSegs * dim * 2;
 
   const int32_t *src = P.stg[T.sel];
+  if (threadIdx.x < dim) {
+    bcur[2 * threadIdx.x] = INT32_MAX;
+    bcur[2 * threadIdx.x + 1] = INT32_MIN;
+  }
+  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;   // bins start at zero
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
     for (int c = 0; c < dim; ++c) sc[c * cap + q] = src[c * P.S + T.base + start0 + q];
     sid[q] = src[dim * P.S + T.base + start0 + q];
@@ -710,8 +750,27 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     segid[q] = 0;
   }
   __syncthreads();
+  // the subtree's bounding box: the root segment's bounds
+  for (int c = 0; c < dim; ++c) {
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+      const int32_t x = sc[c * cap + q];
+      lo = min(lo, x);
+      hi = max(hi, x);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bcur[2 * c], lo);
+      atomicMax(&bcur[2 * c + 1], hi);
+    }
+  }
+  __syncthreads();
 
   const int U = T.h - t0;
+  const int nleaf = 1 << U;
+  int32_t *nslot = (int32_t *)hist;   // [2 * nleaf] vEB slots by heap index, once computed
+  bool slots_ready = false;
   bool hist_ready = false;   // `hist` holds this level's first-pass histogram already
   uint16_t *cur = perm0, *nxt = perm1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -731,99 +790,177 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
         seg_range(m0, u, s, a, z);
         s_st[s] = (int)a;
         s_sz[s] = (int)z;
-        s_pre[s] = 0;
+        // the key bits above the open ones are the bounds' common prefix,
+        // the same for every record of the segment
+        const int32_t lo = bcur[(s * dim + c) * 2], hi = bcur[(s * dim + c) * 2 + 1];
+        const int sh = open_key_bits(lo, hi);
+        s_sh[s] = sh;
+        s_pre[s] = sh >= kKeyBits ? 0 : ((uint64_t)lo >> (sh - 31)) << sh;
         s_rank[s] = (int)((z + 1) >> 1);
+        if (s < 3) s_multi[s] = 0;
+        if (s == 0) s_ncand = 0;
         s_done[s] = 0;
         s_fnd[s] = 0;
         s_cnt[s] = 0;
       }
       __syncthreads();
-      // The first pass's histogram (the top w bits of every key) was filled by
-      // the previous level's partition, except at the subtree's first level.
-      // After the first pass, the records that can still hold their
-      // segment's median (key prefix = the chosen digits) are listed once in
-      // `nxt` (free until this level's partition), and the later passes read
-      // only them.
+      // Every pass decides the next w open bits of each segment's median
+      // key (the digit below its s_sh open bits).  The first pass's
+      // histogram was filled by the previous level's partition, except at the
+      // subtree's first level.  After the first pass, the records that can
+      // still hold their segment's median (key prefix = the chosen digits)
+      // are listed once in `nxt` (free until this level's partition), and the
+      // later passes read only them.  The bins are zero at the start of every
+      // pass that counts (each pass's bucket search clears them).
       uint16_t *cand = nxt;
-      int shift = kKeyBits;
       bool first = true;
-      while (true) {
-        const int ns = max(0, shift - w);
-        const int ww = shift - ns;
+      const int nbin = 1 << w, per = (nbin + 31) >> 5;   // bins per segment, per lane
+      for (int pass = 0;; ++pass) {
         if (!(first && hist_ready)) {
-          for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;
-          __syncthreads();
           const int nq = first ? m0 : s_ncand;
           for (int i = threadIdx.x; i < nq; i += blockDim.x) {
             const int q = first ? i : cand[i];
             int s = segid[q];
             if (s_done[s]) continue;
             uint64_t k = skey(sc, sid, cap, c, cur[q]);
-            if ((k >> shift) != (s_pre[s] >> shift)) continue;
+            const int sh = s_sh[s], ns = max(0, sh - w);
+            if ((k >> sh) != (s_pre[s] >> sh)) continue;
             if (s_cnt[s] == 1) { s_res[s] = k; s_fnd[s] = 1; continue; }
-            atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << ww) - 1))], 1u);
+            atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << (sh - ns)) - 1))], 1u);
           }
           __syncthreads();
         }
-        // block exclusive scan of hist -> ex (2048 bins, 2 per thread)
-        {
-          int i2 = 2 * threadIdx.x;
-          uint32_t a0 = hist[i2], a1 = hist[i2 + 1];
-          uint32_t v = a0 + a1, inc = v;
-          for (int o2 = 1; o2 < 32; o2 <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
-            if (lane >= o2) inc += y;
-          }
-          if (lane == 31) s_w[warp] = inc;
-          __syncthreads();
-          if (warp == 0) {
-            uint32_t x = lane < nwarps ? s_w[lane] : 0, xi = x;
-            for (int o2 = 1; o2 < 32; o2 <<= 1) {
-              uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
-              if (lane >= o2) xi += y;
-            }
-            if (lane < nwarps) s_w[lane] = xi - x;
-          }
-          __syncthreads();
-          uint32_t e = inc - v + s_w[warp];
-          ex[i2] = e;
-          ex[i2 + 1] = e + a0;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < kHistBins; j += blockDim.x) {
-          int s = j >> w;
-          if (s >= nseg || s_done[s] || s_cnt[s] == 1) continue;
-          uint32_t below = ex[j] - ex[s << w];
-          uint32_t cj = hist[j];
-          // record the bucket only: s_rank is read by the other bins of this
-          // segment in this same phase and is updated after the barrier
-          if (below < (uint32_t)s_rank[s] && (uint32_t)s_rank[s] <= below + cj) {
-            s_dig[s] = j & ((1 << w) - 1);
-            s_bel[s] = (int)below;
-            s_cnt2[s] = (int)cj;
-          }
-        }
-        __syncthreads();
+        // the bucket holding each segment's rank-th candidate; the segment's
+        // prefix, rank and open bits move into it and the bins are cleared.
+        // s_multi[pass % 3]: a segment's new bucket holds more than one
+        // record (three flags, so that clearing the next pass's needs no
+        // barrier of its own)
+        if (threadIdx.x == 0) s_multi[(pass + 1) % 3] = 0;
         int pending = 0;
-        for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
-          if (s_done[s]) continue;
-          if (s_fnd[s]) { s_done[s] = 1; continue; }
-          s_pre[s] |= (uint64_t)s_dig[s] << ns;
-          s_rank[s] -= s_bel[s];
-          s_cnt[s] = s_cnt2[s];
-          if (ns == 0) { s_res[s] = s_pre[s]; s_done[s] = 1; continue; }
-          pending = 1;
-        }
-        shift = ns;
-        if (!__syncthreads_or(pending)) break;
-        if (first) {   // list the records whose key still matches their segment's prefix
-          if (threadIdx.x == 0) s_ncand = 0;
+        if (nseg < 8) {
+          // few segments: an exclusive scan of all the bins (2 per thread)
+          {
+            const int i2 = 2 * threadIdx.x;
+            const uint32_t a0 = hist[i2], a1 = hist[i2 + 1];
+            const uint32_t v = a0 + a1;
+            uint32_t inc = v;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+              if (lane >= o2) inc += y;
+            }
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+              const uint32_t x = lane < nwarps ? s_w[lane] : 0;
+              uint32_t xi = x;
+              for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
+                if (lane >= o2) xi += y;
+              }
+              if (lane < nwarps) s_w[lane] = xi - x;
+            }
+            __syncthreads();
+            const uint32_t e = inc - v + s_w[warp];
+            ex[i2] = e;
+            ex[i2 + 1] = e + a0;
+          }
           __syncthreads();
+          for (int j = threadIdx.x; j < kHistBins; j += blockDim.x) {
+            const int s = j >> w;
+            const uint32_t cj = hist[j];
+            hist[j] = 0;
+            if (s >= nseg || s_done[s] || s_cnt[s] == 1) continue;
+            const uint32_t below = ex[j] - ex[s << w];
+            // record the bucket only: s_rank is read by the other bins of this
+            // segment in this same phase and is updated after the barrier
+            if (below < (uint32_t)s_rank[s] && (uint32_t)s_rank[s] <= below + cj) {
+              s_dig[s] = j & ((1 << w) - 1);
+              s_bel[s] = (int)below;
+              s_cnt2[s] = (int)cj;
+            }
+          }
+          __syncthreads();
+          for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+            if (s_done[s]) continue;
+            if (s_fnd[s]) { s_done[s] = 1; continue; }
+            const int ns = max(0, s_sh[s] - w);
+            s_pre[s] |= (uint64_t)s_dig[s] << ns;
+            s_rank[s] -= s_bel[s];
+            s_cnt[s] = s_cnt2[s];
+            s_sh[s] = ns;
+            if (ns == 0) { s_res[s] = s_pre[s]; s_done[s] = 1; continue; }
+            pending = 1;
+            if (s_cnt[s] > 1) s_multi[pass % 3] = 1;
+          }
+        } else {
+          // one warp per segment: a scan of the segment's bins across the lanes
+          for (int s = warp; s < nseg; s += nwarps) {
+            if (s_done[s]) continue;
+            if (s_fnd[s]) {
+              if (lane == 0) s_done[s] = 1;
+              continue;
+            }
+            uint32_t *h = hist + (s << w) + lane * per;
+            const int nb = max(0, min(per, nbin - lane * per));
+            uint32_t sum = 0;
+            for (int i = 0; i < nb; ++i) sum += h[i];
+            uint32_t inc = sum;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+              if (lane >= o2) inc += y;
+            }
+            const uint32_t r = (uint32_t)s_rank[s];
+            const bool mine = inc - sum < r && r <= inc;
+            if (mine) {
+              uint32_t below = inc - sum, cj = h[0];
+              int i = 0;
+              while (below + cj < r) {   // ends inside this lane's bins (r <= inc)
+                below += cj;
+                cj = h[++i];
+              }
+              const int ns = max(0, s_sh[s] - w);
+              s_pre[s] |= (uint64_t)(lane * per + i) << ns;
+              s_rank[s] = (int)(r - below);
+              s_cnt[s] = (int)cj;
+              s_sh[s] = ns;
+              if (ns == 0) {
+                s_res[s] = s_pre[s];
+                s_done[s] = 1;
+              } else {
+                pending = 1;
+                if (cj > 1) s_multi[pass % 3] = 1;
+              }
+            }
+            if (!__any_sync(0xffffffffu, mine) && lane == 0) {   // counts inconsistent with the rank
+              atomicOr(T.err, kErrPartition);
+              s_done[s] = 1;
+            }
+            for (int i = 0; i < nb; ++i) h[i] = 0;
+          }
+        }
+        if (!__syncthreads_or(pending)) break;
+        if (!s_multi[pass % 3]) {
+          // every pending segment's bucket holds one record: that record's key
+          // is the median (one scan instead of another pass)
+          const int nq = first ? m0 : s_ncand;
+          for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const int q = first ? i : cand[i];
+            const int s = segid[q];
+            if (s_done[s]) continue;
+            const uint64_t k = skey(sc, sid, cap, c, cur[q]);
+            const int sh = s_sh[s];
+            if ((k >> sh) == (s_pre[s] >> sh)) s_res[s] = k;
+          }
+          __syncthreads();
+          break;
+        }
+        if (first) {   // list the records whose key still matches their segment's prefix
           for (int q = threadIdx.x; q < m0; q += blockDim.x) {
             const int s = segid[q];
             if (s_done[s]) continue;
             const uint64_t k = skey(sc, sid, cap, c, cur[q]);
-            if ((k >> shift) == (s_pre[s] >> shift)) cand[atomicAdd(&s_ncand, 1)] = (uint16_t)q;
+            const int sh = s_sh[s];
+            if ((k >> sh) == (s_pre[s] >> sh)) cand[atomicAdd(&s_ncand, 1)] = (uint16_t)q;
           }
           __syncthreads();
           first = false;
@@ -845,17 +982,54 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       const bool next_radix = u + 1 < U && nsz_ > kWarpMode;
       const int wn = 10 - u;                 // the next level's digit width, 11 - (u + 1)
       const int cn = (t + 1) % dim;
-      if (next_radix)
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;   // ordered by the barriers below
-      const int ipt = (cap + blockDim.x - 1) / blockDim.x;
+      if (next_radix) {
+        // the children's bounds: the parent's, cut at the median's
+        // coordinate in the split dimension (left: coordinates <= v, right:
+        // >= v); and their open key bits in the next split dimension
+        for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+          const int32_t v = (int32_t)(s_res[s] >> 31);
+          for (int cc = 0; cc < dim; ++cc) {
+            const int32_t lo = bcur[(s * dim + cc) * 2], hi = bcur[(s * dim + cc) * 2 + 1];
+            bnxt[(2 * s * dim + cc) * 2] = lo;
+            bnxt[(2 * s * dim + cc) * 2 + 1] = cc == c ? v : hi;
+            bnxt[((2 * s + 1) * dim + cc) * 2] = cc == c ? v : lo;
+            bnxt[((2 * s + 1) * dim + cc) * 2 + 1] = hi;
+          }
+          for (int ch = 2 * s; ch <= 2 * s + 1; ++ch)
+            s_shn[ch] = open_key_bits(bnxt[(ch * dim + cn) * 2], bnxt[(ch * dim + cn) * 2 + 1]);
+        }
+      }
+      const int ipt = (cap + blockDim.x - 1) / blockDim.x;   // 2, 4 or 8 (cap <= 8 x 1024)
       const int q0 = threadIdx.x * ipt;
+      // this thread's positions' records and segments, read once (one vector
+      // load each where the positions fill one: no bank conflicts between
+      // the lanes' neighbouring positions)
+      uint32_t cq[4], sq[2];   // 16-bit record indices, 8-bit segments, packed
+      if (ipt == 8) {
+        const uint4 cv = *reinterpret_cast<const uint4 *>(cur + q0);
+        const uint2 sv = *reinterpret_cast<const uint2 *>(segid + q0);
+        cq[0] = cv.x; cq[1] = cv.y; cq[2] = cv.z; cq[3] = cv.w;
+        sq[0] = sv.x; sq[1] = sv.y;
+      } else {
+        cq[0] = cq[1] = cq[2] = cq[3] = 0;
+        sq[0] = sq[1] = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < ipt) {
+            cq[j >> 1] |= (uint32_t)cur[q0 + j] << (16 * (j & 1));
+            sq[j >> 2] |= (uint32_t)segid[q0 + j] << (8 * (j & 3));
+          }
+        }
+      }
+#define CQ(j) ((int)((cq[(j) >> 1] >> (16 * ((j) & 1))) & 0xffffu))
+#define SQ(j) ((int)((sq[(j) >> 2] >> (8 * ((j) & 3))) & 0xffu))
       uint32_t flags = 0;
       int cnt = 0;
-      for (int j = 0; j < ipt; ++j) {
-        int q = q0 + j;
-        if (q < m0) {
-          int s = segid[q];
-          bool left = skey(sc, sid, cap, c, cur[q]) <= s_res[s];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = q0 + j;
+        if (j < ipt && q < m0) {
+          const bool left = skey(sc, sid, cap, c, CQ(j)) <= s_res[SQ(j)];
           flags |= (uint32_t)left << j;
           cnt += left;
         }
@@ -880,10 +1054,11 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       uint32_t e = inc - cnt + s_w[warp];
       {
         uint32_t run = e;
-        for (int j = 0; j < ipt; ++j) {
-          int q = q0 + j;
-          if (q < m0) {
-            int s = segid[q];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int q = q0 + j;
+          if (j < ipt && q < m0) {
+            const int s = SQ(j);
             if (q == s_st[s]) s_lb[s] = (int)run;
             run += (flags >> j) & 1;
           }
@@ -892,10 +1067,11 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       __syncthreads();
       {
         uint32_t run = e;
-        for (int j = 0; j < ipt; ++j) {
-          int q = q0 + j;
-          if (q < m0) {
-            int s = segid[q];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int q = q0 + j;
+          if (j < ipt && q < m0) {
+            const int s = SQ(j);
             int lrank = (int)run - s_lb[s];
             int half = (s_sz[s] + 1) >> 1;
             int rrank = (q - s_st[s]) - lrank;
@@ -904,30 +1080,43 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             if (left ? (lrank < 0 || lrank >= half) : (rrank < 0 || rrank >= s_sz[s] - half)) {
               atomicOr(T.err, kErrPartition);
             } else {
-              nxt[dst] = cur[q];
+              nxt[dst] = (uint16_t)CQ(j);
               segid_n[dst] = (unsigned char)(2 * s + (left ? 0 : 1));   // child segment
-              if (next_radix) {
-                const int32_t x = sc[cn * cap + cur[q]];
-                atomicAdd(&hist[((2 * s + (left ? 0 : 1)) << wn) + (x >> (kCoordBits - wn))], 1u);
+              if (next_radix) {   // the child's first digit, below its open key bits
+                const int ch = 2 * s + (left ? 0 : 1), sh = s_shn[ch], ns = max(0, sh - wn);
+                const uint64_t kn = skey(sc, sid, cap, cn, CQ(j));
+                atomicAdd(&hist[(ch << wn) + (int)((kn >> ns) & ((1u << (sh - ns)) - 1))], 1u);
               }
             }
             run += (flags >> j) & 1;
           }
         }
       }
+#undef CQ
+#undef SQ
       __syncthreads();
       hist_ready = next_radix;
       unsigned char *ts = segid; segid = segid_n; segid_n = ts;
+      int32_t *tb = bcur; bcur = bnxt; bnxt = tb;
     } else {
       // ---------------- warp mode: one warp sorts each segment -------------
       // Words (key << 13 | position) are distinct and order like the keys
       // (positions < cap <= 8192); a bitonic network across the warp sorts
       // them, so the segment comes out in key order and its median is at
-      // rank ceil(z/2) - 1.
+      // rank ceil(z/2) - 1.  At the first such level every node's vEB slot
+      // is computed once, in heap order (node (u, s) at (1 << u) + s), in the
+      // histogram space (free from here on); the leaves use them too.
+      if (!slots_ready && nleaf <= (int)blockDim.x) {
+        for (int x = threadIdx.x + 1; x < 2 * nleaf; x += blockDim.x) {
+          const int ux = 31 - __clz(x);
+          nslot[x] = (int32_t)veb_slot(l, t0 + ux, (i0 << ux) + (x - (1 << ux)));
+        }
+        slots_ready = true;
+        __syncthreads();
+      }
       for (int s = warp; s < nseg; s += nwarps) {
-        int64_t a64, z64;
-        seg_range(m0, u, s, a64, z64);
-        const int a = (int)a64, z = (int)z64;
+        int a, z;
+        seg_range32(m0, u, s, a, z);
         if (z > 64) { if (lane == 0) atomicOr(T.err, kErrPartition); continue; }
         const int mr = ((z + 1) >> 1) - 1;
         uint64_t med = 0;
@@ -945,7 +1134,10 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
           if (e1 < z) nxt[a + e1] = (uint16_t)(x1 & 8191u);
           med = __shfl_sync(0xffffffffu, (mr & 1) ? x1 : x0, mr >> 1);
         }
-        {
+        if (slots_ready) {
+          const int x = (1 << u) + s;
+          if (lane == 0) o.node[nslot[x]] = Node{med >> 13, nslot[2 * x], nslot[2 * x + 1]};
+        } else {
           // the node's vEB slot and its children's, three lanes at once
           const int64_t bfs = (i0 << u) + s;
           const int64_t sl = lane < 3 ? veb_slot(l, lane ? t + 1 : t, lane ? 2 * bfs + lane - 1 : bfs) : 0;
@@ -960,7 +1152,6 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
 
   // leaves: slot, leaf range, box, live count; then the subtree's internal
   // nodes bottom-up
-  const int nleaf = 1 << U;
   const int64_t nleaves_tree = (int64_t)1 << T.h;
   if (nleaf <= (int)blockDim.x) {
     // Every node's vEB slot once, in heap order in shared memory (node (u, s)
@@ -969,13 +1160,14 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     // per leaf in a thread, pairs combined by warp shuffles up to the warp's
     // subtree, the warps' results by warp 0: no barrier and no read-back of
     // global memory per level.
-    int32_t *nslot = (int32_t *)hist;                  // [2 * nleaf]
     int32_t *wlo = nslot + 2 * nleaf, *whi = wlo + 32; // [32] each: the warps' results
-    for (int x = threadIdx.x + 1; x < 2 * nleaf; x += blockDim.x) {
-      const int u = 31 - __clz(x);
-      nslot[x] = (int32_t)veb_slot(l, t0 + u, (i0 << u) + (x - (1 << u)));
+    if (!slots_ready) {
+      for (int x = threadIdx.x + 1; x < 2 * nleaf; x += blockDim.x) {
+        const int u = 31 - __clz(x);
+        nslot[x] = (int32_t)veb_slot(l, t0 + u, (i0 << u) + (x - (1 << u)));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int lf = threadIdx.x;
     const bool has = lf < nleaf;
     int a = 0, z = 0;
@@ -1196,7 +1388,8 @@ int coop_grid(const void *fn, int threads, int *out) {
 }
 
 size_t subtree_smem_bytes(int dim, int cap) {
-  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap;
+  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap +
+         2 * (size_t)kMaxRadixSegs * dim * 2 * 4;
 }
 
 NodeOut node_out(Tree *t) {
@@ -1210,6 +1403,66 @@ NodeOut node_out(Tree *t) {
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Relative time of an on-chip subtree of n records with U levels below its
+// root: per level, a fixed part (block barriers, bin scans) and a part that
+// grows with the records (a CTA of 8,192 records: 0.3 + 0.7 per level).
+double subtree_cost(int64_t n, int U) { return (double)std::max(U, 1) * (0.3 + 0.7 * (double)n / 8192.0); }
+
+// Finish time of `cost` (any order; run largest first) on `slots` CTA slots
+// that each take the next subtree when free (the block scheduler's order).
+double schedule_makespan(std::vector<double> cost, int slots) {
+  std::sort(cost.begin(), cost.end(), std::greater<double>());
+  std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+  for (int i = 0; i < slots; ++i) q.push(0.0);
+  double ms = 0;
+  for (double c : cost) {
+    const double t = q.top() + c;
+    q.pop();
+    q.push(t);
+    ms = std::max(ms, t);
+  }
+  return ms;
+}
+
+constexpr int64_t kMinDeepened = 512;   // extra global levels keep subtrees at least this big
+
+// Global levels of a tree with `e` extra ones (bounded by gmax and by the
+// smallest subtree worth a CTA).
+int deepened_g(const BuildTree &b, int gmax, int e) {
+  int g = b.g;
+  while (e > 0 && g < gmax && ceil_div(b.s, (int64_t)1 << (g + 1)) >= kMinDeepened) {
+    ++g;
+    --e;
+  }
+  return g;
+}
+
+// Extra global levels for the trees with fewer than the deepest one's: the
+// global kernel runs gmax levels anyway, so splitting such a tree further
+// costs only its records' passes, and its smaller subtrees can fill the last
+// wave of the subtree launch (one CTA per SM, often a few left over).  Of
+// 0, 1, 2 or as many extra levels as allowed (the same for every such tree),
+// the one with the shortest schedule under subtree_cost is applied.
+void balance_subtrees(std::vector<BuildTree> &bt, int gmax, int slots) {
+  if (gmax == 0) return;
+  double best = 0;
+  int best_e = 0;
+  for (int e : {0, 1, 2, 64}) {
+    std::vector<double> c;
+    for (const auto &b : bt) {
+      const int g = deepened_g(b, gmax, e);
+      const double x = subtree_cost(ceil_div(b.s, (int64_t)1 << g), b.h - g);
+      c.insert(c.end(), (size_t)1 << g, x);
+    }
+    const double ms = schedule_makespan(std::move(c), slots);
+    if (e == 0 || ms < best * 0.99) {
+      best = ms;
+      best_e = e;
+    }
+  }
+  for (auto &b : bt) b.g = deepened_g(b, gmax, best_e);
+}
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -1260,10 +1513,17 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     gmax = std::max(gmax, g);
   }
   S = std::max<int64_t>(S, 8);
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+    balance_subtrees(bt, gmax, std::max(sms, 1));   // one subtree CTA per SM (its shared memory)
+  }
 
   // ---- plan arrays ----
   std::vector<DTree> dt(ntree);
   std::vector<int64_t> pool_off(ntree + 1, 0), sub_blk(ntree + 1, 0);
+  std::vector<int32_t> sub_ord(ntree);
   for (int j = 0; j < ntree; ++j) {
     const BuildTree &b = bt[j];
     DTree &d = dt[j];
@@ -1283,8 +1543,12 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     d.idtab = b.idtab;
     d.err = b.err;
     pool_off[j + 1] = pool_off[j] + (b.s - b.from_cleared);
-    sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << b.g);
   }
+  // the subtree launch runs the trees with the costliest subtrees first
+  for (int j = 0; j < ntree; ++j) sub_ord[j] = j;
+  auto cost_of = [&](int j) { return subtree_cost(ceil_div(bt[j].s, (int64_t)1 << bt[j].g), bt[j].h - bt[j].g); };
+  std::stable_sort(sub_ord.begin(), sub_ord.end(), [&](int a, int b) { return cost_of(a) > cost_of(b); });
+  for (int j = 0; j < ntree; ++j) sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << bt[sub_ord[j]].g);
   const int TB = kCoopThreads;   // cleared records per gather work item
   std::vector<DCleared> dc(cl.size());
   std::vector<int64_t> cl_blk(cl.size() + 1, 0);
@@ -1354,7 +1618,8 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   }
   PlanImage img;
   const size_t o_dt = img.put(dt), o_dc = img.put(dc), o_clb = img.put(cl_blk),
-               o_pool = img.put(pool_off), o_sub = img.put(sub_blk), o_act = img.put(act_all),
+               o_pool = img.put(pool_off), o_sub = img.put(sub_blk), o_ord = img.put(sub_ord),
+               o_act = img.put(act_all),
                o_pre = img.put(pre_all), o_lt = img.put(lt_all);
   std::vector<TreeSeg> pk_segs;
   std::vector<int64_t> pk_pre;
@@ -1495,6 +1760,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     P.stg[1] = stg[1];
     P.tree = d_tree;
     P.sub_blk = (const int64_t *)(plan + o_sub);
+    P.sub_ord = (const int32_t *)(plan + o_ord);
     size_t smem = subtree_smem_bytes(dim, cap);
     cudaError_t e = cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSubtreeSmemMax);
