@@ -37,6 +37,11 @@
  *    when a bit is set, with the bits in bdl_last_error(); bdl_poll_error reads
  *    it on demand.  With the environment variable BDL_DEBUG_CHECK=1 (read at
  *    bdl_create) every call also waits for its own kernels and checks the word.
+ *  - Builds: the on-chip subtrees run one CTA per SM; a build gives trees with
+ *    fewer global levels than its deepest tree extra ones when that shortens
+ *    an estimated schedule of the subtree CTAs on the device's SMs
+ *    (BDL_BUILD_SLOTS=n, read at every build, schedules on n slots instead).
+ *    The trees are the same either way.
  */
 #ifndef BDL_H
 #define BDL_H

@@ -547,7 +547,7 @@ struct FillSeg {           // `count` work items of one kind
   int64_t from;            // pool tail: first pool entry copied
   uint32_t *alive;         // alive: the forest's bitmap
   const unsigned long long *errw;  // append: the forest's device error word; a set word
-                                   // sets bit 1 of *flag
+                                   // sets bit 1 of *flag and its bits from bit 8 on
 };
 struct MarkSeg {           // one erase list of one forest
   uint32_t *alive;

@@ -23,6 +23,7 @@
 #include "bdl_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <functional>
 #include <mutex>
 #include <queue>
@@ -1425,13 +1426,12 @@ double schedule_makespan(std::vector<double> cost, int slots) {
   return ms;
 }
 
-constexpr int64_t kMinDeepened = 512;   // extra global levels keep subtrees at least this big
-
-// Global levels of a tree with `e` extra ones (bounded by gmax and by the
-// smallest subtree worth a CTA).
-int deepened_g(const BuildTree &b, int gmax, int e) {
+// Global levels of a tree with `e` extra ones, bounded by gmax and by the
+// global kernels' tiles: a level may split only segments of at least `tile`
+// records (so that a tile meets at most two segments).
+int deepened_g(const BuildTree &b, int gmax, int e, int tile) {
   int g = b.g;
-  while (e > 0 && g < gmax && ceil_div(b.s, (int64_t)1 << (g + 1)) >= kMinDeepened) {
+  while (e > 0 && g < gmax && (b.s >> g) >= tile) {
     ++g;
     --e;
   }
@@ -1444,14 +1444,14 @@ int deepened_g(const BuildTree &b, int gmax, int e) {
 // wave of the subtree launch (one CTA per SM, often a few left over).  Of
 // 0, 1, 2 or as many extra levels as allowed (the same for every such tree),
 // the one with the shortest schedule under subtree_cost is applied.
-void balance_subtrees(std::vector<BuildTree> &bt, int gmax, int slots) {
+void balance_subtrees(std::vector<BuildTree> &bt, int gmax, int slots, int tile) {
   if (gmax == 0) return;
   double best = 0;
   int best_e = 0;
   for (int e : {0, 1, 2, 64}) {
     std::vector<double> c;
     for (const auto &b : bt) {
-      const int g = deepened_g(b, gmax, e);
+      const int g = deepened_g(b, gmax, e, tile);
       const double x = subtree_cost(ceil_div(b.s, (int64_t)1 << g), b.h - g);
       c.insert(c.end(), (size_t)1 << g, x);
     }
@@ -1461,7 +1461,7 @@ void balance_subtrees(std::vector<BuildTree> &bt, int gmax, int slots) {
       best_e = e;
     }
   }
-  for (auto &b : bt) b.g = deepened_g(b, gmax, best_e);
+  for (auto &b : bt) b.g = deepened_g(b, gmax, best_e, tile);
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1517,7 +1517,11 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-    balance_subtrees(bt, gmax, std::max(sms, 1));   // one subtree CTA per SM (its shared memory)
+    if (const char *e = getenv("BDL_BUILD_SLOTS")) {   // slots of the schedule model
+      const int v = atoi(e);
+      if (v > 0) sms = v;
+    }
+    balance_subtrees(bt, gmax, std::max(sms, 1), tile);   // one subtree CTA per SM (its shared memory)
   }
 
   // ---- plan arrays ----

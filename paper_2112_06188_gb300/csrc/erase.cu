@@ -461,7 +461,7 @@ __global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
       // before the flag is read back only ever sees grid coordinates
       g.dst[i] = min(max(v, 0), (1 << kCoordBits) - 1);
       if (v < 0 || v >= (1 << kCoordBits)) atomicOr(g.flag, 1ull);
-      if (i == 0 && g.errw && *g.errw) atomicOr(g.flag, 2ull);
+      if (i == 0 && g.errw && *g.errw) atomicOr(g.flag, 2ull | (*g.errw << 8));   // with the word's bits
       break;
     }
     case kFillPoolTail: g.dst[i] = pool_entry(g, g.from + i); break;

@@ -891,7 +891,8 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
   if (!st && !ahead) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (st) return st;
   // flag bit 0: a coordinate off the grid; bit 1: the forest's device error
-  // word was set by earlier work (a kernel found an index outside its buffers)
+  // word was set by earlier work (a kernel found an index outside its
+  // buffers), whose bits follow from bit 8 on
   auto off_grid = [&]() {
     for (size_t j = 0; j < app.size(); ++j)
       if (hf[j] & 1) return true;
@@ -902,7 +903,12 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
       if (hf[j] & 2) return true;
     return false;
   };
-  if (!ahead && dev_error()) return set_error(BDL_EINTERNAL, "device error word set by earlier work");
+  auto dev_error_msg = [&]() {
+    uint64_t bits = 0;
+    for (size_t j = 0; j < app.size(); ++j) bits |= (uint64_t)hf[j] >> 8;
+    return std::string("device error word set by earlier work, code ") + std::to_string(bits);
+  };
+  if (!ahead && dev_error()) return set_error(BDL_EINTERNAL, dev_error_msg());
   if (!ahead && off_grid()) return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
   // 2. plan every forest (Alg. 3), allocating the new trees
   std::vector<InsertPlan> plans(nf);
@@ -946,7 +952,7 @@ static int insert_many(bdl_forest *const *F, int nf, const int32_t *const *pts, 
     if (!st && (off_grid() || dev_error())) {
       for (auto &ip : plans)
         if (ip.f) drop_plan(ip, s);
-      if (dev_error()) return set_error(BDL_EINTERNAL, "device error word set by earlier work");
+      if (dev_error()) return set_error(BDL_EINTERNAL, dev_error_msg());
       return set_error(BDL_EINVAL, "coordinate outside [0, 2^20)");
     }
   }
