@@ -419,6 +419,13 @@ struct bdl_forest {
   uint64_t version = 0;          // bumped by every change of the trees or the buffer
   cudaEvent_t ev_flags = nullptr;  // recorded behind the insert flags' copy
   bdl::KnnShape knn_shape;         // launch shape of its k-NN calls
+  // per static-tree level: the block of the level's last cleared tree, kept
+  // for its next tree (forests without an hbm budget; freed by bdl_destroy)
+  struct SpareBlock {
+    void *block = nullptr;
+    size_t bytes = 0;
+    int64_t room = 0;
+  } spare[bdl::kMaxLevel];
 };
 
 namespace bdl {

@@ -369,8 +369,26 @@ int h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
   return BDL_OK;
 }
 
+// Static trees of a forest without an hbm budget are laid out for their
+// level's capacity X * 2^level (the most a tree of that level holds), so a
+// cleared tree's block can serve its level's next tree: it is kept as the
+// level's spare instead of going back to the pool.  The binary counter
+// clears a level and later fills it again, so after the first carries a
+// step allocates almost nothing (a batched step over hundreds of forests
+// otherwise makes a pool call per new tree and per cleared one).  Reuse is
+// ordered like the buffer's spare: a forest's calls are ordered on one stream.
+static bool keeps_spares(const bdl_forest *f, int level) {
+  return level < kMaxLevel && f->cfg.hbm_budget_bytes == 0;
+}
+
 static void free_tree(bdl_forest *f, Tree *t, cudaStream_t s) {
   if (!t) return;
+  if (keeps_spares(f, t->level) && !f->spare[t->level].block &&
+      t->room >= ((int64_t)f->cfg.buffer_size << t->level)) {
+    f->spare[t->level] = bdl_forest::SpareBlock{t->block, t->bytes, t->room};   // still the forest's memory
+    delete t;
+    return;
+  }
   dev_free(f, t->block, t->bytes, s);   // the bloom filter, if any, lives in the block
   delete t;
 }
@@ -396,9 +414,19 @@ static void shape_tree(const bdl_forest *f, Tree *t, int64_t size) {
 // A tree of `size` points whose arrays have room for up to `room` points
 // (room >= size; the buffer's tree is laid out for a full buffer and reused).
 static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tree **out, int64_t room = 0) {
+  room = std::max(room, size);
+  bdl_forest::SpareBlock *sp = nullptr;
+  if (keeps_spares(f, level)) {
+    room = std::max(room, (int64_t)f->cfg.buffer_size << level);
+    sp = &f->spare[level];
+    if (sp->block && sp->room < room) {   // too small for this tree: back to the pool
+      dev_free(f, sp->block, sp->bytes, s);
+      sp->block = nullptr;
+    }
+    if (sp->block) room = sp->room;
+  }
   Tree *t = new Tree();
   t->level = level;
-  room = std::max(room, size);
   shape_tree(f, t, room);               // the layout is that of the largest shape
   t->room = room;
   size_t b_pts = a256((size_t)rec_ints(f->dim) * room * 4),
@@ -408,14 +436,25 @@ static int alloc_tree(bdl_forest *f, int level, int64_t size, cudaStream_t s, Tr
          b_pk = a256((size_t)packed_nrec(t->h) * packed_node_ints(f->dim) * 4);
   shape_tree(f, t, size);
   // a static tree's bloom filter (Sec. V-A) is built lazily but its room is
-  // part of the block, so building it needs no allocation
+  // part of the block, so building it needs no allocation (the room is sized
+  // for the layout's capacity, the filter for the tree's size)
   const int64_t blocks = level < kMaxLevel ? bloom_blocks_for(f, size) : 0;
-  const size_t b_bloom = a256((size_t)blocks * 32);
+  const int64_t room_blocks = level < kMaxLevel ? bloom_blocks_for(f, sp ? room : size) : 0;
+  const size_t b_bloom = a256((size_t)room_blocks * 32);
   t->bytes = b_pts + b_node + b_box + b_live + b_leaf + b_pk + b_bloom;
-  int st = dev_alloc(f, &t->block, t->bytes, s);
-  if (st) {
-    delete t;
-    return st;
+  if (sp && sp->block && sp->bytes == t->bytes) {
+    t->block = sp->block;
+    sp->block = nullptr;
+  } else {
+    if (sp && sp->block) {   // (a layout of the same room has the same bytes)
+      dev_free(f, sp->block, sp->bytes, s);
+      sp->block = nullptr;
+    }
+    const int st = dev_alloc(f, &t->block, t->bytes, s);
+    if (st) {
+      delete t;
+      return st;
+    }
   }
   char *p = (char *)t->block;
   t->pts = (int32_t *)p; p += b_pts;
@@ -1824,6 +1863,8 @@ int bdl_destroy(bdl_forest *f) {
   cudaStream_t s = 0;
   for (int i = 0; i < kMaxLevel; ++i) free_tree(f, f->trees[i], s);
   free_tree(f, f->btree, s);
+  for (auto &sp : f->spare)
+    if (sp.block) dev_free(f, sp.block, sp.bytes, s);
   if (f->id_cap) {
     dev_free(f, f->idtab, (size_t)f->id_cap * f->dim * 4, s);
     dev_free(f, f->alive, (size_t)f->id_cap / 8, s);
