@@ -71,7 +71,10 @@ class Forest:
         extent, Sec. V-C); k-NN answers are the same either way."""
         capi.load()
         self.dim = dim
-        self.device = torch.device(device or "cuda")
+        dev = torch.device(device or "cuda")
+        if dev.type == "cuda" and dev.index is None:   # "cuda": the current device, by index
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
         self.stream = stream
         cfg = capi.bdl_default_config()
         cfg.leaf_size, cfg.buffer_size = leaf_size, buffer_size

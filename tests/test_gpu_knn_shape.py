@@ -108,3 +108,20 @@ def test_shape_values_checked():
         assert L.bdl_set_knn_shape(g._h, b, q) == capi.BDL_EINVAL
     assert L.bdl_set_knn_shape(g._h, 0, 0) == capi.BDL_OK          # the defaults
     g.close()
+
+
+def test_default_device_accepts_current_device_outputs():
+    """A forest made without a device index lives on the current device, and
+    output buffers there (cuda:N) are accepted."""
+    from paper_2112_06188_gb300.forest import Forest
+    g, o, lp = forest_pair(2, 5_000, seed=580)
+    h = Forest(2)
+    assert h.device == torch.device("cuda", torch.cuda.current_device())
+    h.insert(dev(lp))
+    q = inputs.uniform_points(100, 2, seed=581)
+    n = torch.cuda.current_device()
+    out = (torch.empty((100, 4), dtype=torch.int32, device="cuda:%d" % n),
+           torch.empty((100, 4), dtype=torch.int64, device="cuda:%d" % n))
+    h.knn(dev(q), 4, out=out)
+    g.close()
+    h.close()
