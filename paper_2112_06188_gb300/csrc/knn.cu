@@ -364,7 +364,7 @@ __device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, c
 // J.ntrees), then the buffer.  The timed instance (STATS false) is called by
 // whole warps of one job, which stay resident and converged until each of
 // their lanes is done; the counting instance walks each lane on its own.
-template <int D, bool STATS, int S>
+template <int D, bool STATS, int S, bool TREES_SMEM = false>
 __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees, int64_t t, int k,
                                           unsigned long long *stats) {
   // k (d2, id) slots per thread (TopK<S>'s layout)
@@ -390,7 +390,19 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
 
   const int ntrees = J.ntrees;
   for (int ti = 0; ti < ntrees; ++ti) {
-    const TreeView &T = trees[ti];
+    // from a job table in global memory (TREES_SMEM), each tree's view is
+    // copied into a shared slot of the warp, read where used during the walk
+    // (kernel-parameter views are read through the constant cache instead)
+    const TreeView *tp = &trees[ti];
+    if (TREES_SMEM) {
+      __shared__ TreeView s_tree[kKnnMaxThreads / 32];
+      TreeView &slot = s_tree[threadIdx.x >> 5];
+      __syncwarp();   // the warp is done with the previous tree's view
+      if ((threadIdx.x & 31) == 0) slot = trees[ti];
+      __syncwarp();
+      tp = &slot;
+    }
+    const TreeView &T = *tp;
     if (T.live[0] <= 0) continue;
     if (STATS) walk_nodes<D>(J, T, q, dim, k, best, stk, nvisit, npts);
     else walk_packed<D>(J, T, active, q, dim, k, best, stk);
@@ -431,17 +443,22 @@ __device__ __forceinline__ void knn_query(const KnnJob &J, const TreeView *trees
 template <int D, bool STATS, bool GEN>
 __global__ void __launch_bounds__(GEN ? kKnnMaxThreads : kKnnThreads, GEN ? 6 : 12)
     k_knn(const KnnJob *jobs, const int64_t *job_warp, int njobs, int k, int qpw, unsigned long long *stats) {
+  // the warp's job, copied into shared memory: its fields are read where
+  // used instead of held in registers through the walk
+  __shared__ KnnJob s_job[kKnnMaxThreads / 32];
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= job_warp[njobs]) return;
+  if (w >= job_warp[njobs]) return;   // (whole warps)
   const int jb = knn_find(job_warp, njobs, w);
+  KnnJob &J = s_job[threadIdx.x >> 5];
+  if ((threadIdx.x & 31) == 0) J = jobs[jb];
+  __syncwarp();
+  const int64_t t0 = w - job_warp[jb];
   if (!GEN) {
-    knn_query<D, STATS, kKnnThreads>(jobs[jb], jobs[jb].trees, (w - job_warp[jb]) * 32 + (threadIdx.x & 31), k,
-                                     stats);
+    knn_query<D, STATS, kKnnThreads, !STATS>(J, J.trees, t0 * 32 + (threadIdx.x & 31), k, stats);
     return;
   }
-  const int64_t t0 = (w - job_warp[jb]) * qpw, m = jobs[jb].m;
-  for (int r = 0; r < qpw && t0 + r < m; r += 32) {   // warp-uniform bounds
-    knn_query<D, STATS, 32>(jobs[jb], jobs[jb].trees, t0 + r + (threadIdx.x & 31), k, stats);
+  for (int r = 0; r < qpw && t0 * qpw + r < J.m; r += 32) {   // warp-uniform bounds
+    knn_query<D, STATS, 32, !STATS>(J, J.trees, t0 * qpw + r + (threadIdx.x & 31), k, stats);
     __syncwarp();
   }
 }
