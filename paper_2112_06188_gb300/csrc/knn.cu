@@ -455,11 +455,11 @@ __global__ void __launch_bounds__(GEN ? kKnnMaxThreads : kKnnThreads, GEN ? 6 : 
   const int64_t t0 = w - job_warp[jb];
   if (!GEN) {
     knn_query<D, STATS, kKnnThreads, !STATS>(J, J.trees, t0 * 32 + (threadIdx.x & 31), k, stats);
-    return;
-  }
-  for (int r = 0; r < qpw && t0 * qpw + r < J.m; r += 32) {   // warp-uniform bounds
-    knn_query<D, STATS, 32, !STATS>(J, J.trees, t0 * qpw + r + (threadIdx.x & 31), k, stats);
-    __syncwarp();
+  } else {
+    for (int r = 0; r < qpw && t0 * qpw + r < J.m; r += 32) {   // warp-uniform bounds
+      knn_query<D, STATS, 32, !STATS>(J, J.trees, t0 * qpw + r + (threadIdx.x & 31), k, stats);
+      __syncwarp();
+    }
   }
 }
 
@@ -477,12 +477,12 @@ __global__ void __launch_bounds__(GEN ? kKnnMaxThreads : kKnnThreads, GEN ? 6 : 
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((t & ~(int64_t)31) >= P.job.m) return;     // whole warp past the end
     knn_query<D, STATS, kKnnThreads>(P.job, P.trees, t, k, stats);
-    return;
-  }
-  const int64_t t0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * qpw;
-  for (int r = 0; r < qpw && t0 + r < P.job.m; r += 32) {   // warp-uniform bounds
-    knn_query<D, STATS, 32>(P.job, P.trees, t0 + r + (threadIdx.x & 31), k, stats);
-    __syncwarp();
+  } else {
+    const int64_t t0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * qpw;
+    for (int r = 0; r < qpw && t0 + r < P.job.m; r += 32) {   // warp-uniform bounds
+      knn_query<D, STATS, 32>(P.job, P.trees, t0 + r + (threadIdx.x & 31), k, stats);
+      __syncwarp();
+    }
   }
 }
 
@@ -499,17 +499,17 @@ void launch_d(const KnnJob *jobs, const int64_t *job_warp, int njobs, int64_t wa
               const KnnShape &sh, unsigned long long *stats, cudaStream_t s) {
   const int bt = knn_block_for(sh, k);
   const size_t smem = (size_t)k * bt * 12;   // <= 48 KB
-  KScope ks_(stats ? kK_knn_count : kK_knn, s);
   const unsigned grid = (unsigned)((warps * 32 + bt - 1) / bt);
   const bool gen = bt != kKnnThreads || sh.qpw != 32;
-  if (stats && gen)
-    k_knn<D, true, true><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
-  else if (stats)
-    k_knn<D, true, false><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
-  else if (gen)
-    k_knn<D, false, true><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
-  else
-    k_knn<D, false, false><<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
+  void (*fn)(const KnnJob *, const int64_t *, int, int, int, unsigned long long *) =
+      stats ? (gen ? k_knn<D, true, true> : k_knn<D, true, false>)
+            : (gen ? k_knn<D, false, true> : k_knn<D, false, false>);
+  // the kernel's own shared memory (the warps' job and tree slots) comes on
+  // top of the top-k slots: past the default 48 KB per block (k = 32 at 128
+  // threads) the launch needs the opt-in
+  if (smem > 40 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  KScope ks_(stats ? kK_knn_count : kK_knn, s);
+  fn<<<grid, bt, smem, s>>>(jobs, job_warp, njobs, k, sh.qpw, stats);
 }
 
 template <int D>

@@ -125,3 +125,18 @@ def test_default_device_accepts_current_device_outputs():
     h.knn(dev(q), 4, out=out)
     g.close()
     h.close()
+
+
+def test_batched_call_at_k32():
+    """The table-driven kernel at the largest k: its top-k slots fill 48 KB
+    of shared memory at 128 threads, with the warps' job and tree slots on
+    top (the launch opts in to the larger size)."""
+    from paper_2112_06188_gb300.forest import knn_batch
+    pairs = [forest_pair(3, 40_000, seed=590), forest_pair(3, 20_000, seed=591)]
+    qs = [inputs.uniform_points(2_000 + 700 * j, 3, seed=592 + j) for j in range(2)]
+    out = knn_batch([g for g, _, _ in pairs], [dev(q) for q in qs], 32)
+    torch.cuda.synchronize()
+    for j, ((g, o, _), q) in enumerate(zip(pairs, qs)):
+        assert_rows(out[j], oracle_knn(o, q, 32), "k=32 batched, forest %d" % j)
+    for g, _, _ in pairs:
+        g.close()
