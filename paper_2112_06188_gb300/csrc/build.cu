@@ -34,8 +34,9 @@ namespace {
 
 constexpr int kItems = 8;          // records per thread in the tiled kernels
 constexpr int kSubThreads = 1024;  // threads of the subtree kernel
+constexpr int kSmallSubThreads = 256;   // threads of its instance for small subtrees
+constexpr int kSmallSub = 2048;         // subtrees below this many records take that instance
 constexpr int kWarpMode = 64;      // segments this small are sorted by one warp
-constexpr int kMaxRadixSegs = 128; // segments per level in radix mode (cap / 64)
 
 struct SegState {
   unsigned long long cand_n;   // candidates gathered
@@ -697,19 +698,26 @@ __device__ __forceinline__ int open_key_bits(int32_t lo, int32_t hi) {
   return 31 + (lo == hi ? 0 : 32 - __clz(lo ^ hi));
 }
 
-__global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
+// TH threads per CTA (1024, or 256 for subtrees of fewer than 2048 records):
+// 2 * TH histogram bins per pass, TH / 8 segments per radix level at most.
+template <int TH>
+__global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const SubParams P) {
+  constexpr int HB = 2 * TH;                   // bins of a level's histogram (all its segments)
+  constexpr int LB = TH == 1024 ? 11 : TH == 256 ? 9 : -1;   // log2(HB)
+  static_assert(LB > 0, "k_subtree: 1024 or 256 threads");
+  constexpr int MS = TH / 8;                   // segments of a radix level (cap / 64 <= 8 TH / 64)
   extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ uint64_t s_pre[kMaxRadixSegs], s_res[kMaxRadixSegs];
-  __shared__ int32_t s_st[kMaxRadixSegs], s_sz[kMaxRadixSegs], s_rank[kMaxRadixSegs],
-      s_cnt[kMaxRadixSegs], s_cnt2[kMaxRadixSegs], s_lb[kMaxRadixSegs], s_dig[kMaxRadixSegs],
-      s_bel[kMaxRadixSegs];
-  __shared__ unsigned char s_done[kMaxRadixSegs], s_fnd[kMaxRadixSegs];
+  __shared__ uint64_t s_pre[MS], s_res[MS];
+  __shared__ int32_t s_st[MS], s_sz[MS], s_rank[MS],
+      s_cnt[MS], s_cnt2[MS], s_lb[MS], s_dig[MS],
+      s_bel[MS];
+  __shared__ unsigned char s_done[MS], s_fnd[MS];
   __shared__ uint32_t s_w[32];
   __shared__ int s_ncand;
   __shared__ int s_multi[3];   // a pending segment's median bucket holds more than one record
   // key bits still open per segment (the digits below them are the next to
   // decide): this level's, and the next level's set by the partition
-  __shared__ int32_t s_sh[kMaxRadixSegs], s_shn[kMaxRadixSegs];
+  __shared__ int32_t s_sh[MS], s_shn[MS];
 
   const int cap = P.cap, dim = P.dim;
   int b = blockIdx.x;
@@ -726,23 +734,23 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
 
   int32_t *sc = (int32_t *)sm;                          // [dim][cap]
   int32_t *sid = sc + (size_t)dim * cap;                // [cap]
-  uint32_t *hist = (uint32_t *)(sid + cap);             // [2048]
-  uint32_t *ex = hist + kHistBins;                      // [2048] exclusive prefix of hist
-  uint16_t *perm0 = (uint16_t *)(ex + kHistBins);       // [cap]
+  uint32_t *hist = (uint32_t *)(sid + cap);             // [HB]
+  uint32_t *ex = hist + HB;                             // [HB] exclusive prefix of hist
+  uint16_t *perm0 = (uint16_t *)(ex + HB);       // [cap]
   uint16_t *perm1 = perm0 + cap;                        // [cap]
   unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap] segment of each position
   unsigned char *segid_n = segid + cap;                   // [cap] the same for the next level
   // per-segment coordinate bounds [lo, hi] in every dimension, of this
-  // level's segments and of the next level's: [kMaxRadixSegs][dim][2] each
+  // level's segments and of the next level's: [MS][dim][2] each
   int32_t *bcur = (int32_t *)(segid_n + cap);
-  int32_t *bnxt = bcur + kMaxRadixSegs * dim * 2;
+  int32_t *bnxt = bcur + MS * dim * 2;
 
   const int32_t *src = P.stg[T.sel];
   if (threadIdx.x < dim) {
     bcur[2 * threadIdx.x] = INT32_MAX;
     bcur[2 * threadIdx.x + 1] = INT32_MIN;
   }
-  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;   // bins start at zero
+  for (int i = threadIdx.x; i < HB; i += blockDim.x) hist[i] = 0;   // bins start at zero
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
     for (int c = 0; c < dim; ++c) sc[c * cap + q] = src[c * P.S + T.base + start0 + q];
     sid[q] = src[dim * P.S + T.base + start0 + q];
@@ -785,7 +793,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
     const int mmax = (int)sz_;
     if (mmax > kWarpMode) {
       // ---------------- radix mode: all segments of the level together ----
-      const int w = 11 - u;      // nseg << w == 2048 bins
+      const int w = LB - u;      // nseg << w == HB bins
       for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
         int64_t a, z;
         seg_range(m0, u, s, a, z);
@@ -866,7 +874,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             ex[i2 + 1] = e + a0;
           }
           __syncthreads();
-          for (int j = threadIdx.x; j < kHistBins; j += blockDim.x) {
+          for (int j = threadIdx.x; j < HB; j += blockDim.x) {
             const int s = j >> w;
             const uint32_t cj = hist[j];
             hist[j] = 0;
@@ -981,7 +989,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
       int64_t nst_, nsz_;
       seg_range(m0, u + 1, 0, nst_, nsz_);
       const bool next_radix = u + 1 < U && nsz_ > kWarpMode;
-      const int wn = 10 - u;                 // the next level's digit width, 11 - (u + 1)
+      const int wn = LB - 1 - u;             // the next level's digit width, LB - (u + 1)
       const int cn = (t + 1) % dim;
       if (next_radix) {
         // the children's bounds: the parent's, cut at the median's
@@ -1000,7 +1008,7 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subtree(const SubParams P) {
             s_shn[ch] = open_key_bits(bnxt[(ch * dim + cn) * 2], bnxt[(ch * dim + cn) * 2 + 1]);
         }
       }
-      const int ipt = (cap + blockDim.x - 1) / blockDim.x;   // 2, 4 or 8 (cap <= 8 x 1024)
+      const int ipt = (cap + blockDim.x - 1) / blockDim.x;   // 2, 4 or 8 (cap <= 8 TH)
       const int q0 = threadIdx.x * ipt;
       // this thread's positions' records and segments, read once (one vector
       // load each where the positions fill one: no bank conflicts between
@@ -1388,9 +1396,11 @@ int coop_grid(const void *fn, int threads, int *out) {
   return BDL_OK;
 }
 
-size_t subtree_smem_bytes(int dim, int cap) {
-  return (size_t)cap * (4 * dim + 4) + 2 * kHistBins * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap +
-         2 * (size_t)kMaxRadixSegs * dim * 2 * 4;
+// Dynamic shared memory of a k_subtree CTA of `th` threads for subtrees of
+// at most `cap` records.
+size_t subtree_smem_bytes(int dim, int cap, int th = kSubThreads) {
+  return (size_t)cap * (4 * dim + 4) + 2 * (size_t)(2 * th) * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap +
+         2 * (size_t)(th / 8) * dim * 2 * 4;
 }
 
 NodeOut node_out(Tree *t) {
@@ -1513,8 +1523,9 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     gmax = std::max(gmax, g);
   }
   S = std::max<int64_t>(S, 8);
+  int sms = 0;
   {
-    int dev = 0, sms = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
     if (const char *e = getenv("BDL_BUILD_SLOTS")) {   // slots of the schedule model
@@ -1526,7 +1537,7 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
 
   // ---- plan arrays ----
   std::vector<DTree> dt(ntree);
-  std::vector<int64_t> pool_off(ntree + 1, 0), sub_blk(ntree + 1, 0);
+  std::vector<int64_t> pool_off(ntree + 1, 0);
   std::vector<int32_t> sub_ord(ntree);
   for (int j = 0; j < ntree; ++j) {
     const BuildTree &b = bt[j];
@@ -1552,7 +1563,25 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   for (int j = 0; j < ntree; ++j) sub_ord[j] = j;
   auto cost_of = [&](int j) { return subtree_cost(ceil_div(bt[j].s, (int64_t)1 << bt[j].g), bt[j].h - bt[j].g); };
   std::stable_sort(sub_ord.begin(), sub_ord.end(), [&](int a, int b) { return cost_of(a) > cost_of(b); });
-  for (int j = 0; j < ntree; ++j) sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << bt[sub_ord[j]].g);
+  // trees whose subtrees hold fewer than kSmallSub records (buffer trees,
+  // the smallest trees) go to the 256-thread instance, in a launch of their
+  // own after the 1,024-thread one, when there are enough of them to fill
+  // the SMs (a batched build over many forests); a few stay in the large
+  // launch, whose last wave they fill.  Each launch has its own order and
+  // prefix.
+  auto small = [&](int j) { return ceil_div(bt[j].s, (int64_t)1 << bt[j].g) < kSmallSub; };
+  int64_t nsmall_sub = 0;
+  for (int j = 0; j < ntree; ++j)
+    if (small(j)) nsmall_sub += (int64_t)1 << bt[j].g;
+  const bool split_small = nsmall_sub >= std::max(sms, 1);
+  const int nbig = split_small ? (int)(std::stable_partition(sub_ord.begin(), sub_ord.end(),
+                                                             [&](int j) { return !small(j); }) -
+                                       sub_ord.begin())
+                               : ntree;
+  std::vector<int64_t> sub_blk(nbig + 1, 0), sub_blk_s(ntree - nbig + 1, 0);
+  for (int j = 0; j < nbig; ++j) sub_blk[j + 1] = sub_blk[j] + ((int64_t)1 << bt[sub_ord[j]].g);
+  for (int j = nbig; j < ntree; ++j)
+    sub_blk_s[j - nbig + 1] = sub_blk_s[j - nbig] + ((int64_t)1 << bt[sub_ord[j]].g);
   const int TB = kCoopThreads;   // cleared records per gather work item
   std::vector<DCleared> dc(cl.size());
   std::vector<int64_t> cl_blk(cl.size() + 1, 0);
@@ -1622,7 +1651,8 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
   }
   PlanImage img;
   const size_t o_dt = img.put(dt), o_dc = img.put(dc), o_clb = img.put(cl_blk),
-               o_pool = img.put(pool_off), o_sub = img.put(sub_blk), o_ord = img.put(sub_ord),
+               o_pool = img.put(pool_off), o_sub = img.put(sub_blk), o_subs = img.put(sub_blk_s),
+               o_ord = img.put(sub_ord),
                o_act = img.put(act_all),
                o_pre = img.put(pre_all), o_lt = img.put(lt_all);
   std::vector<TreeSeg> pk_segs;
@@ -1753,35 +1783,41 @@ int build_trees_object(bdl_forest *af, int dim, std::vector<BuildTree> &bt,
     st = coop((const void *)k_build_levels, kCoopThreads, args, kK_build_levels, gbytes + lv_bytes);
   }
 
-  // ---- subtrees on chip ----
-  if (!st) {
+  // ---- subtrees on chip: the 1,024-thread launch, then the 256-thread one ----
+  for (int part = 0; part < 2 && !st; ++part) {
+    const int j0 = part ? nbig : 0, j1 = part ? ntree : nbig;
+    if (j0 == j1) continue;
     SubParams P;
-    P.ntrees = ntree;
+    P.ntrees = j1 - j0;
     P.dim = dim;
-    P.cap = cap;
+    P.cap = part ? kSmallSub : cap;
     P.S = S;
     P.stg[0] = stg[0];
     P.stg[1] = stg[1];
     P.tree = d_tree;
-    P.sub_blk = (const int64_t *)(plan + o_sub);
-    P.sub_ord = (const int32_t *)(plan + o_ord);
-    size_t smem = subtree_smem_bytes(dim, cap);
-    cudaError_t e = cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSubtreeSmemMax);
-    if (e != cudaSuccess) {
-      st = cuda_check(e, "cudaFuncSetAttribute(k_subtree)");
-    } else {
-      // algorithmic bytes: every record read from staging (d + 1 words) and
-      // written in leaf order (rec_ints words); every node below the global
-      // levels written (16-byte node, box, live count); the leaf offsets
-      double sub_bytes = 0;
-      for (auto &b : bt)
-        sub_bytes += (double)b.s * 4.0 * ((dim + 1) + rec_ints(dim)) +
-                     (double)(((int64_t)2 << b.h) - ((int64_t)1 << b.g)) * (16.0 + 8.0 * dim + 4.0) +
-                     4.0 * (double)(((int64_t)1 << b.h) + 1);
-      KScope ks_(kK_subtree, s, sub_bytes);
-      k_subtree<<<(unsigned)sub_blk.back(), kSubThreads, smem, s>>>(P);
+    P.sub_blk = (const int64_t *)(plan + (part ? o_subs : o_sub));
+    P.sub_ord = (const int32_t *)(plan + o_ord) + j0;
+    const int th = part ? kSmallSubThreads : kSubThreads;
+    const size_t smem = subtree_smem_bytes(dim, P.cap, th);
+    const void *fn = part ? (const void *)k_subtree<kSmallSubThreads> : (const void *)k_subtree<kSubThreads>;
+    st = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "cudaFuncSetAttribute(k_subtree)");
+    if (st) break;
+    // algorithmic bytes: every record read from staging (d + 1 words) and
+    // written in leaf order (rec_ints words); every node below the global
+    // levels written (16-byte node, box, live count); the leaf offsets
+    double sub_bytes = 0;
+    for (int j = j0; j < j1; ++j) {
+      const BuildTree &b = bt[sub_ord[j]];
+      sub_bytes += (double)b.s * 4.0 * ((dim + 1) + rec_ints(dim)) +
+                   (double)(((int64_t)2 << b.h) - ((int64_t)1 << b.g)) * (16.0 + 8.0 * dim + 4.0) +
+                   4.0 * (double)(((int64_t)1 << b.h) + 1);
     }
+    const unsigned grid = (unsigned)(part ? sub_blk_s.back() : sub_blk.back());
+    KScope ks_(kK_subtree, s, sub_bytes);
+    if (part) k_subtree<kSmallSubThreads><<<grid, kSmallSubThreads, smem, s>>>(P);
+    else k_subtree<kSubThreads><<<grid, kSubThreads, smem, s>>>(P);
+    st = cuda_check(cudaGetLastError(), "k_subtree");
   }
 
   // ---- boxes and live counts of the global-level nodes, deepest first ----

@@ -72,3 +72,37 @@ def test_batched_builds_mixed_dims(monkeypatch):
         same_forest(g, o, "forest %d" % j)
     for g in gs:
         g.close()
+
+
+def test_small_subtree_instance(monkeypatch):
+    """Subtrees of fewer than 2,048 records go to the kernel's 256-thread
+    instance when they are at least as many as the schedule's slots (two
+    here): many small forests, of four dimensions, built in batched calls and
+    rebuilt by an erase, tree by tree against the oracle; then k-NN rows
+    (whose buffer trees are built the same way)."""
+    from paper_2112_06188_gb300.forest import Forest, erase_batch, insert_batch, knn_batch
+    from oracle.threads import oracle_knn
+    monkeypatch.setenv("BDL_BUILD_SLOTS", "2")
+    specs = [(d, n) for d in (2, 3, 5, 7) for n in (1_100, 2_500, 5_900)]
+    gs = [Forest(d) for d, _ in specs]
+    os_ = [OracleForest(d) for d, _ in specs]
+    pts = [inputs.uniform_points(n, d, seed=740 + j) for j, (d, n) in enumerate(specs)]
+    insert_batch(gs, [dev(p) for p in pts])
+    for o, p in zip(os_, pts):
+        o.insert(p)
+    for j, (g, o) in enumerate(zip(gs, os_)):
+        same_forest(g, o, "forest %d after the build" % j)
+    eras = [inputs.sample_ids(np.arange(n), int(0.6 * n), seed=760 + j) for j, (_, n) in enumerate(specs)]
+    erase_batch(gs, [dev(e) for e in eras])
+    for o, e in zip(os_, eras):
+        o.erase(e)
+    for j, (g, o) in enumerate(zip(gs, os_)):
+        same_forest(g, o, "forest %d after the erase" % j)
+    qs = [inputs.uniform_points(600, d, seed=780 + j) for j, (d, _) in enumerate(specs)]
+    out = knn_batch(gs, [dev(q) for q in qs], 6)
+    torch.cuda.synchronize()
+    for j, ((gi, gd), o, q) in enumerate(zip(out, os_, qs)):
+        oi, od = oracle_knn(o, q, 6)
+        assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od), "k-NN of forest %d" % j
+    for g in gs:
+        g.close()
