@@ -42,6 +42,11 @@
  *    an estimated schedule of the subtree CTAs on the device's SMs
  *    (BDL_BUILD_SLOTS=n, read at every build, schedules on n slots instead).
  *    The trees are the same either way.
+ *  - Memory: without an hbm budget, static trees are laid out for their
+ *    level's capacity X*2^level and each level keeps the block of its last
+ *    cleared tree for the level's next tree (no allocation per carry); those
+ *    blocks stay the forest's until bdl_destroy.  With a budget, trees take
+ *    exactly their size and nothing is kept.
  */
 #ifndef BDL_H
 #define BDL_H
