@@ -709,12 +709,11 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint64_t s_pre[MS], s_res[MS];
   __shared__ int32_t s_st[MS], s_sz[MS], s_rank[MS],
-      s_cnt[MS], s_cnt2[MS], s_lb[MS], s_dig[MS],
-      s_bel[MS];
-  __shared__ unsigned char s_done[MS], s_fnd[MS];
-  __shared__ uint32_t s_w[32];
+      s_cnt2[MS], s_lb[MS], s_dig[MS],
+      s_bel[MS], s_wq[MS];
+  __shared__ unsigned char s_done[MS];
+  __shared__ uint32_t s_w[32], s_base[8];
   __shared__ int s_ncand;
-  __shared__ int s_multi[3];   // a pending segment's median bucket holds more than one record
   // key bits still open per segment (the digits below them are the next to
   // decide): this level's, and the next level's set by the partition
   __shared__ int32_t s_sh[MS], s_shn[MS];
@@ -735,10 +734,13 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
   int32_t *sc = (int32_t *)sm;                          // [dim][cap]
   int32_t *sid = sc + (size_t)dim * cap;                // [cap]
   uint32_t *hist = (uint32_t *)(sid + cap);             // [HB]
-  uint32_t *ex = hist + HB;                             // [HB] exclusive prefix of hist
-  uint16_t *perm0 = (uint16_t *)(ex + HB);       // [cap]
+  // [HB] a record that the pass counted in the bin: the only one where the
+  // bin's count is 1
+  uint16_t *wit = (uint16_t *)(hist + HB);
+  uint16_t *perm0 = wit + HB;                           // [cap]
   uint16_t *perm1 = perm0 + cap;                        // [cap]
-  unsigned char *segid = (unsigned char *)(perm1 + cap);  // [cap] segment of each position
+  uint16_t *binq = perm1 + cap;                         // [cap] first digit of each position's key
+  unsigned char *segid = (unsigned char *)(binq + cap);   // [cap] segment of each position
   unsigned char *segid_n = segid + cap;                   // [cap] the same for the next level
   // per-segment coordinate bounds [lo, hi] in every dimension, of this
   // level's segments and of the next level's: [MS][dim][2] each
@@ -778,7 +780,9 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
 
   const int U = T.h - t0;
   const int nleaf = 1 << U;
-  int32_t *nslot = (int32_t *)hist;   // [2 * nleaf] vEB slots by heap index, once computed
+  // [2 * nleaf] vEB slots by heap index, once computed after the radix
+  // levels (with the warps' 64 results it may run on into `wit`)
+  int32_t *nslot = (int32_t *)hist;
   bool slots_ready = false;
   bool hist_ready = false;   // `hist` holds this level's first-pass histogram already
   uint16_t *cur = perm0, *nxt = perm1;
@@ -806,109 +810,138 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
         s_sh[s] = sh;
         s_pre[s] = sh >= kKeyBits ? 0 : ((uint64_t)lo >> (sh - 31)) << sh;
         s_rank[s] = (int)((z + 1) >> 1);
-        if (s < 3) s_multi[s] = 0;
+        s_cnt2[s] = 0;
         if (s == 0) s_ncand = 0;
         s_done[s] = 0;
-        s_fnd[s] = 0;
-        s_cnt[s] = 0;
       }
       __syncthreads();
       // Every pass decides the next w open bits of each segment's median
-      // key (the digit below its s_sh open bits).  The first pass's
-      // histogram was filled by the previous level's partition, except at the
-      // subtree's first level.  After the first pass, the records that can
-      // still hold their segment's median (key prefix = the chosen digits)
-      // are listed once in `nxt` (free until this level's partition), and the
-      // later passes read only them.  The bins are zero at the start of every
-      // pass that counts (each pass's bucket search clears them).
+      // key (the digit below its s_sh open bits) from a histogram of the
+      // records that still match the segment's prefix.  Pass 0 counts every
+      // record; its histogram was filled by the previous level's partition,
+      // except at the subtree's first level, and each position's digit is
+      // kept in `binq`.  Pass 1 lists the records whose digit is their
+      // segment's chosen one (in `nxt`, free until this level's partition)
+      // and counts them; later passes read only that list.  A bucket that
+      // holds one record ends its segment's search: the bin's witness is
+      // the median.  The bins are zero at the start of every pass that
+      // counts (each pass's bucket search clears them).
       uint16_t *cand = nxt;
-      bool first = true;
       const int nbin = 1 << w, per = (nbin + 31) >> 5;   // bins per segment, per lane
       for (int pass = 0;; ++pass) {
-        if (!(first && hist_ready)) {
-          const int nq = first ? m0 : s_ncand;
+        if (pass == 0) {
+          if (!hist_ready) {
+            for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+              const int s = segid[q], it = cur[q];
+              const uint64_t k = skey(sc, sid, cap, c, it);
+              const int sh = s_sh[s], ns = max(0, sh - w);
+              const int dg = (int)((k >> ns) & ((1u << (sh - ns)) - 1));
+              binq[q] = (uint16_t)dg;
+              wit[(s << w) + dg] = (uint16_t)it;
+              atomicAdd(&hist[(s << w) + dg], 1u);
+            }
+            __syncthreads();
+          }
+        } else if (pass == 1) {
+          for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+            const int s = segid[q];
+            if (s_done[s] || binq[q] != s_dig[s]) continue;
+            cand[atomicAdd(&s_ncand, 1)] = (uint16_t)q;
+            const int it = cur[q];
+            const uint64_t k = skey(sc, sid, cap, c, it);
+            const int sh = s_sh[s], ns = max(0, sh - w);
+            const int dg = (int)((k >> ns) & ((1u << (sh - ns)) - 1));
+            wit[(s << w) + dg] = (uint16_t)it;
+            atomicAdd(&hist[(s << w) + dg], 1u);
+          }
+          __syncthreads();
+        } else {
+          const int nq = s_ncand;
           for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-            const int q = first ? i : cand[i];
-            int s = segid[q];
+            const int q = cand[i];
+            const int s = segid[q];
             if (s_done[s]) continue;
-            uint64_t k = skey(sc, sid, cap, c, cur[q]);
+            const int it = cur[q];
+            const uint64_t k = skey(sc, sid, cap, c, it);
             const int sh = s_sh[s], ns = max(0, sh - w);
             if ((k >> sh) != (s_pre[s] >> sh)) continue;
-            if (s_cnt[s] == 1) { s_res[s] = k; s_fnd[s] = 1; continue; }
-            atomicAdd(&hist[(s << w) + (int)((k >> ns) & ((1u << (sh - ns)) - 1))], 1u);
+            const int dg = (int)((k >> ns) & ((1u << (sh - ns)) - 1));
+            wit[(s << w) + dg] = (uint16_t)it;
+            atomicAdd(&hist[(s << w) + dg], 1u);
           }
           __syncthreads();
         }
         // the bucket holding each segment's rank-th candidate; the segment's
-        // prefix, rank and open bits move into it and the bins are cleared.
-        // s_multi[pass % 3]: a segment's new bucket holds more than one
-        // record (three flags, so that clearing the next pass's needs no
-        // barrier of its own)
-        if (threadIdx.x == 0) s_multi[(pass + 1) % 3] = 0;
+        // prefix, rank and open bits move into it and the bins are cleared
         int pending = 0;
         if (nseg < 8) {
           // few segments: an exclusive scan of all the bins (2 per thread)
-          {
-            const int i2 = 2 * threadIdx.x;
-            const uint32_t a0 = hist[i2], a1 = hist[i2 + 1];
-            const uint32_t v = a0 + a1;
-            uint32_t inc = v;
+          const int i2 = 2 * threadIdx.x;
+          const uint32_t a0 = hist[i2], a1 = hist[i2 + 1];
+          const uint32_t v = a0 + a1;
+          uint32_t inc = v;
+          for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+            if (lane >= o2) inc += y;
+          }
+          if (lane == 31) s_w[warp] = inc;
+          __syncthreads();
+          if (warp == 0) {
+            const uint32_t x = lane < nwarps ? s_w[lane] : 0;
+            uint32_t xi = x;
             for (int o2 = 1; o2 < 32; o2 <<= 1) {
-              const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
-              if (lane >= o2) inc += y;
+              const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
+              if (lane >= o2) xi += y;
             }
-            if (lane == 31) s_w[warp] = inc;
-            __syncthreads();
-            if (warp == 0) {
-              const uint32_t x = lane < nwarps ? s_w[lane] : 0;
-              uint32_t xi = x;
-              for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o2);
-                if (lane >= o2) xi += y;
-              }
-              if (lane < nwarps) s_w[lane] = xi - x;
-            }
-            __syncthreads();
-            const uint32_t e = inc - v + s_w[warp];
-            ex[i2] = e;
-            ex[i2 + 1] = e + a0;
+            if (lane < nwarps) s_w[lane] = xi - x;
           }
           __syncthreads();
-          for (int j = threadIdx.x; j < HB; j += blockDim.x) {
-            const int s = j >> w;
-            const uint32_t cj = hist[j];
-            hist[j] = 0;
-            if (s >= nseg || s_done[s] || s_cnt[s] == 1) continue;
-            const uint32_t below = ex[j] - ex[s << w];
+          const uint32_t e = inc - v + s_w[warp];
+          if ((i2 & (nbin - 1)) == 0) s_base[i2 >> w] = e;   // the segment's first bin
+          __syncthreads();
+          hist[i2] = 0;
+          hist[i2 + 1] = 0;
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int j = i2 + h2, s = j >> w;
+            const uint32_t cj = h2 ? a1 : a0;
+            if (s_done[s]) continue;
             // record the bucket only: s_rank is read by the other bins of this
             // segment in this same phase and is updated after the barrier
-            if (below < (uint32_t)s_rank[s] && (uint32_t)s_rank[s] <= below + cj) {
-              s_dig[s] = j & ((1 << w) - 1);
+            const uint32_t below = (h2 ? e + a0 : e) - s_base[s], r = (uint32_t)s_rank[s];
+            if (below < r && r <= below + cj) {
+              s_dig[s] = j & (nbin - 1);
               s_bel[s] = (int)below;
               s_cnt2[s] = (int)cj;
+              s_wq[s] = wit[j];
             }
           }
           __syncthreads();
           for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
             if (s_done[s]) continue;
-            if (s_fnd[s]) { s_done[s] = 1; continue; }
+            const int cnt = s_cnt2[s];
+            s_cnt2[s] = 0;
             const int ns = max(0, s_sh[s] - w);
             s_pre[s] |= (uint64_t)s_dig[s] << ns;
             s_rank[s] -= s_bel[s];
-            s_cnt[s] = s_cnt2[s];
             s_sh[s] = ns;
-            if (ns == 0) { s_res[s] = s_pre[s]; s_done[s] = 1; continue; }
-            pending = 1;
-            if (s_cnt[s] > 1) s_multi[pass % 3] = 1;
+            if (cnt == 1) {
+              s_res[s] = skey(sc, sid, cap, c, s_wq[s]);
+              s_done[s] = 1;
+            } else if (cnt == 0) {   // counts inconsistent with the rank
+              atomicOr(T.err, kErrPartition);
+              s_done[s] = 1;
+            } else if (ns == 0) {
+              s_res[s] = s_pre[s];
+              s_done[s] = 1;
+            } else {
+              pending = 1;
+            }
           }
         } else {
           // one warp per segment: a scan of the segment's bins across the lanes
           for (int s = warp; s < nseg; s += nwarps) {
             if (s_done[s]) continue;
-            if (s_fnd[s]) {
-              if (lane == 0) s_done[s] = 1;
-              continue;
-            }
             uint32_t *h = hist + (s << w) + lane * per;
             const int nb = max(0, min(per, nbin - lane * per));
             uint32_t sum = 0;
@@ -927,17 +960,19 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
                 below += cj;
                 cj = h[++i];
               }
-              const int ns = max(0, s_sh[s] - w);
-              s_pre[s] |= (uint64_t)(lane * per + i) << ns;
+              const int ns = max(0, s_sh[s] - w), dg = lane * per + i;
+              s_dig[s] = dg;
+              s_pre[s] |= (uint64_t)dg << ns;
               s_rank[s] = (int)(r - below);
-              s_cnt[s] = (int)cj;
               s_sh[s] = ns;
-              if (ns == 0) {
+              if (cj == 1) {
+                s_res[s] = skey(sc, sid, cap, c, wit[(s << w) + dg]);
+                s_done[s] = 1;
+              } else if (ns == 0) {
                 s_res[s] = s_pre[s];
                 s_done[s] = 1;
               } else {
                 pending = 1;
-                if (cj > 1) s_multi[pass % 3] = 1;
               }
             }
             if (!__any_sync(0xffffffffu, mine) && lane == 0) {   // counts inconsistent with the rank
@@ -948,32 +983,6 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
           }
         }
         if (!__syncthreads_or(pending)) break;
-        if (!s_multi[pass % 3]) {
-          // every pending segment's bucket holds one record: that record's key
-          // is the median (one scan instead of another pass)
-          const int nq = first ? m0 : s_ncand;
-          for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-            const int q = first ? i : cand[i];
-            const int s = segid[q];
-            if (s_done[s]) continue;
-            const uint64_t k = skey(sc, sid, cap, c, cur[q]);
-            const int sh = s_sh[s];
-            if ((k >> sh) == (s_pre[s] >> sh)) s_res[s] = k;
-          }
-          __syncthreads();
-          break;
-        }
-        if (first) {   // list the records whose key still matches their segment's prefix
-          for (int q = threadIdx.x; q < m0; q += blockDim.x) {
-            const int s = segid[q];
-            if (s_done[s]) continue;
-            const uint64_t k = skey(sc, sid, cap, c, cur[q]);
-            const int sh = s_sh[s];
-            if ((k >> sh) == (s_pre[s] >> sh)) cand[atomicAdd(&s_ncand, 1)] = (uint16_t)q;
-          }
-          __syncthreads();
-          first = false;
-        }
       }
       hist_ready = false;
       // node keys
@@ -1094,7 +1103,10 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
               if (next_radix) {   // the child's first digit, below its open key bits
                 const int ch = 2 * s + (left ? 0 : 1), sh = s_shn[ch], ns = max(0, sh - wn);
                 const uint64_t kn = skey(sc, sid, cap, cn, CQ(j));
-                atomicAdd(&hist[(ch << wn) + (int)((kn >> ns) & ((1u << (sh - ns)) - 1))], 1u);
+                const int dg = (int)((kn >> ns) & ((1u << (sh - ns)) - 1));
+                binq[dst] = (uint16_t)dg;
+                wit[(ch << wn) + dg] = (uint16_t)CQ(j);
+                atomicAdd(&hist[(ch << wn) + dg], 1u);
               }
             }
             run += (flags >> j) & 1;
@@ -1399,7 +1411,7 @@ int coop_grid(const void *fn, int threads, int *out) {
 // Dynamic shared memory of a k_subtree CTA of `th` threads for subtrees of
 // at most `cap` records.
 size_t subtree_smem_bytes(int dim, int cap, int th = kSubThreads) {
-  return (size_t)cap * (4 * dim + 4) + 2 * (size_t)(2 * th) * 4 + (size_t)cap * 2 * 2 + 2 * (size_t)cap +
+  return (size_t)cap * (4 * dim + 4) + (size_t)(2 * th) * (4 + 2) + (size_t)cap * 2 * 3 + 2 * (size_t)cap +
          2 * (size_t)(th / 8) * dim * 2 * 4;
 }
 
