@@ -636,6 +636,14 @@ struct SubParams {
   const int32_t *sub_ord;      // [ntrees] the trees in launch order (largest subtrees first)
 };
 
+// An asynchronous 4-byte copy from global to shared memory (completed by
+// cp.async.wait_all).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
 // Ascending bitonic sort of one 64-bit word per lane across a warp.
 __device__ __forceinline__ uint64_t warp_sort32(uint64_t x, int lane) {
 #pragma unroll
@@ -753,13 +761,17 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
     bcur[2 * threadIdx.x + 1] = INT32_MIN;
   }
   for (int i = threadIdx.x; i < HB; i += blockDim.x) hist[i] = 0;   // bins start at zero
+  // the records' planes, copied asynchronously (all of a thread's copies in
+  // flight at once)
+  const int32_t *rec0 = src + T.base + start0;
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
-    for (int c = 0; c < dim; ++c) sc[c * cap + q] = src[c * P.S + T.base + start0 + q];
-    sid[q] = src[dim * P.S + T.base + start0 + q];
+    for (int c = 0; c < dim; ++c) cp_async4(&sc[c * cap + q], rec0 + c * P.S + q);
+    cp_async4(&sid[q], rec0 + dim * P.S + q);
     perm0[q] = (uint16_t)q;
     perm1[q] = (uint16_t)q;   // any slot a level leaves unwritten still names a record
     segid[q] = 0;
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   // the subtree's bounding box: the root segment's bounds
   for (int c = 0; c < dim; ++c) {
@@ -1297,14 +1309,21 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
       }
     }
   }
-  // point records in leaf order
+  // point records in leaf order (16-byte stores: a record is rs ints, a
+  // multiple of 4)
   const int rs = rec_ints(dim);
   for (int q = threadIdx.x; q < m0; q += blockDim.x) {
-    int it = cur[q];
-    int32_t *dst = o.pts + (start0 + q) * rs;
-    for (int cc = 0; cc < dim; ++cc) dst[cc] = sc[cc * cap + it];
-    dst[dim] = sid[it];
-    for (int cc = dim + 1; cc < rs; ++cc) dst[cc] = 0;
+    const int it = cur[q];
+    int4 *dst = reinterpret_cast<int4 *>(o.pts + (start0 + q) * rs);
+    for (int c4 = 0; c4 < rs; c4 += 4) {
+      int32_t v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int cc = c4 + e;
+        v[e] = cc < dim ? sc[cc * cap + it] : cc == dim ? sid[it] : 0;
+      }
+      dst[c4 >> 2] = make_int4(v[0], v[1], v[2], v[3]);
+    }
   }
 }
 
