@@ -215,6 +215,20 @@ __device__ __forceinline__ TileSegs tile_segs(const LvParams &P, const LvTree &T
   return g;
 }
 
+// Eight consecutive ints from x[p] (x + p is 32-byte aligned when p is a
+// multiple of 8); positions at or past `end` are not read.
+__device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, int32_t v[kItems]) {
+  if (p + kItems <= end) {
+    const int4 a = reinterpret_cast<const int4 *>(x + p)[0];
+    const int4 b = reinterpret_cast<const int4 *>(x + p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) v[j] = p + j < end ? x[p + j] : 0;
+  }
+}
+
 // Tile b of the level: 11-bit histogram of the split coordinate, per segment.
 __device__ void level_hist(const LvParams &P, int64_t b, uint32_t (*h)[kHistBins]) {
   const LvTree &T = tree_by_tile(P, b);
@@ -309,10 +323,17 @@ __device__ void level_collect(const LvParams &P, int64_t b) {
   uint64_t key[kItems];
   unsigned slot[kItems];
   int nk = 0;
-  for (int64_t p = g.p0 + threadIdx.x; p < g.p1; p += blockDim.x) {
-    int32_t c = x[p];
-    int w = p >= g.st1;
-    if ((c >> kHistShift) == (w ? bk1 : bk0)) {
+  // the tile's split coordinates, eight consecutive ones per thread
+  // (kCoopThreads * kItems = tile)
+  const int64_t pb = g.p0 + (int64_t)threadIdx.x * kItems;
+  int32_t cv[kItems];
+  load8(x, pb, g.p1, cv);
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t p = pb + j;
+    const int32_t c = cv[j];
+    const int w = p >= g.st1;
+    if (p < g.p1 && (c >> kHistShift) == (w ? bk1 : bk0)) {
       key[nk] = ((uint64_t)(c & ((1 << kHistShift) - 1)) << 31) | (uint32_t)xi[p];
       slot[nk] = (atomicAdd(&cnt[w], 1u) << 1) | (unsigned)w;
       nk++;
@@ -418,19 +439,6 @@ __device__ void level_select(const LvParams &P, int64_t gs, uint64_t *keys) {
   }
 }
 
-// Eight consecutive ints from x[p] (x + p is 32-byte aligned when p is a
-// multiple of 8); positions at or past `end` are not read.
-__device__ __forceinline__ void load8(const int32_t *x, int64_t p, int64_t end, int32_t v[kItems]) {
-  if (p + kItems <= end) {
-    const int4 a = reinterpret_cast<const int4 *>(x + p)[0];
-    const int4 b = reinterpret_cast<const int4 *>(x + p)[1];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) v[j] = p + j < end ? x[p + j] : 0;
-  }
-}
 
 // K2: partition every tile's records around their segment's median into the
 // other staging buffer.  Left records of a segment go to [st, st+ceil(m/2)),
@@ -518,11 +526,13 @@ __device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage, ui
   }
   // each array: scatter into shared memory, then write every class's run
   // with consecutive threads on consecutive addresses; the next level's
-  // split coordinate also goes into its child segment's histogram
+  // split coordinate also goes into its child segment's histogram.  The
+  // next array's items are loaded as soon as this one's are scattered, so
+  // that their loads overlap the barrier and the stores.
   const int ntile = coff[4];
+  int32_t v[kItems];
+  load8(P.src + T.base, pb, g.p1, v);
   for (int c = 0; c <= P.dim; ++c) {
-    int32_t v[kItems];
-    load8(P.src + c * P.S + T.base, pb, g.p1, v);
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
       if (spos[j] >= 0) {
@@ -532,6 +542,7 @@ __device__ void level_partition(const LvParams &P, int64_t b, int32_t *stage, ui
           atomicAdd(&hnext[cls[j] * (kHistBins / 2) + (bin >> 1)], 1u << (16 * (bin & 1)));
         }
       }
+    if (c < P.dim) load8(P.src + (c + 1) * P.S + T.base, pb, g.p1, v);
     __syncthreads();
     int32_t *y = P.dst + c * P.S + T.base;
     for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
