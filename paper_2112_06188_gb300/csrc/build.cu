@@ -236,10 +236,12 @@ __device__ void level_hist(const LvParams &P, int64_t b, uint32_t (*h)[kHistBins
   for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const int32_t *x = P.src + T.c * P.S + T.base;
-  for (int64_t p = g.p0 + threadIdx.x; p < g.p1; p += blockDim.x) {
-    int32_t c = x[p];
-    atomicAdd(&h[p >= g.st1][c >> kHistShift], 1u);
-  }
+  const int64_t pb = g.p0 + (int64_t)threadIdx.x * kItems;   // kCoopThreads * kItems = tile
+  int32_t cv[kItems];
+  load8(x, pb, g.p1, cv);
+#pragma unroll
+  for (int j = 0; j < kItems; ++j)
+    if (pb + j < g.p1) atomicAdd(&h[pb + j >= g.st1][cv[j] >> kHistShift], 1u);
   __syncthreads();
   uint32_t *h0 = P.hist + (T.seg_off + g.idx0) * kHistBins;
   for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) {
@@ -1143,12 +1145,19 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
       unsigned char *ts = segid; segid = segid_n; segid_n = ts;
       int32_t *tb = bcur; bcur = bnxt; bnxt = tb;
     } else {
-      // ---------------- warp mode: one warp sorts each segment -------------
-      // Words (key << 13 | position) are distinct and order like the keys
-      // (positions < cap <= 8192); a bitonic network across the warp sorts
-      // them, so the segment comes out in key order and its median is at
-      // rank ceil(z/2) - 1.  At the first such level every node's vEB slot
-      // is computed once, in heap order (node (u, s) at (1 << u) + s), in the
+      // ---------------- warp mode: one warp splits each segment ------------
+      // A segment of z <= 64 records.  Above the last level, two per lane
+      // (positions a + lane and a + 32 + lane): the median key (rank
+      // ceil(z/2) - 1; the keys are distinct) is found bit by bit from the
+      // highest bit where the segment's keys differ (a ballot counts the
+      // candidates with a 0 there, and the candidates keep the side that
+      // holds the rank, until one is left), and the records with keys up to
+      // the median take the segment's first ceil(z/2) positions (ballot
+      // prefix counts).  At the last level a bitonic network across the warp
+      // sorts words (key << 13 | position), distinct and ordered like the
+      // keys (positions < cap <= 8192), so that every leaf holds its records
+      // in key order.  At the first such level every node's vEB slot is
+      // computed once, in heap order (node (u, s) at (1 << u) + s), in the
       // histogram space (free from here on); the leaves use them too.
       if (!slots_ready && nleaf <= (int)blockDim.x) {
         for (int x = threadIdx.x + 1; x < 2 * nleaf; x += blockDim.x) {
@@ -1158,35 +1167,76 @@ __global__ void __launch_bounds__(TH, TH == kSubThreads ? 1 : 3) k_subtree(const
         slots_ready = true;
         __syncthreads();
       }
+      const unsigned lt_mask = (1u << lane) - 1;   // lanes before this one
       for (int s = warp; s < nseg; s += nwarps) {
         int a, z;
         seg_range32(m0, u, s, a, z);
         if (z > 64) { if (lane == 0) atomicOr(T.err, kErrPartition); continue; }
-        const int mr = ((z + 1) >> 1) - 1;
         uint64_t med = 0;
-        if (z <= 32) {
-          uint64_t x = lane < z ? (skey(sc, sid, cap, c, cur[a + lane]) << 13) | cur[a + lane] : ~0ull;
-          x = warp_sort32(x, lane);
-          if (lane < z) nxt[a + lane] = (uint16_t)(x & 8191u);
-          med = __shfl_sync(0xffffffffu, x, mr);
+        if (u == U - 1) {
+          const int mr = ((z + 1) >> 1) - 1;
+          if (z <= 32) {
+            uint64_t x = lane < z ? (skey(sc, sid, cap, c, cur[a + lane]) << 13) | cur[a + lane] : ~0ull;
+            x = warp_sort32(x, lane);
+            if (lane < z) nxt[a + lane] = (uint16_t)(x & 8191u);
+            med = __shfl_sync(0xffffffffu, x, mr) >> 13;
+          } else {
+            const int e0 = 2 * lane, e1 = 2 * lane + 1;
+            uint64_t x0 = e0 < z ? (skey(sc, sid, cap, c, cur[a + e0]) << 13) | cur[a + e0] : ~0ull;
+            uint64_t x1 = e1 < z ? (skey(sc, sid, cap, c, cur[a + e1]) << 13) | cur[a + e1] : ~0ull;
+            warp_sort64(x0, x1, lane);
+            if (e0 < z) nxt[a + e0] = (uint16_t)(x0 & 8191u);
+            if (e1 < z) nxt[a + e1] = (uint16_t)(x1 & 8191u);
+            med = __shfl_sync(0xffffffffu, (mr & 1) ? x1 : x0, mr >> 1) >> 13;
+          }
         } else {
-          const int e0 = 2 * lane, e1 = 2 * lane + 1;
-          uint64_t x0 = e0 < z ? (skey(sc, sid, cap, c, cur[a + e0]) << 13) | cur[a + e0] : ~0ull;
-          uint64_t x1 = e1 < z ? (skey(sc, sid, cap, c, cur[a + e1]) << 13) | cur[a + e1] : ~0ull;
-          warp_sort64(x0, x1, lane);
-          if (e0 < z) nxt[a + e0] = (uint16_t)(x0 & 8191u);
-          if (e1 < z) nxt[a + e1] = (uint16_t)(x1 & 8191u);
-          med = __shfl_sync(0xffffffffu, (mr & 1) ? x1 : x0, mr >> 1);
+          const bool v0 = lane < z, v1 = 32 + lane < z;
+          const int ra = v0 ? cur[a + lane] : 0, rb = v1 ? cur[a + 32 + lane] : 0;
+          const uint64_t k0 = v0 ? skey(sc, sid, cap, c, ra) : 0, k1 = v1 ? skey(sc, sid, cap, c, rb) : 0;
+          // the bits where the keys differ: OR and AND over the records
+          const uint64_t ko = (v0 ? k0 : 0) | (v1 ? k1 : 0), ka = (v0 ? k0 : ~0ull) & (v1 ? k1 : ~0ull);
+          const uint64_t all_or = ((uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)(ko >> 32)) << 32) |
+                                  __reduce_or_sync(0xffffffffu, (unsigned)ko);
+          const uint64_t all_and = ((uint64_t)__reduce_and_sync(0xffffffffu, (unsigned)(ka >> 32)) << 32) |
+                                   __reduce_and_sync(0xffffffffu, (unsigned)ka);
+          const uint64_t diff = all_or ^ all_and;
+          bool c0 = v0, c1 = v1;   // still candidates for the median
+          int r = ((z + 1) >> 1) - 1, n = z;
+          for (int bit = diff ? 63 - __clzll(diff) : -1; bit >= 0 && n > 1; --bit) {
+            const bool b0 = (k0 >> bit) & 1, b1 = (k1 >> bit) & 1;
+            const int cz = __popc(__ballot_sync(0xffffffffu, c0 && !b0)) + __popc(__ballot_sync(0xffffffffu, c1 && !b1));
+            if (r < cz) {
+              c0 = c0 && !b0;
+              c1 = c1 && !b1;
+              n = cz;
+            } else {
+              c0 = c0 && b0;
+              c1 = c1 && b1;
+              r -= cz;
+              n -= cz;
+            }
+          }
+          const unsigned m0b = __ballot_sync(0xffffffffu, c0), m1b = __ballot_sync(0xffffffffu, c1);
+          med = __shfl_sync(0xffffffffu, m0b ? k0 : k1, __ffs(m0b ? m0b : m1b) - 1);
+          // the split: left records first, each side in position order
+          const bool l0 = v0 && k0 <= med, l1 = v1 && k1 <= med;
+          const unsigned L0 = __ballot_sync(0xffffffffu, l0), L1 = __ballot_sync(0xffffffffu, l1);
+          const unsigned R0 = __ballot_sync(0xffffffffu, v0 && !l0), R1 = __ballot_sync(0xffffffffu, v1 && !l1);
+          const int nl = __popc(L0) + __popc(L1);
+          if (v0) nxt[a + (l0 ? __popc(L0 & lt_mask) : nl + __popc(R0 & lt_mask))] = (uint16_t)ra;
+          if (v1) nxt[a + (l1 ? __popc(L0) + __popc(L1 & lt_mask) : nl + __popc(R0) + __popc(R1 & lt_mask))] = (uint16_t)rb;
+          if (lane == 0 && (n != 1 || __popc(m0b) + __popc(m1b) != 1 || nl != (z + 1) >> 1))
+            atomicOr(T.err, kErrPartition);
         }
         if (slots_ready) {
           const int x = (1 << u) + s;
-          if (lane == 0) o.node[nslot[x]] = Node{med >> 13, nslot[2 * x], nslot[2 * x + 1]};
+          if (lane == 0) o.node[nslot[x]] = Node{med, nslot[2 * x], nslot[2 * x + 1]};
         } else {
           // the node's vEB slot and its children's, three lanes at once
           const int64_t bfs = (i0 << u) + s;
           const int64_t sl = lane < 3 ? veb_slot(l, lane ? t + 1 : t, lane ? 2 * bfs + lane - 1 : bfs) : 0;
           const int64_t vl = __shfl_sync(0xffffffffu, sl, 1), vr = __shfl_sync(0xffffffffu, sl, 2);
-          if (lane == 0) o.node[sl] = Node{med >> 13, (int32_t)vl, (int32_t)vr};
+          if (lane == 0) o.node[sl] = Node{med, (int32_t)vl, (int32_t)vr};
         }
       }
       __syncthreads();

@@ -104,8 +104,8 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
   for (int c = 0; c < (D ? D : kMaxDim); ++c) {
     if (c < dd) {
       const int32_t x = q[c];
-      // at most one of the two gaps is positive
-      const float g = (float)(max(box[c] - x, 0) + max(x - box[dd + c], 0));
+      // at most one of the two gaps is positive (lo <= hi)
+      const float g = (float)max(max(box[c] - x, x - box[dd + c]), 0);
       s = fmaf(g, g, s);
     }
   }
@@ -254,10 +254,11 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
           const int4 lo = *reinterpret_cast<const int4 *>(r + 8 + 8 * c);
           const int4 hi = *reinterpret_cast<const int4 *>(r + 12 + 8 * c);
           const int32_t x = q[c];
-          const float g0 = (float)(max(lo.x - x, 0) + max(x - hi.x, 0));
-          const float g1 = (float)(max(lo.y - x, 0) + max(x - hi.y, 0));
-          const float g2 = (float)(max(lo.z - x, 0) + max(x - hi.z, 0));
-          const float g3 = (float)(max(lo.w - x, 0) + max(x - hi.w, 0));
+          // the gap to [lo, hi] (lo <= hi): at most one difference is positive
+          const float g0 = (float)max(max(lo.x - x, x - hi.x), 0);
+          const float g1 = (float)max(max(lo.y - x, x - hi.y), 0);
+          const float g2 = (float)max(max(lo.z - x, x - hi.z), 0);
+          const float g3 = (float)max(max(lo.w - x, x - hi.w), 0);
           s0 = fmaf(g0, g0, s0);
           s1 = fmaf(g1, g1, s1);
           s2 = fmaf(g2, g2, s2);
