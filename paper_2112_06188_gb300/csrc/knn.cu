@@ -46,6 +46,11 @@ constexpr int kKnnMaxThreads = 256;
 // in the default-shape instance, [warp][slot][lane] (S = 32) in the general
 // one, whose block size is a launch parameter.  Only the current k-th pair
 // stays in registers for the pruning tests.
+// The smallest float >= 1 / (1 - 2^-18): 1 + 2^-18 + 2^-23.  Float squared
+// distances (box gaps or leaf points) are compared with the k-th distance
+// scaled up by it (see box_dist_f).
+constexpr float kBoundUp = 1.00000393390655517578125f;
+
 template <int S>
 struct TopK {
   uint64_t *d;     // d[j * S]
@@ -54,7 +59,7 @@ struct TopK {
   uint64_t kd;     // current k-th distance (kNone while fewer than k held)
   int32_t kid;
 
-  float kdf;       // kd rounded up to float (pruning bound)
+  float kdf;       // pruning bound: kd rounded up to float, times kBoundUp rounded up
 
   __device__ __forceinline__ void init(uint64_t *sd, int32_t *sid, int k) {
     const int at = S == 32 ? (threadIdx.x >> 5) * k * 32 + (threadIdx.x & 31) : threadIdx.x;
@@ -85,19 +90,20 @@ struct TopK {
     if (n == k) {
       kd = d[(k - 1) * S];
       kid = id[(k - 1) * S];
-      kdf = __ull2float_ru(kd);
+      kdf = __fmul_ru(__ull2float_ru(kd), kBoundUp);
     }
   }
 };
 
-// Squared distance from q to the box lo[dim], hi[dim] in float, scaled down
-// by (1 - 2^-18): each gap is exact in float and the d <= 16 rounded squares
-// and sums are within (d + 1) * 2^-24 relative of the exact value, so the
-// result never exceeds the exact squared distance.  A subtree is pruned only
-// when this lower bound exceeds the k-th distance rounded up, i.e. never when
-// the exact rule (prune iff mindist^2 > kth) would keep it.
+// Squared distance from q to the box lo[dim], hi[dim] in float.  Each gap is
+// exact in float and the d <= 16 rounded squares and sums are within
+// (d + 1) * 2^-24 < 2^-18 relative of the exact value s*, so s * (1 - 2^-18)
+// <= s*.  A subtree is pruned only when s exceeds the k-th distance kd
+// rounded up and scaled up by kBoundUp >= 1 / (1 - 2^-18) (TopK::kdf): then
+// s* >= s (1 - 2^-18) > kd, i.e. never when the exact rule (prune iff
+// mindist^2 > kth) would keep it.  Leaf points take the same float test.
 template <int D>
-__device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t *box, int dim) {
+__device__ __forceinline__ float box_dist_f(const int32_t *q, const int32_t *box, int dim) {
   const int dd = D ? D : dim;
   float s = 0.f;
 #pragma unroll
@@ -109,7 +115,7 @@ __device__ __forceinline__ float box_mindist_lb(const int32_t *q, const int32_t 
       s = fmaf(g, g, s);
     }
   }
-  return s * (1.0f - 3.814697265625e-06f);   // 1 - 2^-18
+  return s;
 }
 
 // A traversal stack entry: the node code and the lower bound of its box
@@ -142,11 +148,10 @@ __device__ __forceinline__ void cmp_swap(float &a, int &ca, float &b, int &cb) {
 }
 
 // The exact test of the points [pa, pz) of tree T's leaf order against the
-// query: a float filter first (the rounded sum of squares is within (D + 1) *
-// 2^-24 of the exact one, so after the 1 - 2^-18 scaling it exceeds the
-// rounded-up k-th distance only for a point whose exact distance exceeds the
-// k-th), then the exact int64 distance for the points that pass.  Erased
-// points (negative ids) are skipped.
+// query: a float filter first (the rounded sum of squares exceeds the scaled
+// k-th distance TopK::kdf only for a point whose exact distance exceeds the
+// k-th, as for box_dist_f), then the exact int64 distance for the points that
+// pass.  Erased points (negative ids) are skipped.
 template <int D, bool STATS, class TK>
 __device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, const int32_t *q, int dim,
                                           int rs, int k, TK &best, unsigned long long &npts) {
@@ -172,7 +177,7 @@ __device__ __forceinline__ void scan_leaf(const TreeView &T, int pa, int pz, con
         const float g = (float)(q[c] - p[c]);
         sf = fmaf(g, g, sf);
       }
-      if (sf * (1.0f - 3.814697265625e-06f) > best.kdf) continue;
+      if (sf > best.kdf) continue;
 #pragma unroll
       for (int c = 0; c < (D ? D : 1); ++c) {
         int32_t g = q[c] - p[c];
@@ -203,13 +208,12 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
   const int rec = packed_node_ints(dim);
   const int rs = rec_ints(dim);
   const float kInf = __int_as_float(0x7f800000);
-  const float kScale = 1.0f - 3.814697265625e-06f;   // 1 - 2^-18, as in box_mindist_lb
   unsigned long long unused = 0;
   int sp = 0;
   uint64_t cur = 0;   // the next entry to visit (code >= 0: record; < 0: leaf -1-code)
   bool hc = false;
   if (active) {
-    cur = stack_entry(box_mindist_lb<D>(q, T.box, dim), T.h > 0 ? 0 : -1);
+    cur = stack_entry(box_dist_f<D>(q, T.box, dim), T.h > 0 ? 0 : -1);
     hc = true;
   }
   const int32_t nleaf = (int32_t)((int64_t)1 << T.h);
@@ -247,7 +251,7 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
       const int32_t *r = T.pk + (int64_t)code * rec;
       const int4 cd = *reinterpret_cast<const int4 *>(r);
       const int4 lv = *reinterpret_cast<const int4 *>(r + 4);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;   // box distances (see box_mindist_lb)
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;   // box distances (see box_dist_f)
 #pragma unroll
       for (int c = 0; c < (D ? D : kMaxDim); ++c) {
         if (c < dim) {
@@ -267,8 +271,8 @@ __device__ __forceinline__ void walk_packed(const KnnJob &J, const TreeView &T, 
       }
       // entries without live points (and the two unused ones of an odd
       // tree's root) are never visited
-      float b0 = lv.x > 0 ? s0 * kScale : kInf, b1 = lv.y > 0 ? s1 * kScale : kInf;
-      float b2 = lv.z > 0 ? s2 * kScale : kInf, b3 = lv.w > 0 ? s3 * kScale : kInf;
+      float b0 = lv.x > 0 ? s0 : kInf, b1 = lv.y > 0 ? s1 : kInf;
+      float b2 = lv.z > 0 ? s2 : kInf, b3 = lv.w > 0 ? s3 : kInf;
       int c0 = cd.x, c1 = cd.y, c2 = cd.z, c3 = cd.w;
       // ascending by bound: five compare-exchanges
       cmp_swap(b0, c0, b1, c1);
@@ -316,7 +320,7 @@ __device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, c
   const float kInf = __int_as_float(0x7f800000);
   const int32_t nleaf = (int32_t)((int64_t)1 << T.h);
   int sp = 0;
-  stk[sp++] = stack_entry(box_mindist_lb<D>(q, T.box, dim), 0);   // code: node slot
+  stk[sp++] = stack_entry(box_dist_f<D>(q, T.box, dim), 0);   // code: node slot
   while (sp > 0) {
     const uint64_t e = stk[--sp];
     const int v = (int)(uint32_t)e;
@@ -333,8 +337,8 @@ __device__ __forceinline__ void walk_nodes(const KnnJob &J, const TreeView &T, c
     } else if (nd.l >= T.nnodes || nd.r < 0 || nd.r >= T.nnodes || sp + 2 > kStack) {
       atomicOr(J.err, sp + 2 > kStack ? kErrStack : kErrChild);
     } else {
-      const float ml = T.live[nd.l] > 0 ? box_mindist_lb<D>(q, T.box + (int64_t)nd.l * 2 * dim, dim) : kInf;
-      const float mr = T.live[nd.r] > 0 ? box_mindist_lb<D>(q, T.box + (int64_t)nd.r * 2 * dim, dim) : kInf;
+      const float ml = T.live[nd.l] > 0 ? box_dist_f<D>(q, T.box + (int64_t)nd.l * 2 * dim, dim) : kInf;
+      const float mr = T.live[nd.r] > 0 ? box_dist_f<D>(q, T.box + (int64_t)nd.r * 2 * dim, dim) : kInf;
       const bool lfirst = ml <= mr;
       const int vn = lfirst ? nd.l : nd.r, vf = lfirst ? nd.r : nd.l;
       const float mn = lfirst ? ml : mr, mf = lfirst ? mr : ml;
