@@ -467,9 +467,12 @@ __global__ void k_fill_many(const FillSeg *segs, const int64_t *pre, int nseg) {
     case kFillPoolTail: g.dst[i] = pool_entry(g, g.from + i); break;
     case kFillIota: g.dst[i] = (int32_t)(g.first + i); break;
     case kFillZero: g.dst[i] = 0; break;
-    case kFillAlive: {
+    case kFillAlive: {   // consecutive ids: the lanes on one word OR their bits first
       const int64_t id = g.first + i;
-      atomicOr(&g.alive[id >> 5], 1u << (id & 31));
+      uint32_t *wd = &g.alive[id >> 5];
+      const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)wd);
+      const unsigned bits = __reduce_or_sync(peers, 1u << (id & 31));
+      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(wd, bits);
       break;
     }
   }
